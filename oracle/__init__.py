@@ -1,0 +1,215 @@
+"""FP64 CPU oracle for the FDM layer-case time step (arXiv 1911.03225).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by
+the CPU-baseline leg of ``bench.py``; never by the product path.  The arithmetic lives in
+``fdm_oracle.c`` (plain C, FP64); this module only marshals numpy arrays through ctypes.
+It shares no code with the CUDA library and never loads it.
+"""
+import ctypes as C
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_oracle())
+        d = C.POINTER(C.c_double)
+        _lib.oracle_fft1d.argtypes = [C.c_int, d, d, C.c_int]
+        _lib.oracle_fft2d.argtypes = [C.c_int, C.c_int, d, d, C.c_int]
+        _lib.oracle_layer_symbol.argtypes = [C.c_double] * 5
+        _lib.oracle_layer_symbol.restype = C.c_double
+        _lib.oracle_kernel_table.argtypes = [C.c_int] * 4 + [C.c_double, C.c_double, d]
+        _lib.oracle_static_tau.argtypes = [C.c_int, C.c_int, d, d, C.c_double, d]
+        _lib.oracle_curl_inverse.argtypes = [C.c_int, C.c_int, C.c_double, d, d, C.c_double, d, d]
+        _lib.oracle_curl_inverse.restype = C.c_double
+        _lib.oracle_alpha_from_up.argtypes = [C.c_int, C.c_int, C.c_double, d, d, d]
+        _lib.oracle_knp1d_step.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, d, d, d]
+        _lib.oracle_knp2d_step.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, d, d, d]
+        _lib.oracle_sum.argtypes = [C.c_size_t, d]
+        _lib.oracle_sum.restype = C.c_double
+        _lib.oracle_alpha_sums.argtypes = [C.c_int, C.c_int, C.c_double, d, d]
+        _lib.oracle_run.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d]
+        _lib.oracle_run.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Params(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("nz", C.c_int32), ("nh", C.c_int32),
+                ("dx", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("velocity_mode", C.c_int32),
+                ("v0", C.c_double), ("mobility", C.c_double), ("tau_y", C.c_double),
+                ("beta", C.c_double), ("theta", C.c_double), ("cfl", C.c_double),
+                ("dt_max", C.c_double),
+                ("loading_mode", C.c_int32),
+                ("sigma_bar13", C.c_double), ("eps_bar13_0", C.c_double),
+                ("eps_bar13_rate", C.c_double),
+                ("time_level", C.c_int32)]
+
+
+class _Scalars(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
+                ("max_abs_v0", C.c_double), ("mean_up13", C.c_double),
+                ("eps_bar13", C.c_double), ("sigma_bar13", C.c_double)]
+
+
+@dataclass
+class Params:
+    """Dimensionless problem parameters (Sec. 3.2.1 non-dimensionalisation)."""
+    n1: int
+    n2: int
+    nz: int = 0            # 0 -> cubic cell, nz = n1
+    nh: int = 4
+    dx: float = 1.0
+    E: float = 1.0
+    nu: float = 0.3
+    velocity_mode: int = 0  # 0 prescribed uniform v0, 1 stress driven
+    v0: float = 1.0
+    mobility: float = 1.0
+    tau_y: float = 0.0
+    beta: float = 1.0
+    theta: float = 1.0
+    cfl: float = 0.5
+    dt_max: float = 0.0
+    loading_mode: int = 0   # 0 stress, 1 strain ramp, 2 zero mean stress
+    sigma_bar13: float = 0.0
+    eps_bar13_0: float = 0.0
+    eps_bar13_rate: float = 0.0
+    time_level: int = 0     # 0 midpoint, 1 literal
+
+    @property
+    def mu(self):
+        return self.E / (2.0 * (1.0 + self.nu))
+
+    def _c(self):
+        d = asdict(self)
+        if d["nz"] == 0:
+            d["nz"] = d["n1"]
+        return _Params(**d)
+
+
+def fft1d(x, sign=-1):
+    x = np.asarray(x, dtype=np.complex128)
+    re, im = _f64(x.real.copy()), _f64(x.imag.copy())
+    lib().oracle_fft1d(len(x), _p(re), _p(im), sign)
+    return re + 1j * im
+
+
+def fft2d(x, sign=-1):
+    x = np.asarray(x, dtype=np.complex128)
+    n2, n1 = x.shape
+    re, im = _f64(x.real.copy()), _f64(x.imag.copy())
+    lib().oracle_fft2d(n1, n2, _p(re), _p(im), sign)
+    return re + 1j * im
+
+
+def layer_symbol(n1, n2, n3, mu, nu):
+    return lib().oracle_layer_symbol(n1, n2, n3, mu, nu)
+
+
+def kernel_table(n1, n2, nz, nh, mu, nu):
+    K = np.zeros((n2, n1))
+    lib().oracle_kernel_table(n1, n2, nz, nh, mu, nu, _p(K))
+    return K
+
+
+def static_tau(up13, K, sigma_bar13=0.0):
+    up13, K = _f64(up13), _f64(K)
+    out = np.zeros_like(up13)
+    n2, n1 = up13.shape
+    lib().oracle_static_tau(n1, n2, _p(up13), _p(K), sigma_bar13, _p(out))
+    return out
+
+
+def curl_inverse(a11, a12, mean_up13=0.0, dx=1.0):
+    """Returns (U13, relative divergence residual, mean alpha (2,))."""
+    a11, a12 = _f64(a11), _f64(a12)
+    n2, n1 = a11.shape
+    out = np.zeros_like(a11)
+    ma = np.zeros(2)
+    r = lib().oracle_curl_inverse(n1, n2, dx, _p(a11), _p(a12), mean_up13, _p(out), _p(ma))
+    return out, r, ma
+
+
+def alpha_from_up(up13, dx=1.0):
+    up13 = _f64(up13)
+    n2, n1 = up13.shape
+    a11, a12 = np.zeros_like(up13), np.zeros_like(up13)
+    lib().oracle_alpha_from_up(n1, n2, dx, _p(up13), _p(a11), _p(a12))
+    return a11, a12
+
+
+def knp1d_step(phi, v0, dt, theta=1.0, h=1.0, time_level=0):
+    phi = _f64(phi)
+    v0 = _f64(np.broadcast_to(v0, phi.shape))
+    out = np.zeros_like(phi)
+    lib().oracle_knp1d_step(len(phi), h, theta, dt, time_level, _p(phi), _p(v0), _p(out))
+    return out
+
+
+def knp2d_step(phi, v0, dt, theta=1.0, h=1.0, time_level=0):
+    phi = _f64(phi)
+    v0 = _f64(np.broadcast_to(v0, phi.shape))
+    n2, n1 = phi.shape
+    out = np.zeros_like(phi)
+    lib().oracle_knp2d_step(n1, n2, h, theta, dt, time_level, _p(phi), _p(v0), _p(out))
+    return out
+
+
+def compensated_sum(x):
+    x = _f64(np.ravel(x))
+    return lib().oracle_sum(x.size, _p(x))
+
+
+def alpha_sums(up13, h=1.0):
+    up13 = _f64(up13)
+    n2, n1 = up13.shape
+    out = np.zeros(5)
+    lib().oracle_alpha_sums(n1, n2, h, _p(up13), _p(out))
+    return out
+
+
+@dataclass
+class State:
+    up13: np.ndarray
+    step: int = 0
+    t: float = 0.0
+    dt: float = 0.0
+    max_abs_v0: float = 0.0
+    mean_up13: float = 0.0
+    eps_bar13: float = 0.0
+    sigma_bar13: float = 0.0
+    tau13: np.ndarray = field(default=None, repr=False)
+    v0: np.ndarray = field(default=None, repr=False)
+
+
+def run(params: Params, up13, nsteps, K=None, state: State = None):
+    """Advance ``nsteps`` FDM steps (Sec. 3.1.1) from ``up13`` (or ``state``)."""
+    p = params._c()
+    if K is None:
+        K = kernel_table(p.n1, p.n2, p.nz, p.nh, params.mu, params.nu)
+    if state is None:
+        state = State(up13=_f64(up13).copy())
+    sc = _Scalars(step=state.step, t=state.t, dt=state.dt, max_abs_v0=state.max_abs_v0,
+                  mean_up13=state.mean_up13, eps_bar13=state.eps_bar13,
+                  sigma_bar13=state.sigma_bar13)
+    u = _f64(state.up13).copy()
+    tau = np.zeros_like(u)
+    v0 = np.zeros_like(u)
+    rc = lib().oracle_run(C.byref(p), _p(_f64(K)), _p(u), C.byref(sc), int(nsteps), _p(tau), _p(v0))
+    return State(up13=u, step=sc.step, t=sc.t, dt=sc.dt, max_abs_v0=sc.max_abs_v0,
+                 mean_up13=sc.mean_up13, eps_bar13=sc.eps_bar13, sigma_bar13=sc.sigma_bar13,
+                 tau13=tau, v0=v0), rc

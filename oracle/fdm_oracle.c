@@ -1,0 +1,564 @@
+/*
+ * fdm_oracle.c -- plain, slow, FP64 CPU oracle for the field-dislocation-mechanics
+ * (FDM) layer-case time step of Morin, Brenner & Suquet, "Numerical simulation of
+ * model problems in plasticity based on field dislocation mechanics" (arXiv 1911.03225).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  It shares no code, header, table or
+ * helper with the CUDA path and never calls it.
+ *
+ * What it computes, in the paper's order (section 3, "General resolution procedure"):
+ *   1. static problem (Sec. 3.1.2, Eq. for sigma-hat, and Sec. 3.2.1 layer reduction):
+ *        tau13 = IFFT( K(xi1,xi2) * FFT(U13) ) + sigma_bar13
+ *      where K is the layer average of the homogeneous isotropic Green-operator stress
+ *      symbol m(xi) over the 3-D cell (derivation in oracle_kernel_table below);
+ *   2. celerity v0 = (tau_y cos(U13/beta) - tau13)/eta~ (Sec. 3.2.2, Hamiltonian H),
+ *      or a prescribed uniform v0 (Sec. 4.1);
+ *   3. time step from the CFL rule |v0| dt/dx = CFL (Sec. 4.2, Sec. 5.2);
+ *   4. the Kurganov-Noelle-Petrova central-upwind Hamilton-Jacobi update
+ *      (Sec. 3.2.2 Steps 1-4 in 1-D, Sec. 3.2.3 Steps 1-4 in 2-D);
+ *   5. macroscopic loading update (Sec. 5.1: zero mean stress, strain ramp).
+ *
+ * Readings of passages the paper leaves open (each also listed in the design notes):
+ *   G1  2-D projection weights: the 1-D projection of Sec. 3.2.2 Step 4 applied in x and
+ *       in y (a bilinear interpolation between the four intermediate points); the mixed
+ *       a-b+ and a+b- terms therefore carry a minus sign.
+ *   G2  2-D interpolant: on the quadrant cell next to the node, the limited row quadratic
+ *       plus the limited column quadratic plus the bilinear cross term.
+ *   G3  time level: default = midpoint rule (gradient advanced by dt/2 with the local
+ *       Hessian of the interpolant); option "literal" evaluates H at t^n as printed.
+ *   G4  one-sided speeds are the max/min over all four (phi_x^s, phi_y^t) pairs.
+ *   G5  a+ = a- (= 0): the two intermediate points coincide; weights 1/2, 1/2.
+ *   G6  dH/dp at grad phi = 0 is 0.
+ *   G7  v0 is the node's value from the previous static solve; grad v0 is ignored.
+ *   G8  continuous frequencies xi = 2 pi k~/(N dx); even symbols kept at Nyquist, odd
+ *       symbols (curl-inverse, spectral derivative) zeroed there.
+ *   G9  layer of nh voxels in a cubic periodic cell of nz voxels.
+ *   G10 strain control: sigma_bar13 = 2 mu eps_bar13 - mu (nh/nz) <U13>.
+ *
+ * Layout: every 2-D field is row-major [n2][n1] (x1 fastest), FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Complex FFT: textbook iterative radix-2 Cooley-Tukey (decimation in time).  */
+/* sign = -1 forward, +1 inverse; unnormalised.  n must be a power of two.     */
+/* ------------------------------------------------------------------------- */
+static int is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+void oracle_fft1d(int n, double *re, double *im, int sign)
+{
+    /* bit-reversal permutation */
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i]; re[i] = re[j]; re[j] = t;
+            t = im[i]; im[i] = im[j]; im[j] = t;
+        }
+    }
+    /* butterflies */
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len >> 1;
+        for (int k = 0; k < half; k++) {
+            double ang = sign * 2.0 * OR_PI * (double)k / (double)len;
+            double wr = cos(ang), wi = sin(ang);
+            for (int s = 0; s < n; s += len) {
+                int a = s + k, b = s + k + half;
+                double xr = re[b] * wr - im[b] * wi;
+                double xi = re[b] * wi + im[b] * wr;
+                re[b] = re[a] - xr; im[b] = im[a] - xi;
+                re[a] = re[a] + xr; im[a] = im[a] + xi;
+            }
+        }
+    }
+}
+
+/* 2-D transform of a complex [n2][n1] array: all rows, then all columns. */
+void oracle_fft2d(int n1, int n2, double *re, double *im, int sign)
+{
+    for (int y = 0; y < n2; y++) oracle_fft1d(n1, re + (size_t)y * n1, im + (size_t)y * n1, sign);
+    double *cr = malloc(sizeof(double) * n2), *ci = malloc(sizeof(double) * n2);
+    for (int x = 0; x < n1; x++) {
+        for (int y = 0; y < n2; y++) { cr[y] = re[(size_t)y * n1 + x]; ci[y] = im[(size_t)y * n1 + x]; }
+        oracle_fft1d(n2, cr, ci, sign);
+        for (int y = 0; y < n2; y++) { re[(size_t)y * n1 + x] = cr[y]; im[(size_t)y * n1 + x] = ci[y]; }
+    }
+    free(cr); free(ci);
+}
+
+/* signed frequency index k~ in (-n/2, n/2]; at Nyquist k~ = +n/2 */
+static int signed_index(int k, int n) { return (k <= n / 2) ? k : k - n; }
+
+/* ------------------------------------------------------------------------- */
+/* Static problem (Sec. 3.1.2 and Sec. 3.2.1).                                 */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Green-operator stress symbol for U^p = U13 e1 (x) e3 in an isotropic medium.
+ * From sigma-hat = (C0:Gamma0-hat - I):C0:U^p-hat (Sec. 3.1.2) with
+ * Gamma0-hat = [xi (x) (xi.C0.xi)^-1 (x) xi]^(s):  the polarisation stress is
+ * s = 2 mu sym(U^p); with n = xi/|xi|,
+ *   eps13-hat = U/2 (n1^2 + n3^2) - 2 mu kappa n1^2 n3^2 U,  kappa = (lambda+mu)/(mu(lambda+2mu)),
+ *   sigma13-hat = 2 mu (eps13-hat - U/2) = m(n) U,
+ *   m(n) = -mu [ n2^2 + 2 n1^2 n3^2 / (1 - nu) ].
+ */
+double oracle_layer_symbol(double n1, double n2, double n3, double mu, double nu)
+{
+    return -mu * (n2 * n2 + 2.0 * n1 * n1 * n3 * n3 / (1.0 - nu));
+}
+
+/*
+ * K(xi1,xi2): layer average (Sec. 3.2.1, tau13 = (1/h) int sigma13 dx3) of the 3-D
+ * stress produced by U13(x1,x2) chi(x3), chi = indicator of nh contiguous voxels of a
+ * periodic cell nz voxels deep (G9):
+ *   tau13-hat(xi1,xi2) = U13-hat * (1/(nz nh)) sum_k3 m(xi1,xi2,xi3) |chi-hat(k3)|^2,
+ *   |chi-hat(k3)|^2 = sin^2(pi k3 nh / nz) / sin^2(pi k3 / nz)   (= nh^2 at k3 = 0).
+ * The (0,0,0) mode is excluded (it carries the macroscopic stress).  Output [n2][n1].
+ */
+void oracle_kernel_table(int n1, int n2, int nz, int nh, double mu, double nu, double *K)
+{
+    for (int k2 = 0; k2 < n2; k2++) {
+        for (int k1 = 0; k1 < n1; k1++) {
+            /* frequencies on a cubic-voxel grid (dx cancels in the direction n) */
+            double x1 = (double)signed_index(k1, n1) / (double)n1;
+            double x2 = (double)signed_index(k2, n2) / (double)n2;
+            double acc = 0.0;
+            for (int k3 = 0; k3 < nz; k3++) {
+                double x3 = (double)signed_index(k3, nz) / (double)nz;
+                double r2 = x1 * x1 + x2 * x2 + x3 * x3;
+                if (r2 == 0.0) continue;
+                double r = sqrt(r2);
+                double w;
+                if (k3 == 0) {
+                    w = (double)nh * (double)nh;
+                } else {
+                    double sn = sin(OR_PI * (double)k3 * (double)nh / (double)nz);
+                    double sd = sin(OR_PI * (double)k3 / (double)nz);
+                    w = (sn * sn) / (sd * sd);
+                }
+                acc += oracle_layer_symbol(x1 / r, x2 / r, x3 / r, mu, nu) * w;
+            }
+            K[(size_t)k2 * n1 + k1] = acc / ((double)nz * (double)nh);
+        }
+    }
+}
+
+/* tau13 = IFFT2(K * FFT2(U13)) + sigma_bar13 (mean of tau13 = sigma_bar13, Sec. 3.1.2). */
+void oracle_static_tau(int n1, int n2, const double *up13, const double *K, double sigma_bar13,
+                       double *tau13)
+{
+    size_t n = (size_t)n1 * n2;
+    double *re = malloc(sizeof(double) * n), *im = calloc(n, sizeof(double));
+    memcpy(re, up13, sizeof(double) * n);
+    oracle_fft2d(n1, n2, re, im, -1);
+    for (size_t i = 0; i < n; i++) { re[i] *= K[i]; im[i] *= K[i]; }
+    re[0] = sigma_bar13 * (double)n;
+    im[0] = 0.0;
+    oracle_fft2d(n1, n2, re, im, +1);
+    for (size_t i = 0; i < n; i++) tau13[i] = re[i] / (double)n;
+    free(re); free(im);
+}
+
+/*
+ * Curl inverse (Sec. 3.1.2, U^p-hat = i (alpha-hat x xi)/|xi|^2; Sec. 2.2 Poisson problem):
+ * for the layer ansatz alpha = a11 e1(x)e1 + a12 e1(x)e2 (Sec. 3.2.1) the 13 component is
+ *   U13-hat = i (a11-hat xi2 - a12-hat xi1) / |xi|^2,   U13-hat(0) = mean_up13 * N.
+ * Odd multipliers are zeroed at their Nyquist index (G8).  Returns the relative
+ * divergence residual |xi1 a11-hat + xi2 a12-hat| / |alpha-hat| (div alpha = 0, Sec. 2.1)
+ * and writes the mean of (a11, a12) to mean_alpha[2] (net Burgers vector / area).
+ */
+double oracle_curl_inverse(int n1, int n2, double dx, const double *a11, const double *a12,
+                           double mean_up13, double *up13, double *mean_alpha)
+{
+    size_t n = (size_t)n1 * n2;
+    double *r11 = malloc(sizeof(double) * n), *i11 = calloc(n, sizeof(double));
+    double *r12 = malloc(sizeof(double) * n), *i12 = calloc(n, sizeof(double));
+    memcpy(r11, a11, sizeof(double) * n);
+    memcpy(r12, a12, sizeof(double) * n);
+    oracle_fft2d(n1, n2, r11, i11, -1);
+    oracle_fft2d(n1, n2, r12, i12, -1);
+    if (mean_alpha) { mean_alpha[0] = r11[0] / (double)n; mean_alpha[1] = r12[0] / (double)n; }
+    double num = 0.0, den = 0.0;
+    double *pr = malloc(sizeof(double) * n), *pi = malloc(sizeof(double) * n);
+    for (int k2 = 0; k2 < n2; k2++) {
+        for (int k1 = 0; k1 < n1; k1++) {
+            size_t i = (size_t)k2 * n1 + k1;
+            double xi1 = 2.0 * OR_PI * signed_index(k1, n1) / (n1 * dx);
+            double xi2 = 2.0 * OR_PI * signed_index(k2, n2) / (n2 * dx);
+            double o1 = (2 * k1 == n1) ? 0.0 : xi1; /* odd use of xi1 */
+            double o2 = (2 * k2 == n2) ? 0.0 : xi2; /* odd use of xi2 */
+            double dr = o1 * r11[i] + o2 * r12[i], di = o1 * i11[i] + o2 * i12[i];
+            num += dr * dr + di * di;
+            den += (o1 * o1 + o2 * o2) * (r11[i] * r11[i] + i11[i] * i11[i] + r12[i] * r12[i] + i12[i] * i12[i]);
+            double q = xi1 * xi1 + xi2 * xi2;
+            if (q == 0.0) { pr[i] = 0.0; pi[i] = 0.0; continue; }
+            /* w = a11 xi2 - a12 xi1 ; U = i w / q */
+            double wr = r11[i] * o2 - r12[i] * o1;
+            double wi = i11[i] * o2 - i12[i] * o1;
+            pr[i] = -wi / q;
+            pi[i] = wr / q;
+        }
+    }
+    pr[0] = mean_up13 * (double)n;
+    pi[0] = 0.0;
+    oracle_fft2d(n1, n2, pr, pi, +1);
+    for (size_t i = 0; i < n; i++) up13[i] = pr[i] / (double)n;
+    free(r11); free(i11); free(r12); free(i12); free(pr); free(pi);
+    return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+/* alpha11 = -d2 U13, alpha12 = d1 U13 (Sec. 3.2.1), spectral derivatives, odd symbol
+ * zeroed at Nyquist (G8). */
+void oracle_alpha_from_up(int n1, int n2, double dx, const double *up13, double *a11, double *a12)
+{
+    size_t n = (size_t)n1 * n2;
+    double *re = malloc(sizeof(double) * n), *im = calloc(n, sizeof(double));
+    double *br = malloc(sizeof(double) * n), *bi = malloc(sizeof(double) * n);
+    memcpy(re, up13, sizeof(double) * n);
+    oracle_fft2d(n1, n2, re, im, -1);
+    /* a12 = i xi1 U */
+    for (int k2 = 0; k2 < n2; k2++)
+        for (int k1 = 0; k1 < n1; k1++) {
+            size_t i = (size_t)k2 * n1 + k1;
+            double xi1 = (2 * k1 == n1) ? 0.0 : 2.0 * OR_PI * signed_index(k1, n1) / (n1 * dx);
+            br[i] = -xi1 * im[i];
+            bi[i] = xi1 * re[i];
+        }
+    oracle_fft2d(n1, n2, br, bi, +1);
+    for (size_t i = 0; i < n; i++) a12[i] = br[i] / (double)n;
+    /* a11 = -i xi2 U */
+    for (int k2 = 0; k2 < n2; k2++)
+        for (int k1 = 0; k1 < n1; k1++) {
+            size_t i = (size_t)k2 * n1 + k1;
+            double xi2 = (2 * k2 == n2) ? 0.0 : 2.0 * OR_PI * signed_index(k2, n2) / (n2 * dx);
+            br[i] = xi2 * im[i];
+            bi[i] = -xi2 * re[i];
+        }
+    oracle_fft2d(n1, n2, br, bi, +1);
+    for (size_t i = 0; i < n; i++) a11[i] = br[i] / (double)n;
+    free(re); free(im); free(br); free(bi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Transport: Kurganov-Noelle-Petrova central-upwind scheme (Sec. 3.2.2-3.2.3) */
+/* ------------------------------------------------------------------------- */
+
+/* minmod of three arguments (Sec. 3.2.2, Step 1) */
+static double minmod3(double a, double b, double c)
+{
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* limited second difference (Delta phi)'_{j+1/2} from the four first differences
+ * D_{j-1/2}, D_{j+1/2}, D_{j+3/2} (Sec. 3.2.2 Step 1). */
+static double limited_second(double theta, double d_m, double d_c, double d_p)
+{
+    return minmod3(theta * (d_p - d_c), 0.5 * (d_p - d_m), theta * (d_c - d_m));
+}
+
+static int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+
+/*
+ * One 1-D KNP step (Sec. 3.2.2, Steps 1-4) for phi_t + v0 |phi_x| = 0 on a periodic
+ * row of n nodes, v0 given per node.  time_level: 0 = midpoint (G3), 1 = literal.
+ */
+void oracle_knp1d_step(int n, double h, double theta, double dt, int time_level,
+                       const double *phi, const double *v0, double *out)
+{
+    for (int j = 0; j < n; j++) {
+        double f_m2 = phi[wrap(j - 2, n)], f_m1 = phi[wrap(j - 1, n)], f0 = phi[j];
+        double f_p1 = phi[wrap(j + 1, n)], f_p2 = phi[wrap(j + 2, n)];
+        double D_m3 = f_m1 - f_m2, D_m1 = f0 - f_m1, D_p1 = f_p1 - f0, D_p3 = f_p2 - f_p1;
+        double S_p = limited_second(theta, D_m1, D_p1, D_p3); /* (Delta phi)'_{j+1/2} */
+        double S_m = limited_second(theta, D_m3, D_m1, D_p1); /* (Delta phi)'_{j-1/2} */
+        /* Step 2: one-sided derivatives and speeds, H'(p) = v0 sign(p) */
+        double px_p = D_p1 / h - S_p / (2.0 * h);
+        double px_m = D_m1 / h + S_m / (2.0 * h);
+        double c = v0[j];
+        double hp1 = (px_p > 0.0) ? c : (px_p < 0.0 ? -c : 0.0);
+        double hp2 = (px_m > 0.0) ? c : (px_m < 0.0 ? -c : 0.0);
+        double ap = fmax(fmax(hp1, hp2), 0.0), am = fmin(fmin(hp1, hp2), 0.0);
+        /* Step 3: values at x_{j+-} = x_j + a+- dt */
+        double res[2];
+        for (int s = 0; s < 2; s++) {
+            double d = (s == 0 ? ap : am) * dt;
+            double val, der, curv;
+            if (s == 0) { /* right cell [x_j, x_{j+1}] */
+                val = f0 + D_p1 * d / h + S_p * d * (d - h) / (2.0 * h * h);
+                der = D_p1 / h + S_p * (2.0 * d - h) / (2.0 * h * h);
+                curv = S_p / (h * h);
+            } else {      /* left cell [x_{j-1}, x_j] */
+                val = f0 + D_m1 * d / h + S_m * d * (d + h) / (2.0 * h * h);
+                der = D_m1 / h + S_m * (2.0 * d + h) / (2.0 * h * h);
+                curv = S_m / (h * h);
+            }
+            if (time_level == 0) {
+                double hprime = (der > 0.0) ? c : (der < 0.0 ? -c : 0.0);
+                der -= 0.5 * dt * curv * hprime;
+            }
+            res[s] = val - dt * c * fabs(der);
+        }
+        /* Step 4: projection */
+        double wp, wm;
+        if (ap - am > 0.0) { wp = -am / (ap - am); wm = ap / (ap - am); }
+        else { wp = 0.5; wm = 0.5; }
+        out[j] = wm * res[1] + wp * res[0];
+    }
+}
+
+/*
+ * One 2-D KNP step (Sec. 3.2.3, Steps 1-4) for phi_t + v0 sqrt(phi_x^2 + phi_y^2) = 0,
+ * periodic [n2][n1] grid, cell size h in both directions, v0 per node.
+ */
+void oracle_knp2d_step(int n1, int n2, double h, double theta, double dt, int time_level,
+                       const double *phi, const double *v0, double *out)
+{
+#define P(jj, kk) phi[(size_t)wrap((kk), n2) * n1 + wrap((jj), n1)]
+    for (int k = 0; k < n2; k++) {
+        for (int j = 0; j < n1; j++) {
+            double f0 = P(j, k);
+            /* Step 1, x: first differences and limited second differences along the row */
+            double Dx_m3 = P(j - 1, k) - P(j - 2, k), Dx_m1 = f0 - P(j - 1, k);
+            double Dx_p1 = P(j + 1, k) - f0, Dx_p3 = P(j + 2, k) - P(j + 1, k);
+            double Sx_p = limited_second(theta, Dx_m1, Dx_p1, Dx_p3);
+            double Sx_m = limited_second(theta, Dx_m3, Dx_m1, Dx_p1);
+            /* Step 1, y: same along the column */
+            double Dy_m3 = P(j, k - 1) - P(j, k - 2), Dy_m1 = f0 - P(j, k - 1);
+            double Dy_p1 = P(j, k + 1) - f0, Dy_p3 = P(j, k + 2) - P(j, k + 1);
+            double Sy_p = limited_second(theta, Dy_m1, Dy_p1, Dy_p3);
+            double Sy_m = limited_second(theta, Dy_m3, Dy_m1, Dy_p1);
+            /* one-sided derivatives at the node */
+            double px[2] = { Dx_p1 / h - Sx_p / (2.0 * h), Dx_m1 / h + Sx_m / (2.0 * h) };
+            double qy[2] = { Dy_p1 / h - Sy_p / (2.0 * h), Dy_m1 / h + Sy_m / (2.0 * h) };
+            double c = v0[(size_t)k * n1 + j];
+            /* Step 2: one-sided speeds over the four (phi_x^s, phi_y^t) pairs (G4, G6) */
+            double ap = 0.0, am = 0.0, bp = 0.0, bm = 0.0;
+            for (int s = 0; s < 2; s++)
+                for (int t = 0; t < 2; t++) {
+                    double p = px[s], q = qy[t];
+                    double r = sqrt(p * p + q * q);
+                    double Hp = (r > 0.0) ? c * p / r : 0.0;
+                    double Hq = (r > 0.0) ? c * q / r : 0.0;
+                    ap = fmax(ap, Hp); am = fmin(am, Hp);
+                    bp = fmax(bp, Hq); bm = fmin(bm, Hq);
+                }
+            /* Step 3: values at the four intermediate points (G2, G3) */
+            double psi[2][2];
+            for (int s = 0; s < 2; s++) {
+                double dx = (s == 0 ? ap : am) * dt;
+                int cx = (s == 0) ? 1 : -1;
+                double X, dX, Sx;
+                if (s == 0) {
+                    X = Dx_p1 * dx / h + Sx_p * dx * (dx - h) / (2.0 * h * h);
+                    dX = Dx_p1 / h + Sx_p * (2.0 * dx - h) / (2.0 * h * h);
+                    Sx = Sx_p;
+                } else {
+                    X = Dx_m1 * dx / h + Sx_m * dx * (dx + h) / (2.0 * h * h);
+                    dX = Dx_m1 / h + Sx_m * (2.0 * dx + h) / (2.0 * h * h);
+                    Sx = Sx_m;
+                }
+                for (int t = 0; t < 2; t++) {
+                    double dy = (t == 0 ? bp : bm) * dt;
+                    int cy = (t == 0) ? 1 : -1;
+                    double Y, dY, Sy;
+                    if (t == 0) {
+                        Y = Dy_p1 * dy / h + Sy_p * dy * (dy - h) / (2.0 * h * h);
+                        dY = Dy_p1 / h + Sy_p * (2.0 * dy - h) / (2.0 * h * h);
+                        Sy = Sy_p;
+                    } else {
+                        Y = Dy_m1 * dy / h + Sy_m * dy * (dy + h) / (2.0 * h * h);
+                        dY = Dy_m1 / h + Sy_m * (2.0 * dy + h) / (2.0 * h * h);
+                        Sy = Sy_m;
+                    }
+                    double cross = (P(j + cx, k + cy) - P(j + cx, k) - P(j, k + cy) + f0) /
+                                   ((double)(cx * cy) * h * h);
+                    double val = f0 + X + Y + cross * dx * dy;
+                    double p = dX + cross * dy;
+                    double q = dY + cross * dx;
+                    if (time_level == 0) {
+                        double r = sqrt(p * p + q * q);
+                        double gx = (r > 0.0) ? c * p / r : 0.0;
+                        double gy = (r > 0.0) ? c * q / r : 0.0;
+                        double hxx = Sx / (h * h), hyy = Sy / (h * h);
+                        double np = p - 0.5 * dt * (hxx * gx + cross * gy);
+                        double nq = q - 0.5 * dt * (cross * gx + hyy * gy);
+                        p = np; q = nq;
+                    }
+                    psi[s][t] = val - dt * c * sqrt(p * p + q * q);
+                }
+            }
+            /* Step 4: projection, the 1-D weights in x and in y (G1, G5) */
+            double wx[2], wy[2];
+            if (ap - am > 0.0) { wx[0] = -am / (ap - am); wx[1] = ap / (ap - am); }
+            else { wx[0] = 0.5; wx[1] = 0.5; }
+            if (bp - bm > 0.0) { wy[0] = -bm / (bp - bm); wy[1] = bp / (bp - bm); }
+            else { wy[0] = 0.5; wy[1] = 0.5; }
+            out[(size_t)k * n1 + j] = wx[0] * wy[0] * psi[0][0] + wx[0] * wy[1] * psi[0][1] +
+                                      wx[1] * wy[0] * psi[1][0] + wx[1] * wy[1] * psi[1][1];
+        }
+    }
+#undef P
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reductions                                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Neumaier-compensated sum */
+double oracle_sum(size_t n, const double *x)
+{
+    double s = 0.0, c = 0.0;
+    for (size_t i = 0; i < n; i++) {
+        double t = s + x[i];
+        if (fabs(s) >= fabs(x[i])) c += (s - t) + x[i];
+        else c += (x[i] - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+/*
+ * Dislocation-density sums of the staggered (forward-difference) Nye components
+ * a12 = (U_{j+1,k} - U_{jk})/h, a11 = -(U_{j,k+1} - U_{jk})/h (Sec. 3.2.1), over all nodes:
+ * out[0] = sum a12>0, out[1] = sum a12<0, out[2] = sum a11>0, out[3] = sum a11<0,
+ * out[4] = sum sqrt(a11^2 + a12^2).   The total Burgers vector per unit length
+ * (Sec. 4.2, b = int alpha.n dS) is h^2 (out[0] + out[1]) resp. h^2 (out[2] + out[3]).
+ */
+void oracle_alpha_sums(int n1, int n2, double h, const double *up13, double *out)
+{
+    size_t n = (size_t)n1 * n2;
+    double *t = malloc(sizeof(double) * n * 5);
+    for (int k = 0; k < n2; k++)
+        for (int j = 0; j < n1; j++) {
+            size_t i = (size_t)k * n1 + j;
+            double a12 = (up13[(size_t)k * n1 + wrap(j + 1, n1)] - up13[i]) / h;
+            double a11 = -(up13[(size_t)wrap(k + 1, n2) * n1 + j] - up13[i]) / h;
+            t[i] = a12 > 0.0 ? a12 : 0.0;
+            t[n + i] = a12 < 0.0 ? a12 : 0.0;
+            t[2 * n + i] = a11 > 0.0 ? a11 : 0.0;
+            t[3 * n + i] = a11 < 0.0 ? a11 : 0.0;
+            t[4 * n + i] = sqrt(a11 * a11 + a12 * a12);
+        }
+    for (int q = 0; q < 5; q++) out[q] = oracle_sum(n, t + q * n);
+    free(t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Full time step (Sec. 3.1.1: static problem with U^p_n, then transport).     */
+/* ------------------------------------------------------------------------- */
+
+/* parameter block, mirrored field by field by the ctypes wrapper */
+typedef struct {
+    int32_t n1, n2, nz, nh;
+    double dx, E, nu;
+    int32_t velocity_mode;      /* 0 prescribed uniform v0, 1 stress driven */
+    double v0, mobility, tau_y, beta, theta, cfl, dt_max;
+    int32_t loading_mode;       /* 0 stress (sigma_bar13), 1 strain ramp, 2 zero mean stress */
+    double sigma_bar13, eps_bar13_0, eps_bar13_rate;
+    int32_t time_level;         /* 0 midpoint, 1 literal */
+} oracle_params;
+
+/* scalar state carried between steps */
+typedef struct {
+    int64_t step;
+    double t, dt, max_abs_v0, mean_up13, eps_bar13, sigma_bar13;
+} oracle_scalars;
+
+static double shear_modulus(const oracle_params *p) { return p->E / (2.0 * (1.0 + p->nu)); }
+
+/* macroscopic stress at step `step` (Sec. 3.1.2 sigma-hat(0); Sec. 5.1 loading paths; G10) */
+static void loading(const oracle_params *p, int64_t step, double mean_up13, double *eps, double *sig)
+{
+    double mu = shear_modulus(p), frac = (double)p->nh / (double)p->nz;
+    if (p->loading_mode == 0) {
+        *sig = p->sigma_bar13;
+        *eps = (p->sigma_bar13 + mu * frac * mean_up13) / (2.0 * mu);
+    } else if (p->loading_mode == 1) {
+        *eps = p->eps_bar13_0 + p->eps_bar13_rate * (double)step;
+        *sig = 2.0 * mu * (*eps) - mu * frac * mean_up13;
+    } else {
+        *eps = 0.5 * frac * mean_up13;  /* eps_bar13 = <U13>/2 over the cell (Sec. 5.1) */
+        *sig = 0.0;
+    }
+}
+
+/*
+ * Advance `nsteps` steps in place.  K is the table from oracle_kernel_table; tau13 and v0
+ * (may be NULL) receive the fields of the last step's static solve.  Returns 0, or 1 if a
+ * non-finite value appeared.
+ */
+int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_scalars *st,
+               int nsteps, double *tau_out, double *v0_out)
+{
+    int n1 = p->n1, n2 = p->n2;
+    size_t n = (size_t)n1 * n2;
+    double *tau = malloc(sizeof(double) * n), *v0 = malloc(sizeof(double) * n);
+    double *nxt = malloc(sizeof(double) * n);
+    int rc = 0;
+    for (int it = 0; it < nsteps; it++) {
+        double mean = oracle_sum(n, up13) / (double)n;
+        double eps, sig;
+        loading(p, st->step, mean, &eps, &sig);
+        /* static problem with the previous plastic distortion (Sec. 3.1.1) */
+        oracle_static_tau(n1, n2, up13, K, sig, tau);
+        /* celerity (Sec. 3.2.3 Hamiltonian; Sec. 4.1 prescribed) */
+        double vmax = 0.0;
+        for (size_t i = 0; i < n; i++) {
+            double c;
+            if (p->velocity_mode == 0) c = p->v0;
+            else {
+                double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;
+                c = p->mobility * (fr - tau[i]);
+            }
+            v0[i] = c;
+            if (fabs(c) > vmax) vmax = fabs(c);
+        }
+        /* CFL time step (Sec. 5.2: dt adjusted to keep the CFL number) */
+        double dt;
+        if (vmax > 0.0) {
+            dt = p->cfl * p->dx / vmax;
+            if (p->dt_max > 0.0 && dt > p->dt_max) dt = p->dt_max;
+        } else {
+            dt = p->dt_max > 0.0 ? p->dt_max : 0.0;
+        }
+        oracle_knp2d_step(n1, n2, p->dx, p->theta, dt, p->time_level, up13, v0, nxt);
+        memcpy(up13, nxt, sizeof(double) * n);
+        st->step += 1;
+        st->t += dt;
+        st->dt = dt;
+        st->max_abs_v0 = vmax;
+        st->mean_up13 = oracle_sum(n, up13) / (double)n;
+        /* loading state of the new step (used by the next static solve) */
+        loading(p, st->step, st->mean_up13, &eps, &sig);
+        st->eps_bar13 = eps;
+        st->sigma_bar13 = sig;
+        if (!isfinite(dt)) rc = 1;
+    }
+    if (nsteps == 0) {
+        double mean = oracle_sum(n, up13) / (double)n, eps, sig;
+        loading(p, st->step, mean, &eps, &sig);
+        oracle_static_tau(n1, n2, up13, K, sig, tau);
+        for (size_t i = 0; i < n; i++) {
+            double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;
+            v0[i] = (p->velocity_mode == 0) ? p->v0 : p->mobility * (fr - tau[i]);
+        }
+        st->mean_up13 = mean; st->eps_bar13 = eps; st->sigma_bar13 = sig;
+    }
+    for (size_t i = 0; i < n; i++) if (!isfinite(up13[i])) { rc = 1; break; }
+    if (tau_out) memcpy(tau_out, tau, sizeof(double) * n);
+    if (v0_out) memcpy(v0_out, v0, sizeof(double) * n);
+    free(tau); free(v0); free(nxt);
+    return rc;
+}
+
+/* size check used by the wrapper */
+int oracle_valid_size(int n) { return is_pow2(n) && n >= 4; }
