@@ -1,0 +1,372 @@
+"""Benchmark of the FDM layer-case time step on GB300 (cell-steps/s).
+
+Workload (default): coupled FDM under loading on a 2048 x 2048 periodic grid -- seeded
+zero-mean Gaussian random U13 field (correlation length 16 cells, RMS |alpha| 0.1),
+stress-driven velocity with M = 1, E = 1, nu = 0.3, macroscopic shear strain ramped by 1e-4
+per step, adaptive CFL 0.4 time step, minmod limiter.  One "step" = static FFT solve +
+celerity + time-step reduction + KNP transport update (the whole hot path).
+
+Timing: inputs resident in HBM; the L2 is flushed (256 MiB write) before every timed step
+and each step is timed with CUDA events on the library's stream, phase by phase, so the
+dominant kernel's duration is measured in the same run.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n 2048] [--precision fp64|mixed]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDM cell-steps/s (FFT stress + Godunov transport), %HBM roofline; p50/p99 serve"
+UNIT = "cell-steps/s"
+PHASES = ["row_forward", "col_pass", "row_inverse", "knp_step"]
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_GFLOPS = 1250.0            # GB300 FP64 rate (profiling recipe table)
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
+
+
+def workload_params(n, precision):
+    from paper_1911_03225_gb300.binding import Params, V_STRESS, LOAD_STRAIN_RAMP, FP64, MIXED
+    return Params(n1=n, n2=n, velocity_mode=V_STRESS, mobility=1.0, loading_mode=LOAD_STRAIN_RAMP,
+                  eps_bar13_rate=1e-4, cfl=0.4, theta=1.0, E=1.0, nu=0.3,
+                  precision=MIXED if precision == "mixed" else FP64)
+
+
+def workload_input(n, seed):
+    from paper_1911_03225_gb300 import inputs
+    return inputs.random_up(n, seed=seed, ell=16.0, rms_alpha=0.1)
+
+
+def bytes_per_cell(elt):
+    """Algorithmic HBM bytes per cell and launch of each kernel (one read + one write of
+    every array the kernel must touch; halo re-reads and tables excluded)."""
+    return {"row_forward": 2 * elt,   # read U13, write half spectrum (n1/2 complex per row)
+            "col_pass": 2 * elt,      # read + write the half spectrum in place
+            "row_inverse": 2 * elt,   # read half spectrum, write tau13
+            "knp_step": 3 * elt}      # read U13 and tau13, write U13^{n+1}
+
+
+# FP arithmetic per node of the KNP update (counted from knp_node in fdm_device.cuh:
+# +,-,*,min,max,compare = 1, fused multiply-add = 2, sqrt and divide = 1 each).
+KNP_FLOPS_PER_CELL = 330
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_bandwidth_gbs", "copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured (MEASURED_PEAKS.json %s)" % k
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def time_device(sim, steps, flush, stream):
+    """Per-step, per-phase CUDA-event timing with an L2 flush before each step."""
+    import torch
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(len(PHASES) + 1)]
+        e[0].record(stream)
+        for ph in range(len(PHASES)):
+            sim.enqueue_phase(ph)
+            e[ph + 1].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    sim.sync()
+    per_phase = {p: [] for p in PHASES}
+    total = 0.0
+    for e in evs:
+        total += e[0].elapsed_time(e[-1])
+        for i, p in enumerate(PHASES):
+            per_phase[p].append(e[i].elapsed_time(e[i + 1]))
+    return total, per_phase
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    from paper_1911_03225_gb300 import FDM
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n, K, W = args.n, args.steps, args.warmup
+    cells = n * n
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    hbm_peak, peak_src = read_peaks()
+    up0 = workload_input(n, seed=rank)
+
+    results = {}
+    for prec in ([args.precision] if args.precision != "both" else ["fp64", "mixed"]):
+        p = workload_params(n, prec)
+        sim = FDM(p, stream=stream.cuda_stream)
+        sim.set_plastic_distortion(up0)
+        for _ in range(W):
+            flush.zero_()
+            sim.enqueue_steps(1)
+        sim.sync()
+        barrier(world)
+        with ClockSampler(local) as clk:
+            barrier(world)
+            total_ms, per_phase = time_device(sim, K, flush, stream)
+            barrier(world)
+        info = sim.info()
+        t_max = max_over_ranks(total_ms, world)
+        elt = 8 if prec == "fp64" else 4
+        phase_mean = {ph: sum(v) / len(v) for ph, v in per_phase.items()}
+        dom = max(phase_mean, key=phase_mean.get)
+        bpc = bytes_per_cell(elt)
+        results[prec] = {"total_ms": t_max, "phase_ms": phase_mean, "dominant": dom,
+                         "clocks": clk.summary(), "info": info, "bpc": bpc, "sim": sim}
+
+    primary = args.precision if args.precision != "both" else "fp64"
+    r = results[primary]
+    value = cells * K * world / (r["total_ms"] / 1e3)
+    dom = r["dominant"]
+    elt = 8 if primary == "fp64" else 4
+    dom_ms = r["phase_ms"][dom]
+    if dom == "knp_step" and primary == "fp64":
+        roof = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (dom_ms / 1e3) / 1e9,
+                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; FMA-chain probe 1.20)"}
+    else:
+        roof = {"bound": "hbm", "achieved": r["bpc"][dom] * cells / (dom_ms / 1e3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["hbm_frac_of_step"] = (sum(r["bpc"].values()) * cells / (r["total_ms"] / K / 1e3) / 1e9) / hbm_peak
+
+    # end to end through the public API with host buffers (rank-local)
+    sim = r["sim"]
+    up_host = up0.copy()
+    barrier(world)
+    t0 = time.perf_counter()
+    sim.set_plastic_distortion(up_host)
+    for _ in range(K):
+        sim.step(1, info=True)
+    out = sim.read_fields("up13")
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, world)
+    e2e = {"value": cells * K * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": cells * 8 / K, "d2h_bytes_per_step": 104 + cells * 8 / K,
+           "note": "per step: fdm_step(1) with the step's scalars read back; the initial U13 upload and "
+                   "final U13 download are amortised over the K steps"}
+    assert np.isfinite(out["up13"]).all()
+
+    extra = {}
+    for prec, rr in results.items():
+        extra[prec] = {"value": cells * K * world / (rr["total_ms"] / 1e3),
+                       "ms_per_step": rr["total_ms"] / K,
+                       "phase_ms": {k: round(v, 5) for k, v in rr["phase_ms"].items()},
+                       "t_end": rr["info"].t, "clocks": rr["clocks"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": r["total_ms"] / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if primary == "fp64" else "f32 (FP64 scalars)",
+            "data": "synthetic (seeded random U13 field; no dataset in the paper)",
+            "config": {"workload": "coupled FDM under loading, %dx%d periodic layer, random field l=16 "
+                                   "RMS|alpha|=0.1, M=1, E=1, nu=0.3, strain ramp 1e-4/step, CFL 0.4, "
+                                   "minmod" % (n, n),
+                       "n": n, "precision": primary, "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "clocks": r["clocks"],
+            "e2e": e2e,
+            "gpu_launches": len(PHASES) * K,
+            "precisions": extra,
+        }
+        if args.cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    for rr in results.values():
+        rr["sim"].close()
+
+
+def cpu_baseline(seconds):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload:
+    the same coupled configuration on a 512 x 512 grid (layer kernel precompute excluded),
+    stepped until about `seconds` of CPU time has passed."""
+    import oracle
+    n = 512
+    p = workload_params(n, "fp64")
+    op = oracle.Params(**{k: getattr(p, k) for k in oracle.Params.__dataclass_fields__})
+    K = oracle.kernel_table(n, n, n, p.nh, p.E / (2 * (1 + p.nu)), p.nu)
+    up = workload_input(n, seed=0)
+    st = oracle.State(up13=up.copy())
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds or steps < 2:
+        st, rc = oracle.run(op, None, 1, K=K, state=st)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "coupled random-field workload on a %dx%d grid, %d steps (%.1f s), single thread, "
+                      "layer-kernel precompute excluded" % (n, n, steps, dt)}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle (the paper publishes no code or timings)."""
+    if rank != 0:
+        return
+    import oracle
+    n = 512
+    p = workload_params(n, "fp64")
+    op = oracle.Params(**{k: getattr(p, k) for k in oracle.Params.__dataclass_fields__})
+    K = oracle.kernel_table(n, n, n, p.nh, p.E / (2 * (1 + p.nu)), p.nu)
+    st = oracle.State(up13=workload_input(n, seed=0))
+    for _ in range(args.warmup):
+        st, _ = oracle.run(op, None, 1, K=K, state=st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = oracle.run(op, None, 1, K=K, state=st)
+    dt = time.perf_counter() - t0
+    v = n * n * args.steps / dt
+    sample = ("coupled random-field workload on a %dx%d grid (bounded sample of the %dx%d workload), "
+              "single thread, layer-kernel precompute excluded" % (n, n, args.n, args.n))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "coupled FDM under loading (oracle sample)", "n": n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * fdm.h -- C ABI of the GB300 (sm_103a) library for the field-dislocation-mechanics
+ * layer-case time step of Morin, Brenner & Suquet (arXiv 1911.03225).
+ *
+ * Problem (Sec. 2.1 and Sec. 3.2.1): for a periodic plastic distortion
+ * U^p = U13(x1,x2) e1 (x) e3 confined to a thin layer, find the layer-averaged shear
+ * stress tau13 (static problem, Sec. 3.1.2) and advance U13 by the transport equation
+ * dU13/dt + v0 |grad U13| = 0 (Sec. 3.2.3), with v0 = M (tau_y cos(U13/beta) - tau13)
+ * (stress driven) or a prescribed uniform v0 (Sec. 4.1).  The Nye tensor of the layer is
+ * alpha = alpha11 e1(x)e1 + alpha12 e1(x)e2 with alpha11 = -dU13/dx2, alpha12 = dU13/dx1.
+ * Each step (Sec. 3.1.1): static solve with U13^n, then the Kurganov-Noelle-Petrova
+ * central-upwind update (Sec. 3.2.2-3.2.3) with a CFL-bounded time step.
+ *
+ * Units are the dimensionless ones of Sec. 3.2.1 (lengths / b, stresses / mu, ...).
+ *
+ * Conventions for every call:
+ *   - Host arrays are caller-owned, row-major [n2][n1] float64 (x1 fastest); they are
+ *     copied in or out before the call returns.  The handle owns all device memory.
+ *   - Every call returns an fdm_status and never aborts the process.  A NULL handle or
+ *     pointer where one is required gives FDM_ERR_INVALID_ARG.
+ *   - Calls on one handle are not thread-safe; distinct handles are independent.
+ *   - Work is enqueued on the stream given to fdm_create (NULL = the legacy default
+ *     stream); calls that return host data synchronise that stream.
+ */
+#ifndef FDM_GB300_H
+#define FDM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdm_handle fdm_handle;
+
+typedef enum {
+    FDM_OK = 0,
+    FDM_ERR_INVALID_ARG = 1,    /* bad parameter, size or pointer                           */
+    FDM_ERR_OOM = 2,            /* device allocation failed                                  */
+    FDM_ERR_NET_BURGERS = 3,    /* alpha has a non-zero mean (net Burgers vector, Sec. 4.2);
+                                   a periodic U13 cannot represent it; state unchanged       */
+    FDM_WARN_NOT_DIV_FREE = 4,  /* div alpha != 0 beyond tolerance (Sec. 2.1); the state was
+                                   set from the divergence-free part (warning only)           */
+    FDM_ERR_NONFINITE = 5,      /* a non-finite time step or field appeared                  */
+    FDM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up                         */
+    FDM_ERR_DEVICE = 7,         /* a CUDA call failed                                        */
+    FDM_ERR_STATE = 8           /* call out of order (e.g. fdm_step before any fdm_set_*)    */
+} fdm_status;
+
+enum { FDM_V_PRESCRIBED = 0, FDM_V_STRESS = 1 };
+enum { FDM_LOAD_STRESS = 0, FDM_LOAD_STRAIN_RAMP = 1, FDM_LOAD_ZERO_MEAN_STRESS = 2 };
+enum { FDM_FP64 = 0, FDM_MIXED = 1 };
+enum { FDM_T_MIDPOINT = 0, FDM_T_LITERAL = 1 };
+
+/* Problem parameters (dimensionless, Sec. 3.2.1). */
+typedef struct {
+    int32_t n1, n2;          /* in-plane grid, each a power of two in [16, 4096]             */
+    int32_t nz, nh;          /* depth of the 3-D periodic cell and of the layer in voxels;
+                                nz = 0 means nz = n1 (cubic cell); 1 <= nh <= nz (Sec. 5.1)   */
+    double dx;               /* cell size (> 0)                                              */
+    double E, nu;            /* isotropic elasticity, mu = E / (2 (1 + nu)), -1 < nu < 0.5    */
+    int32_t velocity_mode;   /* FDM_V_PRESCRIBED (Sec. 4.1) or FDM_V_STRESS (Sec. 3.2.3)      */
+    double v0;               /* prescribed celerity                                          */
+    double mobility;         /* M = 1 / eta~ (Sec. 3.2.1)                                    */
+    double tau_y, beta;      /* lattice-friction amplitude and period of G (Sec. 3.2.1);
+                                tau_y = 0 disables the term.  Meaningful in FDM_FP64 only.   */
+    double theta;            /* minmod limiter parameter in [1, 2] (Sec. 3.2.2)               */
+    double cfl;              /* |v0|max dt / dx (Sec. 4.3, Sec. 5.2), in (0, 1]               */
+    double dt_max;           /* upper bound on dt (<= 0: none); dt when every v0 is 0         */
+    int32_t loading_mode;    /* FDM_LOAD_* (Sec. 3.1.2 sigma-hat(0); Sec. 5.1)                 */
+    double sigma_bar13;      /* FDM_LOAD_STRESS: macroscopic stress                          */
+    double eps_bar13_0;      /* FDM_LOAD_STRAIN_RAMP: eps_bar13 = eps_bar13_0 + rate * step   */
+    double eps_bar13_rate;
+    int32_t time_level;      /* FDM_T_MIDPOINT (default) or FDM_T_LITERAL (Sec. 3.2.2 Step 3) */
+    int32_t precision;       /* FDM_FP64, or FDM_MIXED: FP32 fields/FFT/stencil with the mean
+                                plastic slip, loading, dt and conserved sums in FP64          */
+} fdm_params;
+
+/* Scalars after the last step of a call.  The sums are over all nodes of the staggered
+ * Nye components a12 = (U_{j+1,k} - U_{jk})/dx, a11 = -(U_{j,k+1} - U_{jk})/dx; the total
+ * Burgers vector per unit length is dx^2 (sum_pos + sum_neg) of each (Sec. 4.2). */
+typedef struct {
+    int64_t step;            /* steps taken since the last fdm_set_*                           */
+    double t;                /* dimensionless time                                             */
+    double dt;               /* last time step                                                 */
+    double max_abs_v0;       /* max |v0| of the last step                                      */
+    double mean_up13;        /* <U13> over the layer after the last step                      */
+    double eps_bar13;        /* macroscopic strain for the next step                          */
+    double sigma_bar13;      /* macroscopic stress for the next step                          */
+    double sum_a12_pos, sum_a12_neg, sum_a11_pos, sum_a11_neg, sum_abs_alpha;
+    int32_t status;          /* fdm_status of the device-side checks                           */
+} fdm_step_info;
+
+enum {
+    FDM_FIELD_UP13 = 1,      /* U13                                                          */
+    FDM_FIELD_ALPHA11 = 2,   /* alpha11 = -dU13/dx2, spectral derivative                     */
+    FDM_FIELD_ALPHA12 = 4,   /* alpha12 =  dU13/dx1, spectral derivative                     */
+    FDM_FIELD_TAU13 = 8,     /* layer-averaged stress of the last static solve                */
+    FDM_FIELD_V1 = 16,       /* V = v0 (alpha12, -alpha11) / |alpha| (Sec. 4.1), 0 where     */
+    FDM_FIELD_V2 = 32        /*   |alpha| = 0                                                */
+};
+
+/* Fills p with the defaults: nz = 0, nh = 4, dx = 1, E = 1, nu = 0.3, prescribed v0 = 1,
+ * M = 1, tau_y = 0, beta = 1, theta = 1, cfl = 0.5, dt_max = 0, stress loading 0,
+ * midpoint time level, FP64.  n1 = n2 = 0 (must be set). */
+void fdm_default_params(fdm_params *p);
+
+/* Bytes of device memory a handle with these parameters holds (0 if invalid). */
+size_t fdm_device_bytes(const fdm_params *p);
+
+/* Validates p, allocates device memory, builds the twiddle tables and the layer Green
+ * kernel K(xi1,xi2) of Sec. 3.1.2/3.2.1.  stream: a cudaStream_t or NULL.  On success
+ * *out is a new handle; on failure *out is NULL and nothing is leaked. */
+fdm_status fdm_create(const fdm_params *p, void *stream, fdm_handle **out);
+
+/* Sets the state from a Nye field (Sec. 2.2, Poisson problem for U^p_0; Sec. 3.1.2,
+ * U^p-hat = i (alpha-hat x xi)/|xi|^2): U13-hat = i (a11-hat xi2 - a12-hat xi1)/|xi|^2,
+ * <U13> = mean_up13.  alpha11, alpha12: host [n2][n1].  Returns FDM_ERR_NET_BURGERS if
+ * |<alpha>| > 1e-9 max|alpha| (state unchanged), FDM_WARN_NOT_DIV_FREE if the relative
+ * divergence residual exceeds 1e-6 (state set from the divergence-free part).  If
+ * div_residual is not NULL it receives the residual
+ * |xi1 a11-hat + xi2 a12-hat| / (|xi| |alpha-hat|) (l2 over the spectrum). Resets step/t. */
+fdm_status fdm_set_density(fdm_handle *h, const double *alpha11, const double *alpha12,
+                           double mean_up13, double *div_residual);
+
+/* Sets U13 directly (host [n2][n1]); resets step and t to 0.  Used for restarts. */
+fdm_status fdm_set_plastic_distortion(fdm_handle *h, const double *up13);
+
+/* Overrides the step counter and time (restart of a run written out earlier). */
+fdm_status fdm_set_clock(fdm_handle *h, int64_t step, double t);
+
+/* Static problem only (Sec. 3.1.2): tau13 for the current U13 and loading; readable with
+ * FDM_FIELD_TAU13 afterwards. */
+fdm_status fdm_static_solve(fdm_handle *h);
+
+/* Advances nsteps >= 0 steps (Sec. 3.1.1).  If info is not NULL it receives the scalars of
+ * the last step (this adds one small reduction and a device-to-host copy).  Returns the
+ * first device-side error seen (FDM_ERR_NONFINITE) or FDM_OK. */
+fdm_status fdm_step(fdm_handle *h, int32_t nsteps, fdm_step_info *info);
+
+/* Enqueues nsteps >= 0 steps on the handle's stream and returns without waiting.
+ * Device-side errors surface at the next synchronising call (fdm_sync, fdm_step,
+ * fdm_get_info).  Requires that no partial step is pending (see fdm_enqueue_phase). */
+fdm_status fdm_enqueue_steps(fdm_handle *h, int32_t nsteps);
+
+/* Enqueues one kernel ("phase") of a step without waiting, so that a caller can bracket
+ * each kernel with its own stream events.  Phases of a step are 0 .. k-1 with
+ * k = fdm_kernels_per_step(h) and must be issued in that order: 0 row transforms of U13,
+ * 1 spectral column pass with the Green kernel, 2 inverse row transforms giving tau13 and
+ * max |v0|, 3 transport update (which completes the step).  FDM_ERR_STATE on a phase out
+ * of order. */
+fdm_status fdm_enqueue_phase(fdm_handle *h, int32_t phase);
+
+/* Waits for the handle's stream; returns the first device-side error (or FDM_OK). */
+fdm_status fdm_sync(fdm_handle *h);
+
+/* Copies the requested fields (mask of FDM_FIELD_*) to host arrays [n2][n1]; pointers of
+ * fields not in the mask may be NULL.  Synchronises the handle's stream. */
+fdm_status fdm_read_fields(fdm_handle *h, uint32_t mask, double *up13, double *alpha11,
+                           double *alpha12, double *tau13, double *v1, double *v2);
+
+/* Scalars of the current state (same content as fdm_step's info). */
+fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
+
+/* Number of kernel launches one step issues (for launch accounting). */
+int32_t fdm_kernels_per_step(const fdm_handle *h);
+
+/* Frees everything; NULL-safe. */
+void fdm_destroy(fdm_handle *h);
+
+/* Static description of a status code. */
+const char *fdm_status_str(fdm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDM_GB300_H */

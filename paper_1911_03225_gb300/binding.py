@@ -1,0 +1,290 @@
+"""Thin ctypes binding of the C ABI in ``include/fdm.h`` (argument marshalling only).
+
+Every step of the FDM time loop runs in the CUDA library ``libfdm_gb300.so``; this module
+converts numpy arrays and parameters, and turns status codes into exceptions.  There is no
+CPU fallback: if the library is missing or cannot be loaded, ``load()`` raises.
+"""
+import ctypes as C
+import os
+import warnings
+from dataclasses import dataclass, asdict, field
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdm_gb300.so")
+
+FDM_OK = 0
+FDM_ERR_INVALID_ARG = 1
+FDM_ERR_OOM = 2
+FDM_ERR_NET_BURGERS = 3
+FDM_WARN_NOT_DIV_FREE = 4
+FDM_ERR_NONFINITE = 5
+FDM_ERR_TIMEOUT = 6
+FDM_ERR_DEVICE = 7
+FDM_ERR_STATE = 8
+
+V_PRESCRIBED, V_STRESS = 0, 1
+LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS = 0, 1, 2
+FP64, MIXED = 0, 1
+T_MIDPOINT, T_LITERAL = 0, 1
+
+FIELD_UP13, FIELD_ALPHA11, FIELD_ALPHA12, FIELD_TAU13, FIELD_V1, FIELD_V2 = 1, 2, 4, 8, 16, 32
+FIELDS = {"up13": FIELD_UP13, "alpha11": FIELD_ALPHA11, "alpha12": FIELD_ALPHA12,
+          "tau13": FIELD_TAU13, "v1": FIELD_V1, "v2": FIELD_V2}
+
+# every entry point declared in include/fdm.h
+EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_density",
+           "fdm_set_plastic_distortion", "fdm_set_clock", "fdm_static_solve", "fdm_step",
+           "fdm_read_fields", "fdm_get_info", "fdm_kernels_per_step", "fdm_destroy",
+           "fdm_status_str", "fdm_enqueue_steps", "fdm_enqueue_phase", "fdm_sync"]
+
+
+class CParams(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("nz", C.c_int32), ("nh", C.c_int32),
+                ("dx", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("velocity_mode", C.c_int32),
+                ("v0", C.c_double), ("mobility", C.c_double), ("tau_y", C.c_double),
+                ("beta", C.c_double), ("theta", C.c_double), ("cfl", C.c_double),
+                ("dt_max", C.c_double),
+                ("loading_mode", C.c_int32),
+                ("sigma_bar13", C.c_double), ("eps_bar13_0", C.c_double),
+                ("eps_bar13_rate", C.c_double),
+                ("time_level", C.c_int32), ("precision", C.c_int32)]
+
+
+class CStepInfo(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double),
+                ("max_abs_v0", C.c_double), ("mean_up13", C.c_double),
+                ("eps_bar13", C.c_double), ("sigma_bar13", C.c_double),
+                ("sum_a12_pos", C.c_double), ("sum_a12_neg", C.c_double),
+                ("sum_a11_pos", C.c_double), ("sum_a11_neg", C.c_double),
+                ("sum_abs_alpha", C.c_double), ("status", C.c_int32)]
+
+
+@dataclass
+class Params:
+    """Mirror of ``fdm_params`` (dimensionless units of Sec. 3.2.1)."""
+    n1: int
+    n2: int
+    nz: int = 0
+    nh: int = 4
+    dx: float = 1.0
+    E: float = 1.0
+    nu: float = 0.3
+    velocity_mode: int = V_PRESCRIBED
+    v0: float = 1.0
+    mobility: float = 1.0
+    tau_y: float = 0.0
+    beta: float = 1.0
+    theta: float = 1.0
+    cfl: float = 0.5
+    dt_max: float = 0.0
+    loading_mode: int = LOAD_STRESS
+    sigma_bar13: float = 0.0
+    eps_bar13_0: float = 0.0
+    eps_bar13_rate: float = 0.0
+    time_level: int = T_MIDPOINT
+    precision: int = FP64
+
+    def to_c(self) -> CParams:
+        return CParams(**asdict(self))
+
+
+@dataclass
+class StepInfo:
+    step: int
+    t: float
+    dt: float
+    max_abs_v0: float
+    mean_up13: float
+    eps_bar13: float
+    sigma_bar13: float
+    sum_a12_pos: float
+    sum_a12_neg: float
+    sum_a11_pos: float
+    sum_a11_neg: float
+    sum_abs_alpha: float
+    status: int
+
+
+class FDMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_str(status), status))
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfdm_gb300.so is not built; run paper_1911_03225_gb300/build.py "
+                          "(or __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    d = C.POINTER(C.c_double)
+    H = C.c_void_p
+    lib.fdm_default_params.argtypes = [C.POINTER(CParams)]
+    lib.fdm_default_params.restype = None
+    lib.fdm_device_bytes.argtypes = [C.POINTER(CParams)]
+    lib.fdm_device_bytes.restype = C.c_size_t
+    lib.fdm_create.argtypes = [C.POINTER(CParams), C.c_void_p, C.POINTER(H)]
+    lib.fdm_set_density.argtypes = [H, d, d, C.c_double, d]
+    lib.fdm_set_plastic_distortion.argtypes = [H, d]
+    lib.fdm_set_clock.argtypes = [H, C.c_int64, C.c_double]
+    lib.fdm_static_solve.argtypes = [H]
+    lib.fdm_step.argtypes = [H, C.c_int32, C.POINTER(CStepInfo)]
+    lib.fdm_read_fields.argtypes = [H, C.c_uint32, d, d, d, d, d, d]
+    lib.fdm_enqueue_steps.argtypes = [H, C.c_int32]
+    lib.fdm_enqueue_phase.argtypes = [H, C.c_int32]
+    lib.fdm_sync.argtypes = [H]
+    lib.fdm_get_info.argtypes = [H, C.POINTER(CStepInfo)]
+    lib.fdm_kernels_per_step.argtypes = [H]
+    lib.fdm_kernels_per_step.restype = C.c_int32
+    lib.fdm_destroy.argtypes = [H]
+    lib.fdm_destroy.restype = None
+    lib.fdm_status_str.argtypes = [C.c_int]
+    lib.fdm_status_str.restype = C.c_char_p
+    for name in ("fdm_create", "fdm_set_density", "fdm_set_plastic_distortion", "fdm_set_clock",
+                 "fdm_static_solve", "fdm_step", "fdm_read_fields", "fdm_get_info",
+                 "fdm_enqueue_steps", "fdm_enqueue_phase", "fdm_sync"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    return load().fdm_status_str(int(s)).decode()
+
+
+def default_params(n1: int, n2: int) -> Params:
+    cp = CParams()
+    load().fdm_default_params(C.byref(cp))
+    d = {f: getattr(cp, f) for f, _ in CParams._fields_}
+    d["n1"], d["n2"] = n1, n2
+    return Params(**d)
+
+
+def device_bytes(p: Params) -> int:
+    return int(load().fdm_device_bytes(C.byref(p.to_c())))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _field(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError("expected array of shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _check(st, what):
+    if st != FDM_OK:
+        raise FDMError(st, what)
+
+
+class FDM:
+    """One FDM layer simulation resident on the GPU (handle of the C ABI)."""
+
+    def __init__(self, params: Params, stream: Optional[int] = None):
+        self.lib = load()
+        self.params = params
+        self.shape = (params.n2, params.n1)
+        h = C.c_void_p()
+        _check(self.lib.fdm_create(C.byref(params.to_c()), C.c_void_p(stream or 0), C.byref(h)), "fdm_create")
+        self.h = h
+
+    # -- state
+    def set_density(self, alpha11, alpha12, mean_up13: float = 0.0) -> float:
+        a11, a12 = _field(alpha11, self.shape), _field(alpha12, self.shape)
+        res = C.c_double(0.0)
+        st = self.lib.fdm_set_density(self.h, _dptr(a11), _dptr(a12), float(mean_up13), C.byref(res))
+        if st == FDM_WARN_NOT_DIV_FREE:
+            warnings.warn("Nye field is not divergence-free (residual %.3e); its divergence-free "
+                          "part was used" % res.value)
+        else:
+            _check(st, "fdm_set_density")
+        return res.value
+
+    def set_plastic_distortion(self, up13):
+        u = _field(up13, self.shape)
+        _check(self.lib.fdm_set_plastic_distortion(self.h, _dptr(u)), "fdm_set_plastic_distortion")
+
+    def set_clock(self, step: int, t: float):
+        _check(self.lib.fdm_set_clock(self.h, int(step), float(t)), "fdm_set_clock")
+
+    # -- compute
+    def static_solve(self):
+        _check(self.lib.fdm_static_solve(self.h), "fdm_static_solve")
+
+    def step(self, nsteps: int = 1, info: bool = True) -> Optional[StepInfo]:
+        if info:
+            ci = CStepInfo()
+            _check(self.lib.fdm_step(self.h, int(nsteps), C.byref(ci)), "fdm_step")
+            return StepInfo(**{f: getattr(ci, f) for f, _ in CStepInfo._fields_})
+        _check(self.lib.fdm_step(self.h, int(nsteps), None), "fdm_step")
+        return None
+
+    def enqueue_steps(self, nsteps: int = 1):
+        """Enqueue steps on the handle's stream without waiting."""
+        _check(self.lib.fdm_enqueue_steps(self.h, int(nsteps)), "fdm_enqueue_steps")
+
+    def enqueue_phase(self, phase: int):
+        """Enqueue kernel ``phase`` of the current step (phases run in order 0..k-1)."""
+        _check(self.lib.fdm_enqueue_phase(self.h, int(phase)), "fdm_enqueue_phase")
+
+    def sync(self):
+        """Wait for the stream; raise on a device-side error."""
+        _check(self.lib.fdm_sync(self.h), "fdm_sync")
+
+    def info(self) -> StepInfo:
+        ci = CStepInfo()
+        _check(self.lib.fdm_get_info(self.h, C.byref(ci)), "fdm_get_info")
+        return StepInfo(**{f: getattr(ci, f) for f, _ in CStepInfo._fields_})
+
+    def read_fields(self, *names, out=None):
+        """Returns {name: array [n2][n1] float64} for names in up13, alpha11, alpha12,
+        tau13, v1, v2 (``out`` may supply preallocated host arrays by name)."""
+        mask = 0
+        arrs = {}
+        ptrs = []
+        for nm in ("up13", "alpha11", "alpha12", "tau13", "v1", "v2"):
+            if nm in names:
+                mask |= FIELDS[nm]
+                a = out[nm] if out and nm in out else np.empty(self.shape, dtype=np.float64)
+                arrs[nm] = a
+                ptrs.append(_dptr(a))
+            else:
+                ptrs.append(None)
+        unknown = set(names) - set(FIELDS)
+        if unknown:
+            raise ValueError("unknown fields %s" % sorted(unknown))
+        _check(self.lib.fdm_read_fields(self.h, mask, *ptrs), "fdm_read_fields")
+        return arrs
+
+    def kernels_per_step(self) -> int:
+        return int(self.lib.fdm_kernels_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fdm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

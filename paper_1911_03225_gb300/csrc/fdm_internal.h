@@ -1,0 +1,65 @@
+// fdm_internal.h -- structures shared by the C-ABI layer and the kernels.
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "../../include/fdm.h"
+
+namespace fdm {
+
+// Per-handle scalars in device memory; every per-step quantity lives here so that a step
+// is a fixed launch sequence (capturable in a CUDA graph).
+struct fdm_dev_scalars {
+    unsigned long long vmax_bits;  // max |v0| of the current step, bits of a double >= 0
+    unsigned int done_count;       // blocks of the stencil kernel that have finished
+    int status;                    // fdm_status of device-side checks
+    long long step;                // steps since the last fdm_set_*
+    double t, dt, max_abs_v0;
+    double mean_up13, eps_bar13, sigma_bar13;  // state at the start of the current step
+    double phi_ref;                // mixed precision: U13 = phi_ref + stored value
+};
+
+struct LaunchGeom {
+    int R;             // rows per block of the row kernels
+    int C;             // spectral columns per block of the column kernel
+    size_t row_smem, col_smem;
+    int row_blocks, col_blocks;
+};
+
+struct Dev {
+    fdm_params p;          // validated copy (nz resolved)
+    LaunchGeom geom;
+    void* phi[2];          // double-buffered U13 (type T)
+    void* tau;             // T
+    void* spec;            // cpx<T> [n1/2][n2]
+    void* spec2;           // cpx<T> [n1/2][n2]
+    void* Kh;              // T [n1/2+1][n2/2+1]
+    void* tw1;             // cpx<T> [n1]
+    void* tw2;             // cpx<T> [n2]
+    double* row_partials;  // [row_blocks]
+    double* red;           // reduction partials [6 * red_blocks]
+    int red_blocks;
+    fdm_dev_scalars* sc;
+    double phi_ref_host;
+};
+
+template <typename T> LaunchGeom geometry(int n1, int n2);
+template <typename T> cudaError_t configure_kernels();
+template <typename T> void launch_step(const Dev& d, const T* phi, T* phi_next, cudaStream_t s);
+template <typename T> void launch_phase(const Dev& d, int phase, const T* phi, T* phi_next, cudaStream_t s);
+template <typename T> void launch_static(const Dev& d, const T* phi, cudaStream_t s);
+template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);
+template <typename T>
+void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,
+                         double* partials, int nblk, cudaStream_t s);
+template <typename T> void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t s);
+template <typename T> void launch_alpha_sums(const Dev& d, const T* phi, double* partials, int nblk, cudaStream_t s);
+template <typename T>
+void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
+                     cudaStream_t s);
+void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
+                         cudaStream_t s);
+
+constexpr int kKernelsPerStep = 4;
+
+}  // namespace fdm

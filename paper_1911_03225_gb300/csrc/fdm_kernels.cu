@@ -1,0 +1,667 @@
+// fdm_kernels.cu -- CUDA kernels (sm_103a) of the FDM layer-case time step
+// (arXiv 1911.03225, Sec. 3.1.1 splitting; Sec. 3.1.2 static problem by FFT;
+// Sec. 3.2.2-3.2.3 Kurganov-Noelle-Petrova transport).
+//
+// Data layout in HBM (x1 fastest):
+//   phi   [n2][n1]            U13 (FP64, or FP32 minus an FP64 reference in mixed mode)
+//   tau   [n2][n1]            layer-averaged shear stress of the last static solve
+//   spec  [n1/2][n2] complex  packed half spectrum, TRANSPOSED: column kx holds, for all
+//                             x2, the row transform's coefficient kx; kx = 0 packs
+//                             X(0) + i X(n1/2) (both real for a real row)
+//   Kh    [n1/2+1][n2/2+1]    layer Green kernel K(kx, |ky|) (even in both indices)
+//
+// One step = row_forward (R2C of every row, transposed store) -> col_pass (FFT along x2,
+// multiply by K, inverse FFT along x2) -> row_inverse (C2R, tau and max|v0|) -> knp_step.
+#include "fdm_device.cuh"
+#include "fdm_internal.h"
+
+namespace fdm {
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// block-wide sum, fixed order (deterministic); result valid in thread 0
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) for (int i = 0; i < nw; ++i) r += red[i];
+    __syncthreads();
+    return r;
+}
+// max of non-negative values, NaN-propagating through the bit order (NaN > +inf)
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+__device__ __forceinline__ void loading_state(const fdm_params& p, long long step, double mean,
+                                              double* eps, double* sig) {
+    const double mu = p.E / (2.0 * (1.0 + p.nu));
+    const double frac = (double)p.nh / (double)p.nz;
+    if (p.loading_mode == FDM_LOAD_STRESS) {
+        *sig = p.sigma_bar13;
+        *eps = (p.sigma_bar13 + mu * frac * mean) / (2.0 * mu);
+    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP) {
+        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (double)step;
+        *sig = 2.0 * mu * (*eps) - mu * frac * mean;
+    } else {
+        *eps = 0.5 * frac * mean;
+        *sig = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ row forward (R2C)
+// grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional per-block FP64 sum of
+// the loaded values (for <U13>).
+template <typename T>
+__global__ void __launch_bounds__(256) row_forward_kernel(const T* __restrict__ src, cpx<T>* __restrict__ spec,
+                                                          int n1, int n2, int R,
+                                                          const cpx<T>* __restrict__ tw1,
+                                                          double* __restrict__ row_partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = n1 >> 1;
+    const int ld = L + 1;  // padded sequence stride (bank spread for the transposed store)
+    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* B = A + (size_t)R * ld;
+    double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
+    const int y0 = blockIdx.x * R;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
+        int r = e / L, m = e - r * L;
+        const T* row = src + (size_t)(y0 + r) * n1;
+        T a = row[2 * m], b = row[2 * m + 1];
+        acc += (double)a + (double)b;
+        A[r * ld + m] = mk(a, b);
+    }
+    if (row_partials) {
+        double s = block_sum(acc, red);
+        if (threadIdx.x == 0) row_partials[blockIdx.x] = s;
+    }
+    __syncthreads();
+    cpx<T>* Z = smem_fft(A, B, L, R, ld, -1, tw1, n1);
+    cpx<T>* P = (Z == A) ? B : A;
+    const int half = L / 2 + 1;
+    for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
+        int r = e / half, k = e - r * half;
+        r2c_twist_pair(Z + r * ld, P + r * ld, L, k, tw1);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
+        int kx = e / R, r = e - kx * R;
+        spec[(size_t)kx * n2 + y0 + r] = P[r * ld + kx];
+    }
+}
+
+// ------------------------------------------------------------------ column pass
+// grid: (n1/2) / C blocks; block handles columns [b C, b C + C) of the transposed spectrum.
+// Multiplier modes (all include the 1/(n1 n2) normalisation):
+//   COL_K         tau-hat = K U-hat, DC = sigma_bar13 (block 0 computes <U13> and loading)
+//   COL_DERIV1    alpha12-hat = i xi1 U-hat  (odd symbol, 0 at the x1 Nyquist index)
+//   COL_DERIV2N   alpha11-hat = -i xi2 U-hat (odd symbol, 0 at the x2 Nyquist index)
+//   COL_FWD       forward transform only (no normalisation)
+//   COL_INV       inverse transform only
+enum ColMode { COL_K = 0, COL_DERIV1 = 1, COL_DERIV2N = 2, COL_FWD = 3, COL_INV = 4 };
+
+struct ColArgs {
+    fdm_params p;
+    int mode;
+    const double* row_partials;  // COL_K: per-row-block sums of U13 (nparts entries)
+    int nparts;
+    fdm_dev_scalars* sc;         // COL_K: scalars (block 0 writes mean/eps/sigma)
+    double dx;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> col_multiplier(const ColArgs& a, const T* __restrict__ Kh, int kxi,
+                                                 int ky, int n1, int n2) {
+    // kxi in [0, n1/2]; ky in [0, n2)
+    const T scl = T(1.0 / ((double)n1 * (double)n2));
+    if (a.mode == COL_K) {
+        int kyf = ky <= n2 / 2 ? ky : n2 - ky;
+        return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf] * scl, T(0));
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    if (a.mode == COL_DERIV1) {
+        if (2 * kxi == n1) return mk(T(0), T(0));
+        T xi1 = T(two_pi * (double)kxi / ((double)n1 * a.dx));
+        return mk(T(0), xi1 * scl);
+    }
+    // COL_DERIV2N
+    if (2 * ky == n2) return mk(T(0), T(0));
+    int kys = ky <= n2 / 2 ? ky : ky - n2;
+    T xi2 = T(two_pi * (double)kys / ((double)n2 * a.dx));
+    return mk(T(0), -xi2 * scl);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
+                                                       int n1, int n2, int C,
+                                                       const cpx<T>* __restrict__ tw2, const T* __restrict__ Kh,
+                                                       ColArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = n2;
+    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* B = A + (size_t)C * ld;
+    __shared__ double s_sigma;
+    const int kx0 = blockIdx.x * C;
+    const cpx<T>* src = in + (size_t)kx0 * n2;
+    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) A[e] = src[e];
+    if (a.mode == COL_K && kx0 == 0 && threadIdx.x == 0) {
+        // <U13> from the row-block sums (fixed order, compensated), then the loading state
+        double s = 0.0, c = 0.0;
+        for (int i = 0; a.row_partials && i < a.nparts; ++i) {
+            double x = a.row_partials[i], t = s + x;
+            c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+            s = t;
+        }
+        double mean = a.row_partials ? a.sc->phi_ref + (s + c) / ((double)n1 * (double)n2) : a.sc->mean_up13;
+        double eps, sig;
+        loading_state(a.p, a.sc->step, mean, &eps, &sig);
+        a.sc->mean_up13 = mean;
+        a.sc->eps_bar13 = eps;
+        a.sc->sigma_bar13 = sig;
+        s_sigma = sig;
+    }
+    __syncthreads();
+    cpx<T>* res = A;
+    if (a.mode != COL_INV) res = smem_fft(A, B, n2, C, ld, -1, tw2, n2);
+    cpx<T>* oth = (res == A) ? B : A;
+    if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N) {
+        for (int e = threadIdx.x; e < C * n2; e += blockDim.x) {
+            int c = e / n2, ky = e - c * n2;
+            int kx = kx0 + c;
+            cpx<T> z = res[c * ld + ky];
+            cpx<T> o;
+            if (kx > 0) {
+                o = cmul(col_multiplier<T>(a, Kh, kx, ky, n1, n2), z);
+            } else {
+                // packed column: z = C0 + i CN (C0, CN transforms of the real columns kx = 0
+                // and kx = n1/2); multiply each by its own symbol and repack:
+                // out = (m0 + mN)/2 z(ky) + (m0 - mN)/2 conj(z(-ky))
+                cpx<T> m0 = col_multiplier<T>(a, Kh, 0, ky, n1, n2);
+                cpx<T> mN = col_multiplier<T>(a, Kh, n1 / 2, ky, n1, n2);
+                cpx<T> zr = conj(res[c * ld + ((n2 - ky) & (n2 - 1))]);
+                o = cmul(scale(m0 + mN, T(0.5)), z) + cmul(scale(m0 - mN, T(0.5)), zr);
+                if (ky == 0 && a.mode == COL_K) o.x = T(s_sigma);  // macroscopic stress
+            }
+            oth[c * ld + ky] = o;
+        }
+        __syncthreads();
+        res = oth;
+        oth = (res == A) ? B : A;
+    }
+    if (a.mode != COL_FWD) res = smem_fft(res, oth, n2, C, ld, +1, tw2, n2);
+    cpx<T>* dst = out + (size_t)kx0 * n2;
+    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = res[e];
+}
+
+// ------------------------------------------------------------------ row inverse (C2R)
+// grid: n2 / R blocks.  mode ROW_PLAIN: write the real rows (+ offset).  ROW_TAU: write
+// tau13 and reduce max |v0| of the celerity law into sc->vmax_bits.
+enum RowMode { ROW_PLAIN = 0, ROW_TAU = 1 };
+
+struct RowArgs {
+    fdm_params p;
+    int mode;
+    const void* phi;           // ROW_TAU with tau_y != 0: current U13 (type T)
+    fdm_dev_scalars* sc;
+    double offset;             // ROW_PLAIN: added to every output value
+};
+
+template <typename T>
+__device__ __forceinline__ T celerity(const fdm_params& p, T tau, T up, double phi_ref) {
+    if (p.velocity_mode == FDM_V_PRESCRIBED) return T(p.v0);
+    T fr = T(0);
+    if (p.tau_y != 0.0) fr = T(p.tau_y * cos(((double)up + phi_ref) / p.beta));
+    return T(p.mobility) * (fr - tau);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) row_inverse_kernel(const cpx<T>* __restrict__ spec, T* __restrict__ dst,
+                                                          int n1, int n2, int R,
+                                                          const cpx<T>* __restrict__ tw1, RowArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = n1 >> 1;
+    const int ld = L + 1;
+    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* B = A + (size_t)R * ld;
+    double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
+    const int y0 = blockIdx.x * R;
+    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
+        int kx = e / R, r = e - kx * R;
+        B[r * ld + kx] = spec[(size_t)kx * n2 + y0 + r];
+    }
+    __syncthreads();
+    const int half = L / 2 + 1;
+    for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
+        int r = e / half, k = e - r * half;
+        c2r_twist_pair(B + r * ld, A + r * ld, L, k, tw1);
+    }
+    __syncthreads();
+    cpx<T>* z = smem_fft(A, B, L, R, ld, +1, tw1, n1);
+    double vmax = 0.0;
+    bool bad = false;
+    const T* up = reinterpret_cast<const T*>(a.phi);
+    const double phi_ref = a.sc ? a.sc->phi_ref : 0.0;
+    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
+        int r = e / L, m = e - r * L;
+        cpx<T> v = z[r * ld + m];
+        size_t o = (size_t)(y0 + r) * n1 + 2 * m;
+        if (a.mode == ROW_TAU) {
+            T u0 = T(0), u1 = T(0);
+            if (a.p.tau_y != 0.0 && a.p.velocity_mode == FDM_V_STRESS) { u0 = up[o]; u1 = up[o + 1]; }
+            T c0 = celerity(a.p, v.x, u0, phi_ref), c1 = celerity(a.p, v.y, u1, phi_ref);
+            vmax = fmax(vmax, fmax(fabs((double)c0), fabs((double)c1)));
+            bad |= (c0 != c0) || (c1 != c1);
+            dst[o] = v.x;
+            dst[o + 1] = v.y;
+        } else {
+            dst[o] = T((double)v.x + a.offset);
+            dst[o + 1] = T((double)v.y + a.offset);
+        }
+    }
+    if (a.mode == ROW_TAU) {
+        // NaN-aware block max through the bit pattern of |v|
+        unsigned long long bits = bad ? 0x7ff8000000000000ull : abs_bits(vmax);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = other > bits ? other : bits;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax(&a.sc->vmax_bits, bits);
+    }
+    (void)red;
+}
+
+// ------------------------------------------------------------------ KNP stencil
+constexpr int TX = 32, TY = 8;
+
+struct KnpArgs {
+    fdm_params p;
+    fdm_dev_scalars* sc;
+    double* blk_partials;  // unused slot for future fused reductions
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* __restrict__ phi, const T* __restrict__ tau,
+                                                           T* __restrict__ out, int n1, int n2, KnpArgs a) {
+    __shared__ T tile[TY + 4][TX + 4];
+    __shared__ unsigned int s_last;
+    const int tx = blockDim.x;  // TX, or n1 when n1 < TX
+    const int bx = blockIdx.x * tx, by = blockIdx.y * TY;
+    const int tid = threadIdx.y * tx + threadIdx.x;
+    for (int e = tid; e < (TY + 4) * (tx + 4); e += tx * TY) {
+        int ly = e / (tx + 4), lx = e - ly * (tx + 4);
+        int gx = (bx + lx - 2) & (n1 - 1), gy = (by + ly - 2) & (n2 - 1);
+        tile[ly][lx] = phi[(size_t)gy * n1 + gx];
+    }
+    __syncthreads();
+    fdm_dev_scalars* sc = a.sc;
+    const double vmax = __longlong_as_double((long long)sc->vmax_bits);
+    double dtd;
+    if (vmax > 0.0) {
+        dtd = a.p.cfl * a.p.dx / vmax;
+        if (a.p.dt_max > 0.0 && dtd > a.p.dt_max) dtd = a.p.dt_max;
+    } else {
+        dtd = a.p.dt_max > 0.0 ? a.p.dt_max : 0.0;
+    }
+    const int x = bx + threadIdx.x, y = by + threadIdx.y;
+    const int lx = threadIdx.x + 2, ly = threadIdx.y + 2;
+    const T up = tile[ly][lx];
+    const T v0 = celerity(a.p, tau[(size_t)y * n1 + x], up, sc->phi_ref);
+    auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
+    T nv = knp_node<T>(f, v0, T(dtd), T(a.p.dx), T(a.p.theta), a.p.time_level);
+    out[(size_t)y * n1 + x] = nv;
+    // last block to finish advances the clock (all blocks have read vmax by then)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        unsigned int total = gridDim.x * gridDim.y;
+        unsigned int prev = atomicAdd(&sc->done_count, 1u);
+        s_last = (prev == total - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+        __threadfence();
+        sc->step += 1;
+        sc->t += dtd;
+        sc->dt = dtd;
+        sc->max_abs_v0 = vmax;
+        if (!(dtd == dtd) || !(vmax == vmax) || isinf(dtd)) sc->status = FDM_ERR_NONFINITE;
+        sc->vmax_bits = 0ull;
+        sc->done_count = 0u;
+    }
+}
+
+// ------------------------------------------------------------------ set-up / readout helpers
+// Layer Green kernel (Sec. 3.1.2 + layer average, Sec. 3.2.1):
+// Kh[kx][ky] = (1/(nz nh)) sum_k3 m(xi) |chi-hat(k3)|^2, m = -mu (n2^2 + 2 n1^2 n3^2/(1-nu)).
+// w3[k3] = |chi-hat(k3)|^2 for k3 in [0, nz/2] (host table), even in k3.
+__global__ void kernel_table_kernel(double* __restrict__ Kh, int n1, int n2, int nz, int nh,
+                                    double mu, double nu, const double* __restrict__ w3) {
+    const int w = n2 / 2 + 1;
+    const int total = (n1 / 2 + 1) * w;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int kx = i / w, ky = i - kx * w;
+        double x1 = (double)kx / (double)n1, x2 = (double)ky / (double)n2;
+        double acc = 0.0;
+        for (int k3 = 0; k3 <= nz / 2; ++k3) {
+            double x3 = (double)k3 / (double)nz;
+            double r2 = x1 * x1 + x2 * x2 + x3 * x3;
+            if (r2 == 0.0) continue;
+            double ir2 = 1.0 / r2;
+            double m = -mu * (x2 * x2 * ir2 + 2.0 * (x1 * x1 * ir2) * (x3 * x3 * ir2) / (1.0 - nu));
+            double mult = (k3 == 0 || 2 * k3 == nz) ? 1.0 : 2.0;
+            acc += mult * m * w3[k3];
+        }
+        Kh[i] = acc / ((double)nz * (double)nh);
+    }
+}
+
+template <typename T>
+__global__ void convert_kernel(const double* __restrict__ a, T* __restrict__ b, size_t n, double offset) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = T(a[i] - offset);
+}
+
+// curl inverse on the forward 2-D spectra (transposed, packed) of alpha11 (sa) and alpha12
+// (sb): U-hat = i (a11-hat xi2 - a12-hat xi1)/|xi|^2 with odd uses zeroed at Nyquist (G8),
+// normalised by 1/(n1 n2); DC = mean_up13.  Also per-block partial sums for the divergence
+// residual |xi1 a11 + xi2 a12|^2 and |xi|^2 |alpha|^2 (Hermitian weights).
+struct CurlArgs { double dx, mean_up13; };
+
+__device__ __forceinline__ double xi_of(int k, int n, double dx) {
+    int ks = k <= n / 2 ? k : k - n;
+    return 6.283185307179586476925286766559 * (double)ks / ((double)n * dx);
+}
+
+template <typename T>
+__global__ void curl_inverse_kernel(const cpx<T>* __restrict__ sa, const cpx<T>* __restrict__ sb,
+                                    cpx<T>* __restrict__ out, int n1, int n2, CurlArgs c,
+                                    double* __restrict__ partials) {
+    __shared__ double red[32];
+    const int L = n1 / 2;
+    const size_t total = (size_t)L * n2;
+    const double scl = 1.0 / ((double)n1 * (double)n2);
+    double num = 0.0, den = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int kx = (int)(i / n2), ky = (int)(i - (size_t)kx * n2);
+        double xi2 = xi_of(ky, n2, c.dx), o2 = (2 * ky == n2) ? 0.0 : xi2;
+        cpx<T> za = sa[i], zb = sb[i];
+        if (kx > 0) {
+            double xi1 = xi_of(kx, n1, c.dx);
+            double ar = za.x, ai = za.y, br = zb.x, bi = zb.y;
+            double dr = xi1 * ar + o2 * br, di = xi1 * ai + o2 * bi;
+            num += 2.0 * (dr * dr + di * di);
+            den += 2.0 * (xi1 * xi1 + o2 * o2) * (ar * ar + ai * ai + br * br + bi * bi);
+            double q = xi1 * xi1 + xi2 * xi2;
+            // w = a11 xi2(odd) - a12 xi1 ; U = i w / q
+            double wr = ar * o2 - br * xi1, wi = ai * o2 - bi * xi1;
+            out[i] = mk(T(-wi / q * scl), T(wr / q * scl));
+        } else {
+            // unpack the two real columns kx = 0 and kx = n1/2 of each field
+            int kr = (n2 - ky) & (n2 - 1);
+            cpx<T> za_r = conj(sa[kr]), zb_r = conj(sb[kr]);
+            cpx<double> A0 = mk(0.5 * ((double)za.x + (double)za_r.x), 0.5 * ((double)za.y + (double)za_r.y));
+            cpx<double> AN = mk(0.5 * ((double)za.y - (double)za_r.y), -0.5 * ((double)za.x - (double)za_r.x));
+            cpx<double> B0 = mk(0.5 * ((double)zb.x + (double)zb_r.x), 0.5 * ((double)zb.y + (double)zb_r.y));
+            cpx<double> BN = mk(0.5 * ((double)zb.y - (double)zb_r.y), -0.5 * ((double)zb.x - (double)zb_r.x));
+            // kx = 0: xi1 = 0; kx = n1/2: xi1 odd-zeroed, even use keeps pi/dx
+            double xiN = 3.14159265358979323846 / c.dx;
+            {
+                double dr = o2 * B0.x, di = o2 * B0.y;
+                num += dr * dr + di * di;
+                den += o2 * o2 * (A0.x * A0.x + A0.y * A0.y + B0.x * B0.x + B0.y * B0.y);
+                dr = o2 * BN.x; di = o2 * BN.y;
+                num += dr * dr + di * di;
+                den += o2 * o2 * (AN.x * AN.x + AN.y * AN.y + BN.x * BN.x + BN.y * BN.y);
+            }
+            cpx<double> U0 = mk(0.0, 0.0), UN = mk(0.0, 0.0);
+            double q0 = xi2 * xi2, qN = xiN * xiN + xi2 * xi2;
+            if (q0 > 0.0) U0 = mk(-(A0.y * o2) / q0, (A0.x * o2) / q0);
+            UN = mk(-(AN.y * o2) / qN, (AN.x * o2) / qN);
+            // repack U0 + i UN
+            cpx<double> r = mk(U0.x - UN.y, U0.y + UN.x);
+            if (ky == 0) r = mk(c.mean_up13 / scl, 0.0);   // UN(0) = 0 (o2 = 0)
+            out[i] = mk(T(r.x * scl), T(r.y * scl));
+        }
+    }
+    double s1 = block_sum(num, red);
+    double s2 = block_sum(den, red);
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = s1; partials[2 * blockIdx.x + 1] = s2; }
+}
+
+// info: FP64 sums over the staggered Nye components of the current state
+template <typename T>
+__global__ void alpha_sums_kernel(const T* __restrict__ phi, int n1, int n2, double dx, double* __restrict__ partials) {
+    __shared__ double red[32];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    const size_t total = (size_t)n1 * n2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int y = (int)(i / n1), x = (int)(i - (size_t)y * n1);
+        double u = (double)phi[i];
+        double a12 = ((double)phi[(size_t)y * n1 + ((x + 1) & (n1 - 1))] - u) / dx;
+        double a11 = -((double)phi[(size_t)((y + 1) & (n2 - 1)) * n1 + x] - u) / dx;
+        s[0] += a12 > 0 ? a12 : 0.0;
+        s[1] += a12 < 0 ? a12 : 0.0;
+        s[2] += a11 > 0 ? a11 : 0.0;
+        s[3] += a11 < 0 ? a11 : 0.0;
+        s[4] += sqrt(a11 * a11 + a12 * a12);
+        s[5] += u;
+    }
+    for (int q = 0; q < 6; ++q) {
+        double r = block_sum(s[q], red);
+        if (threadIdx.x == 0) partials[6 * blockIdx.x + q] = r;
+    }
+}
+
+// velocity readout V = v0 (alpha12, -alpha11)/|alpha| (Sec. 4.1)
+template <typename T>
+__global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__ a12, const T* __restrict__ tau,
+                                const T* __restrict__ phi, T* __restrict__ v1, T* __restrict__ v2, size_t n,
+                                fdm_params p, double phi_ref) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T c = celerity(p, tau[i], phi[i], phi_ref);
+        T m = sqrt(a11[i] * a11[i] + a12[i] * a12[i]);
+        if (m > T(0)) { v1[i] = c * a12[i] / m; v2[i] = -c * a11[i] / m; }
+        else { v1[i] = T(0); v2[i] = T(0); }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static int pick_rows(int n1, int n2, size_t elt) {
+    // rows per block: as many as fit 48 KB per buffer, at most 16, at least 1
+    size_t per_row = (size_t)(n1 / 2 + 1) * 2 * elt;
+    int R = 1;
+    while (R < 16 && (size_t)(2 * R) * per_row <= 48 * 1024 && 2 * R <= n2) R *= 2;
+    return R;
+}
+static int pick_cols(int n1, int n2) {
+    int C = 1;
+    while (C * n2 < 1024 && 2 * C <= n1 / 2) C *= 2;
+    return C;
+}
+
+template <typename T>
+LaunchGeom geometry(int n1, int n2) {
+    LaunchGeom g;
+    g.R = pick_rows(n1, n2, sizeof(T));
+    g.C = pick_cols(n1, n2);
+    g.row_smem = (size_t)2 * g.R * (n1 / 2 + 1) * sizeof(cpx<T>) + 32 * sizeof(double);
+    g.col_smem = (size_t)2 * g.C * n2 * sizeof(cpx<T>);
+    g.row_blocks = n2 / g.R;
+    g.col_blocks = (n1 / 2) / g.C;
+    return g;
+}
+
+template <typename T>
+cudaError_t configure_kernels() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(row_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(row_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(col_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <typename T>
+void launch_row_forward(const Dev& d, const T* src, cpx<T>* spec, double* partials, cudaStream_t s) {
+    const LaunchGeom& g = d.geom;
+    row_forward_kernel<T><<<g.row_blocks, 256, g.row_smem, s>>>(src, spec, d.p.n1, d.p.n2, g.R,
+                                                                (const cpx<T>*)d.tw1, partials);
+}
+
+template <typename T>
+void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, cudaStream_t s) {
+    const LaunchGeom& g = d.geom;
+    ColArgs a;
+    a.p = d.p;
+    a.mode = mode;
+    a.row_partials = with_mean ? d.row_partials : nullptr;
+    a.nparts = g.row_blocks;
+    a.sc = d.sc;
+    a.dx = d.p.dx;
+    col_pass_kernel<T><<<g.col_blocks, 256, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
+                                                             (const cpx<T>*)d.tw2, (const T*)d.Kh, a);
+}
+
+template <typename T>
+void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, const T* phi, double offset,
+                        cudaStream_t s) {
+    const LaunchGeom& g = d.geom;
+    RowArgs a;
+    a.p = d.p;
+    a.mode = mode;
+    a.phi = phi;
+    a.sc = d.sc;
+    a.offset = offset;
+    row_inverse_kernel<T><<<g.row_blocks, 256, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
+                                                                (const cpx<T>*)d.tw1, a);
+}
+
+template <typename T>
+void launch_knp(const Dev& d, const T* phi, const T* tau, T* out, cudaStream_t s) {
+    KnpArgs a;
+    a.p = d.p;
+    a.sc = d.sc;
+    a.blk_partials = nullptr;
+    const int tx = d.p.n1 < TX ? d.p.n1 : TX;
+    dim3 grid(d.p.n1 / tx, d.p.n2 / TY), block(tx, TY);
+    knp_step_kernel<T><<<grid, block, 0, s>>>(phi, tau, out, d.p.n1, d.p.n2, a);
+}
+
+// one full step: static solve with U^n (Sec. 3.1.1) then transport
+template <typename T>
+void launch_phase(const Dev& d, int phase, const T* phi, T* phi_next, cudaStream_t s) {
+    cpx<T>* spec = (cpx<T>*)d.spec;
+    T* tau = (T*)d.tau;
+    switch (phase) {
+        case 0: launch_row_forward<T>(d, phi, spec, d.row_partials, s); break;
+        case 1: launch_col<T>(d, spec, spec, COL_K, true, s); break;
+        case 2: launch_row_inverse<T>(d, spec, tau, ROW_TAU, phi, 0.0, s); break;
+        default: launch_knp<T>(d, phi, tau, phi_next, s); break;
+    }
+}
+
+template <typename T>
+void launch_step(const Dev& d, const T* phi, T* phi_next, cudaStream_t s) {
+    for (int ph = 0; ph < kKernelsPerStep; ++ph) launch_phase<T>(d, ph, phi, phi_next, s);
+}
+
+// static solve only: tau for the current state (also refreshes max|v0| without stepping)
+template <typename T>
+void launch_static(const Dev& d, const T* phi, cudaStream_t s) {
+    cpx<T>* spec = (cpx<T>*)d.spec;
+    launch_row_forward<T>(d, phi, spec, d.row_partials, s);
+    launch_col<T>(d, spec, spec, COL_K, true, s);
+    launch_row_inverse<T>(d, spec, (T*)d.tau, ROW_TAU, phi, 0.0, s);
+}
+
+template <typename T>
+void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s) {
+    cpx<T>* spec = (cpx<T>*)d.spec;
+    cpx<T>* spec2 = (cpx<T>*)d.spec2;
+    launch_row_forward<T>(d, phi, spec, nullptr, s);
+    launch_col<T>(d, spec, spec2, COL_DERIV1, false, s);
+    launch_row_inverse<T>(d, spec2, a12, ROW_PLAIN, nullptr, 0.0, s);
+    launch_col<T>(d, spec, spec2, COL_DERIV2N, false, s);
+    launch_row_inverse<T>(d, spec2, a11, ROW_PLAIN, nullptr, 0.0, s);
+}
+
+template <typename T>
+void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,
+                         double* partials, int nblk, cudaStream_t s) {
+    cpx<T>* spec = (cpx<T>*)d.spec;
+    cpx<T>* spec2 = (cpx<T>*)d.spec2;
+    // a11 / a12 may be the state buffers; the result goes through tau (free here)
+    cpx<T>* tmp = (cpx<T>*)d.tau;
+    launch_row_forward<T>(d, a11, spec, nullptr, s);
+    launch_row_forward<T>(d, a12, spec2, nullptr, s);
+    launch_col<T>(d, spec, spec, COL_FWD, false, s);
+    launch_col<T>(d, spec2, spec2, COL_FWD, false, s);
+    CurlArgs c;
+    c.dx = d.p.dx;
+    c.mean_up13 = mean_up13 - phi_ref;
+    curl_inverse_kernel<T><<<nblk, 256, 0, s>>>(spec, spec2, tmp, d.p.n1, d.p.n2, c, partials);
+    launch_col<T>(d, tmp, spec, COL_INV, false, s);
+    launch_row_inverse<T>(d, spec, phi_out, ROW_PLAIN, nullptr, 0.0, s);
+}
+
+void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
+                         cudaStream_t s) {
+    int total = (n1 / 2 + 1) * (n2 / 2 + 1);
+    int blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    kernel_table_kernel<<<blocks, 256, 0, s>>>(Kh, n1, n2, nz, nh, mu, nu, w3);
+}
+
+template <typename T>
+void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    convert_kernel<T><<<blocks, 256, 0, s>>>(a, b, n, offset);
+}
+
+template <typename T>
+void launch_alpha_sums(const Dev& d, const T* phi, double* partials, int nblk, cudaStream_t s) {
+    alpha_sums_kernel<T><<<nblk, 256, 0, s>>>(phi, d.p.n1, d.p.n2, d.p.dx, partials);
+}
+
+template <typename T>
+void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
+                     cudaStream_t s) {
+    size_t n = (size_t)d.p.n1 * d.p.n2;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, d.p, d.phi_ref_host);
+}
+
+// explicit instantiations
+#define FDM_INST(T)                                                                                         \
+    template LaunchGeom geometry<T>(int, int);                                                              \
+    template cudaError_t configure_kernels<T>();                                                            \
+    template void launch_step<T>(const Dev&, const T*, T*, cudaStream_t);                                   \
+    template void launch_phase<T>(const Dev&, int, const T*, T*, cudaStream_t);                             \
+    template void launch_static<T>(const Dev&, const T*, cudaStream_t);                                     \
+    template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
+    template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
+                                         cudaStream_t);                                                     \
+    template void launch_convert<T>(const double*, T*, size_t, double, cudaStream_t);                       \
+    template void launch_alpha_sums<T>(const Dev&, const T*, double*, int, cudaStream_t);                   \
+    template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
+                                     cudaStream_t);
+FDM_INST(double)
+FDM_INST(float)
+
+}  // namespace fdm

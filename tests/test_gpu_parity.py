@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element
+on the same seeded inputs.  Tolerances: FP64 path 1e-11 relative L2; mixed precision
+(FP32 fields, FFT and stencil; FP64 scalars) 1e-5 relative L2 unless stated."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_03225_gb300 import FDM, FDMError, Params, inputs
+from paper_1911_03225_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def oparams(p: Params) -> oracle.Params:
+    d = {k: getattr(p, k) for k in oracle.Params.__dataclass_fields__}
+    return oracle.Params(**d)
+
+
+def run_both(p: Params, up0=None, alpha=None, mean=0.0, steps=10):
+    with FDM(p) as sim:
+        if alpha is not None:
+            sim.set_density(alpha[0], alpha[1], mean)
+            start = sim.read_fields("up13")["up13"]
+        else:
+            sim.set_plastic_distortion(up0)
+            start = up0
+        info = sim.step(steps)
+        got = sim.read_fields("up13", "tau13")
+    if alpha is not None:
+        up_o, _, _ = oracle.curl_inverse(alpha[0], alpha[1], mean, p.dx)
+    else:
+        up_o = up0
+    ref, rc = oracle.run(oparams(p), up_o, steps)
+    assert rc == 0
+    return got, info, ref, start
+
+
+# ------------------------------------------------------------------ static problem
+@pytest.mark.parametrize("shape", [(32, 64), (64, 64), (128, 32), (256, 256)])
+@pytest.mark.parametrize("nh", [1, 4])
+def test_static_solve_matches_oracle(shape, nh):
+    n2, n1 = shape
+    up = np.random.default_rng(n1 + n2).standard_normal(shape)
+    p = Params(n1=n1, n2=n2, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.013)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up)
+        sim.static_solve()
+        tau = sim.read_fields("tau13")["tau13"]
+    K = oracle.kernel_table(n1, n2, n1, nh, p.E / (2 * (1 + p.nu)), p.nu)
+    ref = oracle.static_tau(up, K, 0.013)
+    assert rel(tau, ref) < 1e-12
+
+
+def test_static_solve_strain_control_and_zero_alpha():
+    n = 64
+    up = np.full((n, n), 0.37)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_0=2e-3)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up)
+        sim.static_solve()
+        tau = sim.read_fields("tau13")["tau13"]
+    mu = 1 / 2.6
+    np.testing.assert_allclose(tau, 2 * mu * 2e-3 - mu * (4 / 64) * 0.37, rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------ curl inverse and readout
+@pytest.mark.parametrize("precision,tol", [(B.FP64, 1e-12), (B.MIXED, 1e-5)])
+def test_set_density_matches_oracle(precision, tol):
+    n = 128
+    a11, a12 = inputs.ring_alpha(n, r0=30.0, sigma=2.0)
+    p = Params(n1=n, n2=n, precision=precision)
+    with FDM(p) as sim:
+        res = sim.set_density(a11, a12, 0.25)
+        up = sim.read_fields("up13")["up13"]
+    ref, res_o, _ = oracle.curl_inverse(a11, a12, 0.25)
+    assert rel(up, ref) < tol
+    assert abs(res - res_o) < 1e-6
+
+
+def test_set_density_non_square_and_residual():
+    n1, n2 = 64, 32
+    u = np.random.default_rng(5).standard_normal((n2, n1))
+    a11, a12 = oracle.alpha_from_up(u)
+    # add a gradient (non-divergence-free) part
+    g1, g2 = np.gradient(np.random.default_rng(6).standard_normal((n2, n1)))
+    b11, b12 = a11 + g2 - g2.mean(), a12 + g1 - g1.mean()
+    with FDM(Params(n1=n1, n2=n2)) as sim:
+        with pytest.warns(UserWarning):
+            res = sim.set_density(b11, b12, -0.5)
+        up = sim.read_fields("up13")["up13"]
+    ref, res_o, _ = oracle.curl_inverse(b11, b12, -0.5)
+    assert rel(up, ref) < 1e-12
+    assert res == pytest.approx(res_o, rel=1e-9)
+
+
+def test_net_burgers_vector_rejected():
+    n = 32
+    a11 = np.full((n, n), 0.1)
+    with FDM(Params(n1=n, n2=n)) as sim:
+        with pytest.raises(FDMError) as e:
+            sim.set_density(a11, np.zeros((n, n)))
+        assert e.value.status == B.FDM_ERR_NET_BURGERS
+
+
+@pytest.mark.parametrize("precision,tol", [(B.FP64, 1e-12), (B.MIXED, 2e-5)])
+def test_alpha_and_velocity_readout(precision, tol):
+    n1, n2 = 128, 64
+    u = inputs.random_up(128, seed=2, ell=5.0)[:n2, :]
+    u = oracle.curl_inverse(*oracle.alpha_from_up(u))[0]   # periodic, band-limited
+    p = Params(n1=n1, n2=n2, velocity_mode=B.V_STRESS, precision=precision, mobility=1.5)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(u)
+        sim.static_solve()
+        f = sim.read_fields("alpha11", "alpha12", "v1", "v2", "tau13")
+    a11, a12 = oracle.alpha_from_up(u)
+    assert rel(f["alpha11"], a11) < tol and rel(f["alpha12"], a12) < tol
+    K = oracle.kernel_table(n1, n2, n1, 4, 1 / 2.6, 0.3)
+    v0 = -1.5 * oracle.static_tau(u, K, 0.0)
+    m = np.hypot(a11, a12)
+    assert rel(f["v1"], v0 * a12 / m) < 10 * tol and rel(f["v2"], -v0 * a11 / m) < 10 * tol
+
+
+# ------------------------------------------------------------------ time stepping
+def test_config0_lines_annihilation_fp64():
+    """128x128, two opposite edge walls 32 apart, v0 = +1, minmod, CFL 0.5, 200 steps,
+    static solve every step, E = 1, nu = 0.3, no load."""
+    n = 128
+    a11, a12 = inputs.lines_alpha(n)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_PRESCRIBED, v0=1.0, theta=1.0, cfl=0.5)
+    got, info, ref, start = run_both(p, alpha=(a11, a12), mean=0.0, steps=200)
+    assert rel(got["up13"], ref.up13) < TOL64
+    # the walls have annihilated by t = 100: tau13 is zero up to rounding, so compare it on
+    # the scale of the initial stress
+    K = oracle.kernel_table(n, n, n, 4, 1 / 2.6, 0.3)
+    scale = np.linalg.norm(oracle.static_tau(start, K, 0.0))
+    assert np.linalg.norm(got["tau13"] - ref.tau13) < TOL64 * scale
+    assert info.step == 200 and info.t == pytest.approx(ref.t, rel=1e-14)
+    assert info.dt == pytest.approx(0.5, rel=1e-15)
+    s = oracle.alpha_sums(ref.up13)
+    assert info.sum_abs_alpha == pytest.approx(s[4], rel=1e-11, abs=1e-12)
+    assert abs(info.sum_a12_pos + info.sum_a12_neg) < 1e-9   # total Burgers vector
+
+
+@pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.MIXED, TOL_MIXED)])
+def test_ring_expansion_short(precision, tol):
+    """Config-1 shape at reduced size: ring, MC limiter (theta = 2), CFL 0.4, v0 = -1."""
+    n = 256
+    a11, a12 = inputs.ring_alpha(n, r0=50.0, sigma=2.0)
+    p = Params(n1=n, n2=n, v0=-1.0, theta=2.0, cfl=0.4, precision=precision)
+    got, info, ref, _ = run_both(p, alpha=(a11, a12), mean=0.0, steps=8)
+    assert rel(got["up13"], ref.up13) < tol
+    assert rel(got["tau13"], ref.tau13) < tol
+
+
+@pytest.mark.parametrize("precision,eps", [(B.FP64, 1e-16), (B.MIXED, 6e-8)])
+def test_ring_expansion_long_within_rounding_envelope(precision, eps):
+    """With the MC limiter the scheme amplifies rounding differences (about 1e-16 -> 1e-11
+    in 10 steps, saturating near 1e-8): over 100 steps the GPU must stay within the
+    oracle's own spread under a perturbation of the size of the path's rounding."""
+    n, steps = 256, 100
+    a11, a12 = inputs.ring_alpha(n, r0=50.0, sigma=2.0)
+    p = Params(n1=n, n2=n, v0=-1.0, theta=2.0, cfl=0.4, precision=precision)
+    got, info, ref, _ = run_both(p, alpha=(a11, a12), mean=0.0, steps=steps)
+    up0, _, _ = oracle.curl_inverse(a11, a12, 0.0)
+    pert = up0 * (1 + eps * np.random.default_rng(0).standard_normal(up0.shape))
+    ref2, _ = oracle.run(oparams(p), pert, steps)
+    envelope = rel(ref2.up13, ref.up13)
+    assert rel(got["up13"], ref.up13) < 10 * envelope + 1e-14
+    # physics: the loop radius grows as r0 + t and the total Burgers vector stays zero
+    assert abs(info.sum_a12_pos + info.sum_a12_neg) < 1e-9 * info.sum_abs_alpha
+    assert info.t == pytest.approx(40.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(128, 128), (64, 256)])
+@pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.MIXED, TOL_MIXED)])
+def test_coupled_random_field(shape, precision, tol):
+    """Config-2 shape at reduced size: random field, stress-driven velocity M = 1, strain
+    ramp 1e-4 per step, CFL 0.4 adaptive, minmod."""
+    n2, n1 = shape
+    up0 = inputs.random_up(max(shape), seed=0, ell=16.0)[:n2, :n1]
+    up0 = up0 - up0.mean()
+    p = Params(n1=n1, n2=n2, velocity_mode=B.V_STRESS, mobility=1.0, loading_mode=B.LOAD_STRAIN_RAMP,
+               eps_bar13_rate=1e-4, cfl=0.4, theta=1.0, precision=precision)
+    got, info, ref, _ = run_both(p, up0=up0, steps=60)
+    assert rel(got["up13"], ref.up13) < tol
+    assert rel(got["tau13"], ref.tau13) < tol
+    assert info.t == pytest.approx(ref.t, rel=tol)
+    assert info.eps_bar13 == pytest.approx(ref.eps_bar13, rel=1e-15)
+    assert info.sigma_bar13 == pytest.approx(ref.sigma_bar13, rel=tol, abs=1e-14)
+    assert info.mean_up13 == pytest.approx(ref.mean_up13, rel=tol, abs=1e-13)
+
+
+@pytest.mark.parametrize("time_level", [B.T_MIDPOINT, B.T_LITERAL])
+@pytest.mark.parametrize("theta", [1.0, 1.5, 2.0])
+def test_scheme_variants(time_level, theta):
+    n = 64
+    up0 = inputs.random_up(n, seed=4, ell=5.0)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.02,
+               mobility=2.0, cfl=0.7, theta=theta, time_level=time_level)
+    got, _, ref, _ = run_both(p, up0=up0, steps=25)
+    assert rel(got["up13"], ref.up13) < TOL64
+
+
+def test_zero_mean_stress_and_friction():
+    n = 64
+    up0 = inputs.random_up(n, seed=8, ell=6.0) + 0.3
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_ZERO_MEAN_STRESS,
+               tau_y=0.01, beta=0.05, cfl=0.4, nh=2, nz=32)
+    got, info, ref, _ = run_both(p, up0=up0, steps=20)
+    assert rel(got["up13"], ref.up13) < TOL64
+    assert info.sigma_bar13 == 0.0
+    assert info.eps_bar13 == pytest.approx(ref.eps_bar13, rel=1e-12)
+
+
+def test_uniform_state_and_zero_steps():
+    n = 32
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, dt_max=0.5)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(np.full((n, n), 1.25))
+        i0 = sim.step(0)
+        assert i0.step == 0 and i0.t == 0.0
+        i = sim.step(3)
+        u = sim.read_fields("up13")["up13"]
+    assert (u == 1.25).all()
+    assert i.t == pytest.approx(1.5) and i.max_abs_v0 == 0.0
+
+
+def test_restart_equals_uninterrupted_run():
+    n = 64
+    up0 = inputs.random_up(n, seed=12, ell=6.0)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_rate=1e-3, cfl=0.4)
+    with FDM(p) as a:
+        a.set_plastic_distortion(up0)
+        i30 = a.step(30)
+        mid = a.read_fields("up13")["up13"]
+        i60 = a.step(30)
+        full = a.read_fields("up13")["up13"]
+    with FDM(p) as b:
+        b.set_plastic_distortion(mid)
+        b.set_clock(30, i30.t)   # the strain ramp is driven by the step counter
+        j60 = b.step(30)
+        again = b.read_fields("up13")["up13"]
+    np.testing.assert_array_equal(again, full)
+    assert j60.t == i60.t and j60.step == 60
+
+
+def test_step_before_state_is_an_error():
+    with FDM(Params(n1=32, n2=32)) as sim:
+        with pytest.raises(FDMError) as e:
+            sim.step(1)
+        assert e.value.status == B.FDM_ERR_STATE
+
+
+def test_nonfinite_state_reported():
+    n = 32
+    up = np.zeros((n, n))
+    up[3, 4] = 1e308
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up)
+        with pytest.raises(FDMError) as e:
+            sim.step(2)
+        assert e.value.status == B.FDM_ERR_NONFINITE
+
+
+def test_largest_grid_runs_and_conserves():
+    """Maximum size 4096^2 FP64: one coupled step; the total Burgers vector stays 0 and the
+    mean stress equals the macroscopic stress."""
+    n = 4096
+    up0 = inputs.random_up(n, seed=1, ell=16.0)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_rate=1e-4, cfl=0.4)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        info = sim.step(1)
+        f = sim.read_fields("tau13", "up13")
+    assert np.isfinite(f["tau13"]).all() and np.isfinite(f["up13"]).all()
+    assert abs(info.sum_a12_pos + info.sum_a12_neg) < 1e-8 * info.sum_abs_alpha
+    # the static solve of step 0 had sigma_bar13 = -mu (nh/nz) <U13^0>
+    sig0 = -(1 / 2.6) * (4 / n) * up0.mean()
+    assert abs(f["tau13"].mean() - sig0) < 1e-12 * np.abs(f["tau13"]).max()
