@@ -58,8 +58,8 @@ def bytes_per_cell(elt):
 
 
 # FP arithmetic per node of the KNP update (counted from knp_node in fdm_device.cuh:
-# +,-,*,min,max,compare = 1, fused multiply-add = 2, sqrt and divide = 1 each).
-KNP_FLOPS_PER_CELL = 330
+# +,-,*,min,max,compare = 1, multiply-add = 2, rsqrt and reciprocal = 1 each).
+KNP_FLOPS_PER_CELL = 380
 
 
 def read_peaks():

@@ -25,59 +25,97 @@ template <typename T> __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* __
     return sign < 0 ? w : conj(w);
 }
 
-// Batched Stockham autosort FFT in shared memory (Govindaraju et al., SC'08 formulation):
-// nseq sequences of length L (power of two, >= 2), sequence s at a[s * ld].  b is scratch
-// of the same shape.  Unnormalised; sign -1 forward, +1 inverse.  tw: table of length
-// tw_len (a multiple of L) of exp(-2 pi i m / tw_len).  Must be called by all threads of
-// the block.  Returns the buffer holding the result (a or b).
+// In-register DFT of R = 2, 4 or 8 points, sign -1 forward / +1 inverse, natural order.
+template <typename T, int R> struct Dft;
+template <typename T> struct Dft<T, 2> {
+    static __device__ __forceinline__ void run(cpx<T>* v, int) {
+        cpx<T> a = v[0], b = v[1];
+        v[0] = a + b; v[1] = a - b;
+    }
+};
+template <typename T> struct Dft<T, 4> {
+    static __device__ __forceinline__ void run(cpx<T>* v, int sign) {
+        cpx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_si(v[1] - v[3], sign);
+        v[0] = t0 + t2; v[1] = t1 + t3; v[2] = t0 - t2; v[3] = t1 - t3;
+    }
+};
+template <typename T> struct Dft<T, 8> {
+    // radix-2 decimation in frequency, three stages, bit-reversed result reordered
+    static __device__ __forceinline__ void run(cpx<T>* a, int s) {
+        const T r = T(0.70710678118654752440084436210485);
+        cpx<T> b0 = a[0] + a[4], b4 = a[0] - a[4];
+        cpx<T> b1 = a[1] + a[5], b5 = a[1] - a[5];
+        cpx<T> b2 = a[2] + a[6], b6 = a[2] - a[6];
+        cpx<T> b3 = a[3] + a[7], b7 = a[3] - a[7];
+        // b5 *= W8, b6 *= W8^2 = s i, b7 *= W8^3   (W8 = exp(s 2 pi i / 8))
+        b5 = mk(r * (b5.x - T(s) * b5.y), r * (b5.y + T(s) * b5.x));
+        b6 = mul_si(b6, s);
+        b7 = mk(r * (-b7.x - T(s) * b7.y), r * (-b7.y + T(s) * b7.x));
+        cpx<T> c0 = b0 + b2, c2 = b0 - b2, c1 = b1 + b3, c3 = mul_si(b1 - b3, s);
+        cpx<T> c4 = b4 + b6, c6 = b4 - b6, c5 = b5 + b7, c7 = mul_si(b5 - b7, s);
+        a[0] = c0 + c1; a[4] = c0 - c1;
+        a[2] = c2 + c3; a[6] = c2 - c3;
+        a[1] = c4 + c5; a[5] = c4 - c5;
+        a[3] = c6 + c7; a[7] = c6 - c7;
+    }
+};
+
+// One Stockham autosort pass of radix R (Govindaraju et al., SC'08 formulation) over nseq
+// sequences of length L: for j in [0, L/R), k = j mod Ns,
+//   v_r = in[j + r L/R] w^(r k),  w = exp(sign 2 pi i / (Ns R)),  v = DFT_R(v),
+//   out[(j - k) R + k + r Ns] = v_r.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_pass(const cpx<T>* in, cpx<T>* out, int L, int nseq, int ld, int Ns,
+                                              int sign, const cpx<T>* __restrict__ tw, int tw_len) {
+    const int q = L / R;
+    const int lq = 31 - __clz(q);  // q is a power of two: shifts instead of divisions
+    const int items = nseq * q;
+    const int stride = tw_len / (Ns * R);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int s = it >> lq, j = it & (q - 1);
+        const int k = j & (Ns - 1);
+        const cpx<T>* src = in + (size_t)s * ld;
+        cpx<T>* dst = out + (size_t)s * ld;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * q];
+        if (Ns > 1) {
+            const int m = k * stride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, r * m, sign));
+        }
+        Dft<T, R>::run(v, sign);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[d + r * Ns] = v[r];
+    }
+}
+
+// Batched FFT in shared memory: nseq sequences of length L (power of two, 2..8192),
+// sequence s at a[s * ld]; b is scratch of the same shape.  Unnormalised; sign -1 forward,
+// +1 inverse.  tw: table of length tw_len (a multiple of L) of exp(-2 pi i m / tw_len).
+// Radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor.  Must be
+// called by all threads of the block.  Returns the buffer holding the result (a or b).
 template <typename T>
 __device__ cpx<T>* smem_fft(cpx<T>* a, cpx<T>* b, int L, int nseq, int ld, int sign,
                             const cpx<T>* __restrict__ tw, int tw_len) {
     cpx<T>* in = a;
     cpx<T>* out = b;
-    int log2L = 31 - __clz(L);
     int Ns = 1;
-    if (log2L & 1) {  // one radix-2 pass (Ns = 1: no twiddles)
-        const int half = L >> 1;
-        const int items = nseq * half;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            int s = it / half, j = it - s * half;
-            const cpx<T>* src = in + (size_t)s * ld;
-            cpx<T>* dst = out + (size_t)s * ld;
-            cpx<T> v0 = src[j], v1 = src[j + half];
-            dst[2 * j] = v0 + v1;
-            dst[2 * j + 1] = v0 - v1;
-        }
+    while (Ns * 8 <= L) {
+        stockham_pass<T, 8>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
         __syncthreads();
         cpx<T>* t = in; in = out; out = t;
-        Ns = 2;
+        Ns *= 8;
     }
-    const int q = L >> 2;
-    while (Ns < L) {
-        const int items = nseq * q;
-        const int stride = tw_len / (4 * Ns);
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            int s = it / q, j = it - s * q;
-            int k = j & (Ns - 1);
-            const cpx<T>* src = in + (size_t)s * ld;
-            cpx<T>* dst = out + (size_t)s * ld;
-            cpx<T> v0 = src[j], v1 = src[j + q], v2 = src[j + 2 * q], v3 = src[j + 3 * q];
-            if (Ns > 1) {
-                int m = k * stride;
-                v1 = cmul(v1, twiddle(tw, m, sign));
-                v2 = cmul(v2, twiddle(tw, 2 * m, sign));
-                v3 = cmul(v3, twiddle(tw, 3 * m, sign));
-            }
-            cpx<T> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = mul_si(v1 - v3, sign);
-            int d = (j - k) * 4 + k;  // (j / Ns) * Ns * 4 + k
-            dst[d] = t0 + t2;
-            dst[d + Ns] = t1 + t3;
-            dst[d + 2 * Ns] = t0 - t2;
-            dst[d + 3 * Ns] = t1 - t3;
-        }
+    if (Ns * 4 == L) {
+        stockham_pass<T, 4>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
         __syncthreads();
         cpx<T>* t = in; in = out; out = t;
-        Ns <<= 2;
+    } else if (Ns * 2 == L) {
+        stockham_pass<T, 2>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
+        __syncthreads();
+        cpx<T>* t = in; in = out; out = t;
     }
     return in;
 }
@@ -120,12 +158,31 @@ __device__ __forceinline__ void c2r_twist_pair(const cpx<T>* P, cpx<T>* Z, int L
 }
 
 // ---------------------------------------------------------------------------------
+// Precision-typed math.  FP32 (mixed mode) keeps every operation on the FP32 pipes and
+// uses the approximate special-function unit; FP64 uses the FP64 library routines.
+// Nothing in a float instantiation may promote to double: the FP64 pipe of GB300 runs
+// at 1/64 of the FP32 rate.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+// 1/sqrt(x) for x > 0
+__device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+// 1/x for x != 0
+__device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+
+// ---------------------------------------------------------------------------------
 // Kurganov-Noelle-Petrova update of one node (Sec. 3.2.3 Steps 1-4; readings G1-G7).
 // f(i, j): value at node offset (i along x1, j along x2), i, j in [-2, 2].
 // ---------------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
-    if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
-    if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
+    if (a > T(0) && b > T(0) && c > T(0)) return tmin(a, tmin(b, c));
+    if (a < T(0) && b < T(0) && c < T(0)) return tmax(a, tmax(b, c));
     return T(0);
 }
 
@@ -151,25 +208,26 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_le
     // one-sided derivatives at the node
     T px[2] = {(xs[0].D - T(0.5) * xs[0].S) * inv_h, (xs[1].D + T(0.5) * xs[1].S) * inv_h};
     T qy[2] = {(ys[0].D - T(0.5) * ys[0].S) * inv_h, (ys[1].D + T(0.5) * ys[1].S) * inv_h};
-    // Step 2: one-sided speeds over the four pairs
+    // Step 2: one-sided speeds over the four pairs (dH/dp = v0 p / |(p,q)|, 0 at the origin)
     T ap = 0, am = 0, bp = 0, bm = 0;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             T p = px[s], q = qy[t];
-            T r = sqrt(p * p + q * q);
+            T r2 = p * p + q * q;
             T Hp = T(0), Hq = T(0);
-            if (r > T(0)) { Hp = v0 * p / r; Hq = v0 * q / r; }
-            ap = fmax(ap, Hp); am = fmin(am, Hp);
-            bp = fmax(bp, Hq); bm = fmin(bm, Hq);
+            if (r2 > T(0)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
+            ap = tmax(ap, Hp); am = tmin(am, Hp);
+            bp = tmax(bp, Hq); bm = tmin(bm, Hq);
         }
-    // Step 4 weights (G1, G5)
-    T wx[2], wy[2];
-    if (ap - am > T(0)) { T iw = T(1) / (ap - am); wx[0] = -am * iw; wx[1] = ap * iw; }
-    else { wx[0] = T(0.5); wx[1] = T(0.5); }
-    if (bp - bm > T(0)) { T iw = T(1) / (bp - bm); wy[0] = -bm * iw; wy[1] = bp * iw; }
-    else { wy[0] = T(0.5); wy[1] = T(0.5); }
+    // Step 4 weights (G1, G5): w(s,t) = nx[s] ny[t] / (dxw dyw), one reciprocal
+    T nx[2], ny[2], dxw, dyw;
+    if (ap - am > T(0)) { nx[0] = -am; nx[1] = ap; dxw = ap - am; }
+    else { nx[0] = T(0.5); nx[1] = T(0.5); dxw = T(1); }
+    if (bp - bm > T(0)) { ny[0] = -bm; ny[1] = bp; dyw = bp - bm; }
+    else { ny[0] = T(0.5); ny[1] = T(0.5); dyw = T(1); }
+    const T inv_w = trcp(dxw * dyw);
     // Step 3: values at the four intermediate points (G2, G3)
     T acc = T(0);
 #pragma unroll
@@ -180,6 +238,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_le
         const T sgx = (s == 0) ? T(-1) : T(1);  // dx (dx -+ h)
         const T X = Dx * ddx * inv_h + Sx * ddx * (ddx + sgx * h) * (T(0.5) * inv_h2);
         const T dX = Dx * inv_h + Sx * (T(2) * ddx + sgx * h) * (T(0.5) * inv_h2);
+        T accs = T(0);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int cy = (t == 0) ? 1 : -1;
@@ -193,19 +252,22 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_le
             T p = dX + cross * ddy;
             T q = dY + cross * ddx;
             if (time_level == 0) {
-                T r = sqrt(p * p + q * q);
+                T r2 = p * p + q * q;
                 T gx = T(0), gy = T(0);
-                if (r > T(0)) { gx = v0 * p / r; gy = v0 * q / r; }
+                if (r2 > T(0)) { T vr = v0 * trsqrt(r2); gx = vr * p; gy = vr * q; }
                 T hxx = Sx * inv_h2, hyy = Sy * inv_h2;
                 T np = p - T(0.5) * dt * (hxx * gx + cross * gy);
                 T nq = q - T(0.5) * dt * (cross * gx + hyy * gy);
                 p = np; q = nq;
             }
-            const T psi = val - dt * v0 * sqrt(p * p + q * q);
-            acc += wx[s] * wy[t] * psi;
+            const T s2 = p * p + q * q;
+            const T g = (s2 > T(0)) ? s2 * trsqrt(s2) : T(0);   // |grad|
+            const T psi = val - dt * v0 * g;
+            accs += ny[t] * psi;
         }
+        acc += nx[s] * accs;
     }
-    return acc;
+    return acc * inv_w;
 }
 
 }  // namespace fdm

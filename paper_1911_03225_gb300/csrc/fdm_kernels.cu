@@ -61,11 +61,13 @@ __device__ __forceinline__ void loading_state(const fdm_params& p, long long ste
     }
 }
 
+constexpr int kFftThreads = 512;  // threads per block of the FFT kernels
+
 // ------------------------------------------------------------------ row forward (R2C)
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional per-block FP64 sum of
 // the loaded values (for <U13>).
 template <typename T>
-__global__ void __launch_bounds__(256) row_forward_kernel(const T* __restrict__ src, cpx<T>* __restrict__ spec,
+__global__ void __launch_bounds__(512) row_forward_kernel(const T* __restrict__ src, cpx<T>* __restrict__ spec,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1,
                                                           double* __restrict__ row_partials) {
@@ -76,16 +78,31 @@ __global__ void __launch_bounds__(256) row_forward_kernel(const T* __restrict__ 
     cpx<T>* B = A + (size_t)R * ld;
     double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
     const int y0 = blockIdx.x * R;
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
-        int r = e / L, m = e - r * L;
-        const T* row = src + (size_t)(y0 + r) * n1;
-        T a = row[2 * m], b = row[2 * m + 1];
-        acc += (double)a + (double)b;
-        A[r * ld + m] = mk(a, b);
+    const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
+    T acc = T(0), comp = T(0);  // compensated (Kahan) per-thread sum in the field's type
+    const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
+    const int total = R * L, step = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
+        cpx<T> v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e = e0 + u * step;
+            if (e < total) v[u] = src2[e];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e = e0 + u * step;
+            if (e < total) {
+                T y = (v[u].x + v[u].y) - comp;
+                T t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+                A[(e >> lL) * ld + (e & (L - 1))] = v[u];
+            }
+        }
     }
     if (row_partials) {
-        double s = block_sum(acc, red);
+        double s = block_sum((double)acc - (double)comp, red);
         if (threadIdx.x == 0) row_partials[blockIdx.x] = s;
     }
     __syncthreads();
@@ -93,12 +110,12 @@ __global__ void __launch_bounds__(256) row_forward_kernel(const T* __restrict__ 
     cpx<T>* P = (Z == A) ? B : A;
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
-        int r = e / half, k = e - r * half;
+        int r = e / half, k = e - r * half;  // half = L/2 + 1 is not a power of two
         r2c_twist_pair(Z + r * ld, P + r * ld, L, k, tw1);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
-        int kx = e / R, r = e - kx * R;
+        int kx = e >> lR, r = e & (R - 1);
         spec[(size_t)kx * n2 + y0 + r] = P[r * ld + kx];
     }
 }
@@ -113,73 +130,88 @@ __global__ void __launch_bounds__(256) row_forward_kernel(const T* __restrict__ 
 //   COL_INV       inverse transform only
 enum ColMode { COL_K = 0, COL_DERIV1 = 1, COL_DERIV2N = 2, COL_FWD = 3, COL_INV = 4 };
 
+template <typename T>
 struct ColArgs {
     fdm_params p;
     int mode;
     const double* row_partials;  // COL_K: per-row-block sums of U13 (nparts entries)
     int nparts;
     fdm_dev_scalars* sc;         // COL_K: scalars (block 0 writes mean/eps/sigma)
-    double dx;
+    T scl;                       // 1 / (n1 n2)
+    T xi1_unit, xi2_unit;        // 2 pi / (n dx): xi = k~ * unit
 };
 
 template <typename T>
-__device__ __forceinline__ cpx<T> col_multiplier(const ColArgs& a, const T* __restrict__ Kh, int kxi,
+__device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* __restrict__ Kh, int kxi,
                                                  int ky, int n1, int n2) {
     // kxi in [0, n1/2]; ky in [0, n2)
-    const T scl = T(1.0 / ((double)n1 * (double)n2));
     if (a.mode == COL_K) {
         int kyf = ky <= n2 / 2 ? ky : n2 - ky;
-        return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf] * scl, T(0));
+        return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf] * a.scl, T(0));
     }
-    const double two_pi = 6.283185307179586476925286766559;
     if (a.mode == COL_DERIV1) {
         if (2 * kxi == n1) return mk(T(0), T(0));
-        T xi1 = T(two_pi * (double)kxi / ((double)n1 * a.dx));
-        return mk(T(0), xi1 * scl);
+        return mk(T(0), T(kxi) * a.xi1_unit * a.scl);
     }
     // COL_DERIV2N
     if (2 * ky == n2) return mk(T(0), T(0));
     int kys = ky <= n2 / 2 ? ky : ky - n2;
-    T xi2 = T(two_pi * (double)kys / ((double)n2 * a.dx));
-    return mk(T(0), -xi2 * scl);
+    return mk(T(0), -(T(kys) * a.xi2_unit) * a.scl);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
+__global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
                                                        int n1, int n2, int C,
                                                        const cpx<T>* __restrict__ tw2, const T* __restrict__ Kh,
-                                                       ColArgs a) {
+                                                       ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ld = n2;
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* B = A + (size_t)C * ld;
     __shared__ double s_sigma;
+    __shared__ double s_red[32];
     const int kx0 = blockIdx.x * C;
     const cpx<T>* src = in + (size_t)kx0 * n2;
-    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) A[e] = src[e];
-    if (a.mode == COL_K && kx0 == 0 && threadIdx.x == 0) {
-        // <U13> from the row-block sums (fixed order, compensated), then the loading state
+    {
+        const int total = C * n2, step = blockDim.x;
+        for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
+            cpx<T> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u * step < total) v[u] = src[e0 + u * step];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u * step < total) A[e0 + u * step] = v[u];
+        }
+    }
+    if (a.mode == COL_K && kx0 == 0) {
+        // <U13> from the row-block sums (fixed order, compensated per thread), then the
+        // loading state of this step (Sec. 5.1)
         double s = 0.0, c = 0.0;
-        for (int i = 0; a.row_partials && i < a.nparts; ++i) {
+        for (int i = threadIdx.x; a.row_partials && i < a.nparts; i += blockDim.x) {
             double x = a.row_partials[i], t = s + x;
             c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
             s = t;
         }
-        double mean = a.row_partials ? a.sc->phi_ref + (s + c) / ((double)n1 * (double)n2) : a.sc->mean_up13;
-        double eps, sig;
-        loading_state(a.p, a.sc->step, mean, &eps, &sig);
-        a.sc->mean_up13 = mean;
-        a.sc->eps_bar13 = eps;
-        a.sc->sigma_bar13 = sig;
-        s_sigma = sig;
+        double tot = block_sum(s + c, s_red);
+        if (threadIdx.x == 0) {
+            double mean = a.row_partials ? a.sc->phi_ref + tot / ((double)n1 * (double)n2) : a.sc->mean_up13;
+            double eps, sig;
+            loading_state(a.p, a.sc->step, mean, &eps, &sig);
+            a.sc->mean_up13 = mean;
+            a.sc->eps_bar13 = eps;
+            a.sc->sigma_bar13 = sig;
+            s_sigma = sig;
+        }
     }
     __syncthreads();
     cpx<T>* res = A;
     if (a.mode != COL_INV) res = smem_fft(A, B, n2, C, ld, -1, tw2, n2);
     cpx<T>* oth = (res == A) ? B : A;
     if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N) {
+        const int ln2 = 31 - __clz(n2);
         for (int e = threadIdx.x; e < C * n2; e += blockDim.x) {
-            int c = e / n2, ky = e - c * n2;
+            int c = e >> ln2, ky = e & (n2 - 1);
             int kx = kx0 + c;
             cpx<T> z = res[c * ld + ky];
             cpx<T> o;
@@ -211,26 +243,47 @@ __global__ void __launch_bounds__(256) col_pass_kernel(const cpx<T>* in, cpx<T>*
 // tau13 and reduce max |v0| of the celerity law into sc->vmax_bits.
 enum RowMode { ROW_PLAIN = 0, ROW_TAU = 1 };
 
-struct RowArgs {
-    fdm_params p;
-    int mode;
-    const void* phi;           // ROW_TAU with tau_y != 0: current U13 (type T)
-    fdm_dev_scalars* sc;
-    double offset;             // ROW_PLAIN: added to every output value
+// celerity law (Sec. 3.2.3 Hamiltonian; Sec. 4.1 prescribed), parameters in the field type
+template <typename T>
+struct VelLaw {
+    int mode;            // FDM_V_PRESCRIBED or FDM_V_STRESS
+    int friction;        // tau_y != 0 and stress driven
+    T v0, mobility;
+    double tau_y, beta;  // lattice friction (FP64; evaluated only when friction != 0)
 };
 
-template <typename T>
-__device__ __forceinline__ T celerity(const fdm_params& p, T tau, T up, double phi_ref) {
-    if (p.velocity_mode == FDM_V_PRESCRIBED) return T(p.v0);
-    T fr = T(0);
-    if (p.tau_y != 0.0) fr = T(p.tau_y * cos(((double)up + phi_ref) / p.beta));
-    return T(p.mobility) * (fr - tau);
+template <typename T> VelLaw<T> make_vel(const fdm_params& p) {
+    VelLaw<T> v;
+    v.mode = p.velocity_mode;
+    v.friction = (p.tau_y != 0.0 && p.velocity_mode == FDM_V_STRESS) ? 1 : 0;
+    v.v0 = T(p.v0);
+    v.mobility = T(p.mobility);
+    v.tau_y = p.tau_y;
+    v.beta = p.beta;
+    return v;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) row_inverse_kernel(const cpx<T>* __restrict__ spec, T* __restrict__ dst,
+__device__ __forceinline__ T celerity(const VelLaw<T>& v, T tau, T up, double phi_ref) {
+    if (v.mode == FDM_V_PRESCRIBED) return v.v0;
+    T fr = T(0);
+    if (v.friction) fr = T(v.tau_y * cos(((double)up + phi_ref) / v.beta));
+    return v.mobility * (fr - tau);
+}
+
+template <typename T>
+struct RowArgs {
+    VelLaw<T> vel;
+    int mode;
+    const void* phi;           // ROW_TAU with tau_y != 0: current U13 (type T)
+    fdm_dev_scalars* sc;
+    T offset;                  // ROW_PLAIN: added to every output value
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* __restrict__ spec, T* __restrict__ dst,
                                                           int n1, int n2, int R,
-                                                          const cpx<T>* __restrict__ tw1, RowArgs a) {
+                                                          const cpx<T>* __restrict__ tw1, RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = n1 >> 1;
     const int ld = L + 1;
@@ -238,9 +291,22 @@ __global__ void __launch_bounds__(256) row_inverse_kernel(const cpx<T>* __restri
     cpx<T>* B = A + (size_t)R * ld;
     double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
     const int y0 = blockIdx.x * R;
-    for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
-        int kx = e / R, r = e - kx * R;
-        B[r * ld + kx] = spec[(size_t)kx * n2 + y0 + r];
+    const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
+    {
+        const int total = R * L, step = blockDim.x;
+        for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
+            cpx<T> v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int e = e0 + u * step;
+                if (e < total) v[u] = spec[(size_t)(e >> lR) * n2 + y0 + (e & (R - 1))];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int e = e0 + u * step;
+                if (e < total) B[(e & (R - 1)) * ld + (e >> lR)] = v[u];
+            }
+        }
     }
     __syncthreads();
     const int half = L / 2 + 1;
@@ -250,30 +316,31 @@ __global__ void __launch_bounds__(256) row_inverse_kernel(const cpx<T>* __restri
     }
     __syncthreads();
     cpx<T>* z = smem_fft(A, B, L, R, ld, +1, tw1, n1);
-    double vmax = 0.0;
+    T vmax = T(0);
     bool bad = false;
     const T* up = reinterpret_cast<const T*>(a.phi);
-    const double phi_ref = a.sc ? a.sc->phi_ref : 0.0;
+    const double phi_ref = (a.sc && a.vel.friction) ? a.sc->phi_ref : 0.0;
+    const bool need_up = a.vel.friction != 0;
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
-        int r = e / L, m = e - r * L;
+        int r = e >> lL, m = e & (L - 1);
         cpx<T> v = z[r * ld + m];
         size_t o = (size_t)(y0 + r) * n1 + 2 * m;
         if (a.mode == ROW_TAU) {
             T u0 = T(0), u1 = T(0);
-            if (a.p.tau_y != 0.0 && a.p.velocity_mode == FDM_V_STRESS) { u0 = up[o]; u1 = up[o + 1]; }
-            T c0 = celerity(a.p, v.x, u0, phi_ref), c1 = celerity(a.p, v.y, u1, phi_ref);
-            vmax = fmax(vmax, fmax(fabs((double)c0), fabs((double)c1)));
+            if (need_up) { u0 = up[o]; u1 = up[o + 1]; }
+            T c0 = celerity(a.vel, v.x, u0, phi_ref), c1 = celerity(a.vel, v.y, u1, phi_ref);
+            vmax = tmax(vmax, tmax(tabs(c0), tabs(c1)));
             bad |= (c0 != c0) || (c1 != c1);
             dst[o] = v.x;
             dst[o + 1] = v.y;
         } else {
-            dst[o] = T((double)v.x + a.offset);
-            dst[o + 1] = T((double)v.y + a.offset);
+            dst[o] = v.x + a.offset;
+            dst[o + 1] = v.y + a.offset;
         }
     }
     if (a.mode == ROW_TAU) {
-        // NaN-aware block max through the bit pattern of |v|
-        unsigned long long bits = bad ? 0x7ff8000000000000ull : abs_bits(vmax);
+        // NaN-aware block max through the bit pattern of |v| (max is exact in any precision)
+        unsigned long long bits = bad ? 0x7ff8000000000000ull : abs_bits((double)vmax);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
@@ -287,61 +354,72 @@ __global__ void __launch_bounds__(256) row_inverse_kernel(const cpx<T>* __restri
 // ------------------------------------------------------------------ KNP stencil
 constexpr int TX = 32, TY = 8;
 
+template <typename T>
 struct KnpArgs {
-    fdm_params p;
+    VelLaw<T> vel;
+    double cfl, dx, dt_max;  // time-step rule (FP64)
+    T h, theta;
+    int time_level;
     fdm_dev_scalars* sc;
-    double* blk_partials;  // unused slot for future fused reductions
 };
+
+// dt from the CFL rule |v0|max dt / dx = CFL (Sec. 4.3, Sec. 5.2), in FP64
+__device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, double dt_max) {
+    double dtd;
+    if (vmax > 0.0) {
+        dtd = cfl * dx / vmax;
+        if (dt_max > 0.0 && dtd > dt_max) dtd = dt_max;
+    } else {
+        dtd = dt_max > 0.0 ? dt_max : 0.0;
+    }
+    return dtd;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* __restrict__ phi, const T* __restrict__ tau,
-                                                           T* __restrict__ out, int n1, int n2, KnpArgs a) {
+                                                           T* __restrict__ out, int n1, int n2, KnpArgs<T> a) {
     __shared__ T tile[TY + 4][TX + 4];
-    __shared__ unsigned int s_last;
+    __shared__ T s_dt;
     const int tx = blockDim.x;  // TX, or n1 when n1 < TX
     const int bx = blockIdx.x * tx, by = blockIdx.y * TY;
     const int tid = threadIdx.y * tx + threadIdx.x;
-    for (int e = tid; e < (TY + 4) * (tx + 4); e += tx * TY) {
-        int ly = e / (tx + 4), lx = e - ly * (tx + 4);
-        int gx = (bx + lx - 2) & (n1 - 1), gy = (by + ly - 2) & (n2 - 1);
-        tile[ly][lx] = phi[(size_t)gy * n1 + gx];
+    for (int ly = threadIdx.y; ly < TY + 4; ly += TY) {
+        const int gy = (by + ly - 2) & (n2 - 1);
+        for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
+            const int gx = (bx + lx - 2) & (n1 - 1);
+            tile[ly][lx] = phi[(size_t)gy * n1 + gx];
+        }
+    }
+    fdm_dev_scalars* sc = a.sc;
+    if (tid == 0) {
+        // dt of this step from the max |v0| reduced by the previous kernel; the last block to
+        // read it advances the clock and clears the running max for the next step (every
+        // other block has read it by then: each reads before its fenced counter increment)
+        const double vmax = __longlong_as_double((long long)sc->vmax_bits);
+        const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
+        s_dt = T(dtd);
+        __threadfence();
+        const unsigned int total = gridDim.x * gridDim.y;
+        if (atomicAdd(&sc->done_count, 1u) == total - 1) {
+            __threadfence();
+            sc->step += 1;
+            sc->t += dtd;
+            sc->dt = dtd;
+            sc->max_abs_v0 = vmax;
+            if (!(dtd == dtd) || !(vmax == vmax) || isinf(dtd)) sc->status = FDM_ERR_NONFINITE;
+            sc->vmax_bits = 0ull;
+            sc->done_count = 0u;
+        }
     }
     __syncthreads();
-    fdm_dev_scalars* sc = a.sc;
-    const double vmax = __longlong_as_double((long long)sc->vmax_bits);
-    double dtd;
-    if (vmax > 0.0) {
-        dtd = a.p.cfl * a.p.dx / vmax;
-        if (a.p.dt_max > 0.0 && dtd > a.p.dt_max) dtd = a.p.dt_max;
-    } else {
-        dtd = a.p.dt_max > 0.0 ? a.p.dt_max : 0.0;
-    }
+    const T dt = s_dt;
     const int x = bx + threadIdx.x, y = by + threadIdx.y;
     const int lx = threadIdx.x + 2, ly = threadIdx.y + 2;
     const T up = tile[ly][lx];
-    const T v0 = celerity(a.p, tau[(size_t)y * n1 + x], up, sc->phi_ref);
+    const double phi_ref = a.vel.friction ? sc->phi_ref : 0.0;
+    const T v0 = celerity(a.vel, tau[(size_t)y * n1 + x], up, phi_ref);
     auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
-    T nv = knp_node<T>(f, v0, T(dtd), T(a.p.dx), T(a.p.theta), a.p.time_level);
-    out[(size_t)y * n1 + x] = nv;
-    // last block to finish advances the clock (all blocks have read vmax by then)
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        unsigned int total = gridDim.x * gridDim.y;
-        unsigned int prev = atomicAdd(&sc->done_count, 1u);
-        s_last = (prev == total - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last && tid == 0) {
-        __threadfence();
-        sc->step += 1;
-        sc->t += dtd;
-        sc->dt = dtd;
-        sc->max_abs_v0 = vmax;
-        if (!(dtd == dtd) || !(vmax == vmax) || isinf(dtd)) sc->status = FDM_ERR_NONFINITE;
-        sc->vmax_bits = 0ull;
-        sc->done_count = 0u;
-    }
+    out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.h, a.theta, a.time_level);
 }
 
 // ------------------------------------------------------------------ set-up / readout helpers
@@ -470,7 +548,7 @@ __global__ void alpha_sums_kernel(const T* __restrict__ phi, int n1, int n2, dou
 template <typename T>
 __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__ a12, const T* __restrict__ tau,
                                 const T* __restrict__ phi, T* __restrict__ v1, T* __restrict__ v2, size_t n,
-                                fdm_params p, double phi_ref) {
+                                VelLaw<T> p, double phi_ref) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T c = celerity(p, tau[i], phi[i], phi_ref);
         T m = sqrt(a11[i] * a11[i] + a12[i] * a12[i]);
@@ -518,21 +596,23 @@ cudaError_t configure_kernels() {
 template <typename T>
 void launch_row_forward(const Dev& d, const T* src, cpx<T>* spec, double* partials, cudaStream_t s) {
     const LaunchGeom& g = d.geom;
-    row_forward_kernel<T><<<g.row_blocks, 256, g.row_smem, s>>>(src, spec, d.p.n1, d.p.n2, g.R,
+    row_forward_kernel<T><<<g.row_blocks, kFftThreads, g.row_smem, s>>>(src, spec, d.p.n1, d.p.n2, g.R,
                                                                 (const cpx<T>*)d.tw1, partials);
 }
 
 template <typename T>
 void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, cudaStream_t s) {
     const LaunchGeom& g = d.geom;
-    ColArgs a;
+    ColArgs<T> a;
     a.p = d.p;
     a.mode = mode;
     a.row_partials = with_mean ? d.row_partials : nullptr;
     a.nparts = g.row_blocks;
     a.sc = d.sc;
-    a.dx = d.p.dx;
-    col_pass_kernel<T><<<g.col_blocks, 256, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
+    a.scl = T(1.0 / ((double)d.p.n1 * (double)d.p.n2));
+    a.xi1_unit = T(6.283185307179586476925286766559 / ((double)d.p.n1 * d.p.dx));
+    a.xi2_unit = T(6.283185307179586476925286766559 / ((double)d.p.n2 * d.p.dx));
+    col_pass_kernel<T><<<g.col_blocks, kFftThreads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
                                                              (const cpx<T>*)d.tw2, (const T*)d.Kh, a);
 }
 
@@ -540,22 +620,27 @@ template <typename T>
 void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, const T* phi, double offset,
                         cudaStream_t s) {
     const LaunchGeom& g = d.geom;
-    RowArgs a;
-    a.p = d.p;
+    RowArgs<T> a;
+    a.vel = make_vel<T>(d.p);
     a.mode = mode;
     a.phi = phi;
     a.sc = d.sc;
-    a.offset = offset;
-    row_inverse_kernel<T><<<g.row_blocks, 256, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
+    a.offset = T(offset);
+    row_inverse_kernel<T><<<g.row_blocks, kFftThreads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
                                                                 (const cpx<T>*)d.tw1, a);
 }
 
 template <typename T>
 void launch_knp(const Dev& d, const T* phi, const T* tau, T* out, cudaStream_t s) {
-    KnpArgs a;
-    a.p = d.p;
+    KnpArgs<T> a;
+    a.vel = make_vel<T>(d.p);
+    a.cfl = d.p.cfl;
+    a.dx = d.p.dx;
+    a.dt_max = d.p.dt_max;
+    a.h = T(d.p.dx);
+    a.theta = T(d.p.theta);
+    a.time_level = d.p.time_level;
     a.sc = d.sc;
-    a.blk_partials = nullptr;
     const int tx = d.p.n1 < TX ? d.p.n1 : TX;
     dim3 grid(d.p.n1 / tx, d.p.n2 / TY), block(tx, TY);
     knp_step_kernel<T><<<grid, block, 0, s>>>(phi, tau, out, d.p.n1, d.p.n2, a);
@@ -644,7 +729,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     size_t n = (size_t)d.p.n1 * d.p.n2;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
-    velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, d.p, d.phi_ref_host);
+    velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, make_vel<T>(d.p), d.phi_ref_host);
 }
 
 // explicit instantiations

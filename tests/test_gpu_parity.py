@@ -163,7 +163,7 @@ def test_ring_expansion_short(precision, tol):
     n = 256
     a11, a12 = inputs.ring_alpha(n, r0=50.0, sigma=2.0)
     p = Params(n1=n, n2=n, v0=-1.0, theta=2.0, cfl=0.4, precision=precision)
-    got, info, ref, _ = run_both(p, alpha=(a11, a12), mean=0.0, steps=8)
+    got, info, ref, _ = run_both(p, alpha=(a11, a12), mean=0.0, steps=5)
     assert rel(got["up13"], ref.up13) < tol
     assert rel(got["tau13"], ref.tau13) < tol
 
