@@ -45,7 +45,8 @@ typedef enum {
     FDM_ERR_NONFINITE = 5,      /* a non-finite time step or field appeared                  */
     FDM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up                         */
     FDM_ERR_DEVICE = 7,         /* a CUDA call failed                                        */
-    FDM_ERR_STATE = 8           /* call out of order (e.g. fdm_step before any fdm_set_*)    */
+    FDM_ERR_STATE = 8,          /* call out of order (e.g. fdm_step before any fdm_set_*)    */
+    FDM_ERR_TOO_LARGE = 9       /* grid exceeds the fixed scratch of fdm_static_solve_noalloc */
 } fdm_status;
 
 enum { FDM_V_PRESCRIBED = 0, FDM_V_STRESS = 1 };
@@ -165,6 +166,24 @@ fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
+
+/* Static solve that allocates no device memory (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate -- e.g. a process whose HBM is already
+ * fully handed out to other buffers, or an embedding that forbids allocations outside its
+ * own pool).  Computes tau13 = IFFT(K FFT(U13)) + sigma_bar13 exactly like fdm_static_solve
+ * with FDM_LOAD_STRESS, in FP64, for caller-owned DEVICE arrays d_up13 (input) and
+ * d_tau13 (output), both [n2][n1] float64, not overlapping.  Only the grid, nz, nh, dx, E
+ * and nu fields of p are used; p->precision must be FDM_FP64.
+ * Limits: n1, n2 <= 256 and nz <= 4096; larger grids return FDM_ERR_TOO_LARGE.
+ * All intermediates live in one fixed device array of about 700 KB that every GPU which
+ * loads this library holds until the process exits.  The first call on a device sets that
+ * device up (resolves the array's address, sets kernel attributes); make that first call
+ * before any stream capture.  Every call uses the same array: calls that overlap on the
+ * GPU (different streams or threads at once) race and give wrong results; serialise them.
+ * Work is enqueued on `stream` (NULL = legacy default stream) and the call returns without
+ * waiting; no cudaMalloc, cudaFree or other allocating routine is called. */
+fdm_status fdm_static_solve_noalloc(const fdm_params *p, double sigma_bar13, const double *d_up13,
+                                    double *d_tau13, void *stream);
 
 /* Frees everything; NULL-safe. */
 void fdm_destroy(fdm_handle *h);

@@ -24,6 +24,7 @@ FDM_ERR_NONFINITE = 5
 FDM_ERR_TIMEOUT = 6
 FDM_ERR_DEVICE = 7
 FDM_ERR_STATE = 8
+FDM_ERR_TOO_LARGE = 9
 
 V_PRESCRIBED, V_STRESS = 0, 1
 LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS = 0, 1, 2
@@ -38,7 +39,8 @@ FIELDS = {"up13": FIELD_UP13, "alpha11": FIELD_ALPHA11, "alpha12": FIELD_ALPHA12
 EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_density",
            "fdm_set_plastic_distortion", "fdm_set_clock", "fdm_static_solve", "fdm_step",
            "fdm_read_fields", "fdm_get_info", "fdm_kernels_per_step", "fdm_destroy",
-           "fdm_status_str", "fdm_enqueue_steps", "fdm_enqueue_phase", "fdm_sync"]
+           "fdm_status_str", "fdm_enqueue_steps", "fdm_enqueue_phase", "fdm_sync",
+           "fdm_static_solve_noalloc"]
 
 
 class CParams(C.Structure):
@@ -143,6 +145,8 @@ def load():
     lib.fdm_enqueue_steps.argtypes = [H, C.c_int32]
     lib.fdm_enqueue_phase.argtypes = [H, C.c_int32]
     lib.fdm_sync.argtypes = [H]
+    lib.fdm_static_solve_noalloc.argtypes = [C.POINTER(CParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fdm_static_solve_noalloc.restype = C.c_int
     lib.fdm_get_info.argtypes = [H, C.POINTER(CStepInfo)]
     lib.fdm_kernels_per_step.argtypes = [H]
     lib.fdm_kernels_per_step.restype = C.c_int32
@@ -172,6 +176,20 @@ def default_params(n1: int, n2: int) -> Params:
 
 def device_bytes(p: Params) -> int:
     return int(load().fdm_device_bytes(C.byref(p.to_c())))
+
+
+def static_solve_noalloc(params: Params, sigma_bar13: float, d_up13: int, d_tau13: int,
+                        stream: Optional[int] = None):
+    """tau13 for a caller-owned device array, without any device allocation.
+
+    For callers that cannot allocate device memory (their HBM is already committed, or only
+    their own pool may allocate).  ``d_up13`` and ``d_tau13`` are device addresses of
+    [n2][n1] float64 arrays (e.g. ``tensor.data_ptr()``); work is enqueued on ``stream``.
+    The library's fixed scratch limits the grid to n1, n2 <= 256; overlapping calls race.
+    """
+    _check(load().fdm_static_solve_noalloc(C.byref(params.to_c()), float(sigma_bar13), C.c_void_p(d_up13),
+                                            C.c_void_p(d_tau13), C.c_void_p(stream or 0)),
+           "fdm_static_solve_noalloc")
 
 
 def _dptr(a):

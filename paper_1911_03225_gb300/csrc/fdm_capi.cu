@@ -522,6 +522,7 @@ const char* fdm_status_str(fdm_status s) {
         case FDM_ERR_TIMEOUT: return "device-side wait timed out";
         case FDM_ERR_DEVICE: return "CUDA error";
         case FDM_ERR_STATE: return "call out of order (no state set)";
+        case FDM_ERR_TOO_LARGE: return "grid exceeds the fixed scratch of the no-allocation static solve (n1, n2 <= 256, nz <= 4096)";
     }
     return "unknown status";
 }

@@ -63,7 +63,7 @@ def test_null_arguments(lib):
 
 
 def test_status_strings(lib):
-    for s in range(9):
+    for s in range(10):
         assert binding.status_str(s) not in ("", "unknown status")
     assert binding.status_str(99) == "unknown status"
 

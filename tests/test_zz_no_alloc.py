@@ -1,0 +1,76 @@
+"""The static solve that allocates no device memory, checked against the handle-based one.
+
+Some callers cannot let a library allocate device memory (their HBM is already committed,
+or only their own pool may allocate); fdm_static_solve_noalloc works entirely in a fixed
+library-owned device array.  Its result must equal the regular static solve's within the
+tolerance of the other FP64 parity tests, on two calls in a row (the array keeps the
+previous call's contents, which must not leak into the next result).
+
+This file is collected last on purpose (``zz``).
+"""
+import numpy as np
+import pytest
+
+from paper_1911_03225_gb300 import FDM, Params, inputs
+from paper_1911_03225_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _reference_tau(p: Params, up, sigma):
+    q = Params(**{**p.__dict__, "loading_mode": B.LOAD_STRESS, "sigma_bar13": sigma,
+                  "velocity_mode": B.V_STRESS})
+    with FDM(q) as sim:
+        sim.set_plastic_distortion(up)
+        sim.static_solve()
+        return sim.read_fields("tau13")["tau13"]
+
+
+def _noalloc_tau(p: Params, up, sigma):
+    import torch
+    stream = torch.cuda.current_stream()
+    d_up = torch.from_numpy(np.ascontiguousarray(up)).cuda()
+    d_tau = torch.full_like(d_up, float("nan"))
+    torch.cuda.synchronize()
+    B.static_solve_noalloc(p, sigma, d_up.data_ptr(), d_tau.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    return d_tau.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,nh", [((64, 128), 4), ((256, 256), 2)])
+def test_noalloc_static_solve_matches_handle_path_twice(shape, nh):
+    n2, n1 = shape
+    p = Params(n1=n1, n2=n2, nh=nh)
+    ups = [inputs.random_up(max(shape), seed=s, ell=4.0)[:n2, :n1] for s in (21, 22)]
+    sigmas = [0.0125, -0.3]
+    for up, sig in zip(ups, sigmas):          # two calls in a row, different inputs
+        ref = _reference_tau(p, up, sig)
+        got = _noalloc_tau(p, up, sig)
+        assert np.isfinite(got).all()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < TOL, err
+        assert got.mean() == pytest.approx(sig, abs=1e-13)
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    import torch
+    p = Params(n1=512, n2=64)
+    d = torch.zeros(64, 512, dtype=torch.float64, device="cuda")
+    o = torch.zeros_like(d)
+    with pytest.raises(B.FDMError) as e:
+        B.static_solve_noalloc(p, 0.0, d.data_ptr(), o.data_ptr())
+    assert e.value.status == B.FDM_ERR_TOO_LARGE
+    with pytest.raises(B.FDMError) as e:
+        B.static_solve_noalloc(Params(n1=64, n2=64, precision=B.MIXED), 0.0, d.data_ptr(), o.data_ptr())
+    assert e.value.status == B.FDM_ERR_INVALID_ARG
