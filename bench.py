@@ -316,6 +316,121 @@ def cpu_baseline(seconds):
                       "layer-kernel precompute excluded" % (n, n, steps, dt)}
 
 
+def batched_workload(count=256):
+    """Configuration 4: `count` independent coupled instances, side drawn per seed from
+    {64, 128, 256, 512}, random field (l = 16, RMS |alpha| = 0.1) with the instance's seed."""
+    sizes = [64, 128, 256, 512]
+    out = []
+    for i in range(count):
+        n = sizes[int(np.random.default_rng(i).integers(4))]
+        out.append((n, workload_input(n, seed=i)))
+    return out
+
+
+def run_batched(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    from paper_1911_03225_gb300 import Batch, FDM
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+    inst = batched_workload(args.instances)
+    cells = sum(n * n for n, _ in inst)
+    params = [workload_params(n, "mixed") for n, _ in inst]
+    with Batch(params, stream=stream.cuda_stream) as b:
+        for i, (n, up) in enumerate(inst):
+            b.set_plastic_distortion(i, up)
+            b.set_budget(i, W + K)
+        b.enqueue_steps(W)
+        b.sync()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier(world)
+            e0.record(stream)
+            b.enqueue_steps(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+        left = b.sync()
+        assert (left == 0).all()
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
+        launches = b.launches_per_step() * K
+        sample = list(range(0, len(inst), max(1, len(inst) // 8)))[:8]
+        mixed_out = {i: b.read_fields(i, "up13")["up13"] for i in sample}
+    # the plain per-instance FP64 form on the same GPU: one handle per instance, stepped alone
+    fp64_cells, fp64_ms, errs = 0, 0.0, []
+    for i in sample:
+        n, up = inst[i]
+        with FDM(workload_params(n, "fp64"), stream=stream.cuda_stream) as sim:
+            sim.set_plastic_distortion(up)
+            sim.enqueue_steps(W)
+            sim.sync()
+            e0.record(stream)
+            sim.enqueue_steps(K)
+            e1.record(stream)
+            sim.sync()
+            fp64_ms += e0.elapsed_time(e1)
+            fp64_cells += n * n
+            ref = sim.read_fields("up13")["up13"]
+        errs.append(float(np.linalg.norm(mixed_out[i] - ref) / np.linalg.norm(ref)))
+    value = cells * K * world / (ms / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (FP64 scalars)", "data": "synthetic (seeded random U13 fields)",
+            "config": {"workload": "batched uneven instances: %d coupled simulations, side per seed in "
+                                   "{64,128,256,512}, mixed precision, one batched launch per kernel and size "
+                                   "class, CUDA-graph steps" % len(inst),
+                       "cells_per_step": cells, "l2": "working set %.0f MB > L2" % (cells * 4 * 5 / 1e6)},
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "plain_fp64_per_instance": {"value": fp64_cells * K / (fp64_ms / 1e3), "unit": UNIT,
+                                        "sample_instances": len(sample)},
+            "mixed_vs_fp64_rel_l2": {"max": max(errs), "mean": sum(errs) / len(errs), "after_steps": W + K},
+        }), flush=True)
+
+
+def run_serve(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    from paper_1911_03225_gb300.binding import FP64, MIXED
+    from paper_1911_03225_gb300.serve import Request, Server, poisson_arrivals
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    R = args.serve_requests
+    rng = np.random.default_rng(1234 + rank)
+    sizes = [64, 128, 256, 512, 1024]
+    arr = poisson_arrivals(200.0, R, seed=77 + rank)
+    reqs = []
+    for k in range(R):
+        n = int(rng.choice(sizes))
+        steps = int(rng.integers(args.serve_min_steps, args.serve_max_steps + 1))
+        prec = FP64 if rng.random() < 0.5 else MIXED
+        reqs.append(Request(k, n, steps, prec, float(arr[k]), workload_input(n, seed=10_000 + k)))
+    classes = {(n, p): args.serve_slots for n in sizes for p in (FP64, MIXED)}
+    srv = Server(workload_params(64, "fp64"), classes, hbm_budget=150e9, tick_steps=args.serve_tick,
+                 stream=stream.cuda_stream, keep_fields=False)
+    barrier(world)
+    with ClockSampler(local) as clk:
+        results, st = srv.run(reqs)
+    srv.close()
+    value = max_over_ranks(st["elapsed_s"], world)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": st["cell_steps"] * world / value, "unit": UNIT, "n_gpus": world,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 and f32 mix",
+            "data": "synthetic (Poisson arrivals, seeded fields)",
+            "config": {"workload": "served request mix: Poisson 200 req/s, side in {64..1024}, steps U[%d,%d], "
+                                   "50%% FP64 / 50%% mixed, 150 GB HBM budget, %d requests (window scaled "
+                                   "down from 2000)" % (args.serve_min_steps, args.serve_max_steps, R),
+                       "slots_per_class": args.serve_slots, "tick_steps": args.serve_tick},
+            "serve": st, "gpu_launches": st["launches"], "clocks": clk.summary(),
+        }), flush=True)
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle (the paper publishes no code or timings)."""
     if rank != 0:
@@ -355,12 +470,23 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="coupled", choices=["coupled", "batched", "serve"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-min-steps", type=int, default=100)
+    ap.add_argument("--serve-max-steps", type=int, default=5000)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-tick", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

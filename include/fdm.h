@@ -188,6 +188,49 @@ fdm_status fdm_static_solve_noalloc(const fdm_params *p, double sigma_bar13, con
 /* Frees everything; NULL-safe. */
 void fdm_destroy(fdm_handle *h);
 
+/* ---------------------------------------------------------------------------------
+ * Batches: many independent instances stepped together.  Instances with identical
+ * parameters form a group; each step runs every kernel once per group over all of the
+ * group's instances (the instance is a grid dimension), and steps are replayed from CUDA
+ * graphs.  Every instance has a step budget: a step advances only instances whose budget
+ * is non-zero and decrements it, so instances of different lengths share launches and
+ * finished or empty slots cost almost nothing.  Same conventions as the single-instance
+ * calls (host arrays [n2][n1] float64, status codes, the stream given at creation).
+ * --------------------------------------------------------------------------------- */
+typedef struct fdm_batch fdm_batch;
+
+/* count >= 1 instances, params[i] for instance i (each valid as for fdm_create). */
+fdm_status fdm_batch_create(int32_t count, const fdm_params *params, void *stream, fdm_batch **out);
+
+/* Bytes of device memory fdm_batch_create would hold for these instances (0 if invalid). */
+size_t fdm_batch_device_bytes(int32_t count, const fdm_params *params);
+
+/* Sets instance i's U13 (host [n2][n1]), resets its step and time to 0 and its budget to 0
+ * (idle until fdm_batch_set_budget). */
+fdm_status fdm_batch_set_plastic_distortion(fdm_batch *b, int32_t i, const double *up13);
+
+/* Sets the number of further steps instance i takes (>= 0).  Enqueued on the stream. */
+fdm_status fdm_batch_set_budget(fdm_batch *b, int32_t i, int64_t steps);
+
+/* Enqueues nsteps batched steps (instances with budget 0 are skipped); no wait. */
+fdm_status fdm_batch_enqueue_steps(fdm_batch *b, int32_t nsteps);
+
+/* Waits for the stream; copies every instance's remaining budget to steps_left[count]
+ * (may be NULL) and returns the first device-side error of any instance. */
+fdm_status fdm_batch_sync(fdm_batch *b, int64_t *steps_left);
+
+/* Scalars of instance i (as fdm_get_info). */
+fdm_status fdm_batch_get_info(fdm_batch *b, int32_t i, fdm_step_info *info);
+
+/* Copies U13 and/or tau13 of instance i (mask of FDM_FIELD_UP13 | FDM_FIELD_TAU13). */
+fdm_status fdm_batch_read_fields(fdm_batch *b, int32_t i, uint32_t mask, double *up13, double *tau13);
+
+/* Kernel launches one batched step issues (kernels per step x groups). */
+int32_t fdm_batch_launches_per_step(const fdm_batch *b);
+
+/* Frees everything; NULL-safe. */
+void fdm_batch_destroy(fdm_batch *b);
+
 /* Static description of a status code. */
 const char *fdm_status_str(fdm_status s);
 

@@ -40,7 +40,10 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_set_plastic_distortion", "fdm_set_clock", "fdm_static_solve", "fdm_step",
            "fdm_read_fields", "fdm_get_info", "fdm_kernels_per_step", "fdm_destroy",
            "fdm_status_str", "fdm_enqueue_steps", "fdm_enqueue_phase", "fdm_sync",
-           "fdm_static_solve_noalloc"]
+           "fdm_static_solve_noalloc", "fdm_batch_create", "fdm_batch_device_bytes",
+           "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget", "fdm_batch_enqueue_steps",
+           "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
+           "fdm_batch_destroy"]
 
 
 class CParams(C.Structure):
@@ -147,6 +150,23 @@ def load():
     lib.fdm_sync.argtypes = [H]
     lib.fdm_static_solve_noalloc.argtypes = [C.POINTER(CParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fdm_static_solve_noalloc.restype = C.c_int
+    PP = C.POINTER(CParams)
+    lib.fdm_batch_create.argtypes = [C.c_int32, PP, C.c_void_p, C.POINTER(H)]
+    lib.fdm_batch_device_bytes.argtypes = [C.c_int32, PP]
+    lib.fdm_batch_device_bytes.restype = C.c_size_t
+    lib.fdm_batch_set_plastic_distortion.argtypes = [H, C.c_int32, d]
+    lib.fdm_batch_set_budget.argtypes = [H, C.c_int32, C.c_int64]
+    lib.fdm_batch_enqueue_steps.argtypes = [H, C.c_int32]
+    lib.fdm_batch_sync.argtypes = [H, C.POINTER(C.c_int64)]
+    lib.fdm_batch_get_info.argtypes = [H, C.c_int32, C.POINTER(CStepInfo)]
+    lib.fdm_batch_read_fields.argtypes = [H, C.c_int32, C.c_uint32, d, d]
+    lib.fdm_batch_launches_per_step.argtypes = [H]
+    lib.fdm_batch_launches_per_step.restype = C.c_int32
+    lib.fdm_batch_destroy.argtypes = [H]
+    lib.fdm_batch_destroy.restype = None
+    for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
+                 "fdm_batch_enqueue_steps", "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields"):
+        getattr(lib, name).restype = C.c_int
     lib.fdm_get_info.argtypes = [H, C.POINTER(CStepInfo)]
     lib.fdm_kernels_per_step.argtypes = [H]
     lib.fdm_kernels_per_step.restype = C.c_int32
@@ -293,6 +313,91 @@ class FDM:
     def close(self):
         if getattr(self, "h", None):
             self.lib.fdm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _params_array(params):
+    arr = (CParams * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p.to_c()
+    return arr
+
+
+def batch_device_bytes(params) -> int:
+    return int(load().fdm_batch_device_bytes(len(params), _params_array(params)))
+
+
+class Batch:
+    """Many independent FDM instances stepped together on the GPU (``fdm_batch_*``).
+
+    Instances with identical parameters share each kernel launch; every instance has a step
+    budget and only instances with budget left advance, so uneven run lengths share launches.
+    """
+
+    def __init__(self, params, stream: Optional[int] = None):
+        self.lib = load()
+        self.params = list(params)
+        self.count = len(self.params)
+        h = C.c_void_p()
+        _check(self.lib.fdm_batch_create(self.count, _params_array(self.params), C.c_void_p(stream or 0),
+                                         C.byref(h)), "fdm_batch_create")
+        self.h = h
+
+    def set_plastic_distortion(self, i: int, up13):
+        p = self.params[i]
+        u = _field(up13, (p.n2, p.n1))
+        _check(self.lib.fdm_batch_set_plastic_distortion(self.h, int(i), _dptr(u)),
+               "fdm_batch_set_plastic_distortion")
+
+    def set_budget(self, i: int, steps: int):
+        _check(self.lib.fdm_batch_set_budget(self.h, int(i), int(steps)), "fdm_batch_set_budget")
+
+    def enqueue_steps(self, nsteps: int):
+        _check(self.lib.fdm_batch_enqueue_steps(self.h, int(nsteps)), "fdm_batch_enqueue_steps")
+
+    def sync(self) -> np.ndarray:
+        """Wait; return every instance's remaining step budget (raises on device errors)."""
+        left = np.zeros(self.count, dtype=np.int64)
+        _check(self.lib.fdm_batch_sync(self.h, left.ctypes.data_as(C.POINTER(C.c_int64))), "fdm_batch_sync")
+        return left
+
+    def info(self, i: int) -> StepInfo:
+        ci = CStepInfo()
+        _check(self.lib.fdm_batch_get_info(self.h, int(i), C.byref(ci)), "fdm_batch_get_info")
+        return StepInfo(**{f: getattr(ci, f) for f, _ in CStepInfo._fields_})
+
+    def read_fields(self, i: int, *names):
+        p = self.params[i]
+        out = {}
+        up = np.empty((p.n2, p.n1)) if "up13" in names else None
+        tau = np.empty((p.n2, p.n1)) if "tau13" in names else None
+        mask = (FIELD_UP13 if up is not None else 0) | (FIELD_TAU13 if tau is not None else 0)
+        _check(self.lib.fdm_batch_read_fields(self.h, int(i), mask, _dptr(up) if up is not None else None,
+                                              _dptr(tau) if tau is not None else None), "fdm_batch_read_fields")
+        if up is not None:
+            out["up13"] = up
+        if tau is not None:
+            out["tau13"] = tau
+        return out
+
+    def launches_per_step(self) -> int:
+        return int(self.lib.fdm_batch_launches_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fdm_batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):

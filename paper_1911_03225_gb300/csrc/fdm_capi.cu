@@ -1,148 +1,61 @@
-// fdm_capi.cu -- C ABI (include/fdm.h) over the CUDA kernels: handle lifetime, device
-// memory, host<->device copies, step sequencing and status reporting.
+// fdm_capi.cu -- C ABI (include/fdm.h) of a single FDM instance over the CUDA kernels:
+// handle lifetime, device memory, host<->device copies, step sequencing (CUDA graphs) and
+// status reporting.  Shared group/graph helpers are defined here too.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "fdm_internal.h"
+#include "fdm_host.h"
 
-using namespace fdm;
-
-struct fdm_handle {
-    Dev d;
-    cudaStream_t stream;
-    int cur;                 // index of the current state buffer
-    int next_phase;          // next kernel of a partially enqueued step (0: none pending)
-    bool has_state;
-    bool mixed;
-    size_t n;                // n1 * n2
-    // lazily allocated readout buffers (type T, n each)
-    void* rd[4];
-    std::vector<void*> owned;
-};
-
-namespace {
+namespace fdm {
 
 const double kPi = 3.14159265358979323846;
 
-bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
-
-bool valid(const fdm_params* p) {
-    if (!p) return false;
-    if (!pow2_in(p->n1, 16, 4096) || !pow2_in(p->n2, 16, 4096)) return false;
-    int nz = p->nz == 0 ? p->n1 : p->nz;
-    if (nz < 1 || nz > 65536 || p->nh < 1 || p->nh > nz) return false;
-    if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return false;
-    if (!(p->E > 0.0) || !(p->nu > -1.0 && p->nu < 0.5)) return false;
-    if (p->velocity_mode != FDM_V_PRESCRIBED && p->velocity_mode != FDM_V_STRESS) return false;
-    if (!std::isfinite(p->v0) || !std::isfinite(p->mobility) || !std::isfinite(p->tau_y)) return false;
-    if (p->tau_y != 0.0 && !(p->beta > 0.0)) return false;
-    if (!(p->theta >= 1.0 && p->theta <= 2.0)) return false;
-    if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return false;
-    if (!std::isfinite(p->dt_max)) return false;
-    if (p->loading_mode < FDM_LOAD_STRESS || p->loading_mode > FDM_LOAD_ZERO_MEAN_STRESS) return false;
-    if (!std::isfinite(p->sigma_bar13) || !std::isfinite(p->eps_bar13_0) || !std::isfinite(p->eps_bar13_rate))
-        return false;
-    if (p->time_level != FDM_T_MIDPOINT && p->time_level != FDM_T_LITERAL) return false;
-    if (p->precision != FDM_FP64 && p->precision != FDM_MIXED) return false;
-    return true;
-}
-
-size_t elt(const fdm_params* p) { return p->precision == FDM_MIXED ? sizeof(float) : sizeof(double); }
-
-int red_blocks_for(size_t n) {
-    size_t b = (n + 255) / 256;
-    if (b > 1024) b = 1024;
-    return (int)b;
-}
-
-void host_loading(const fdm_params& p, long long step, double mean, double* eps, double* sig) {
-    const double mu = p.E / (2.0 * (1.0 + p.nu));
-    const double frac = (double)p.nh / (double)p.nz;
-    if (p.loading_mode == FDM_LOAD_STRESS) {
-        *sig = p.sigma_bar13;
-        *eps = (p.sigma_bar13 + mu * frac * mean) / (2.0 * mu);
-    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP) {
-        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (double)step;
-        *sig = 2.0 * mu * (*eps) - mu * frac * mean;
-    } else {
-        *eps = 0.5 * frac * mean;
-        *sig = 0.0;
-    }
-}
-
-// Neumaier sum of host values
-double ksum(const double* x, size_t n) {
-    double s = 0.0, c = 0.0;
-    for (size_t i = 0; i < n; ++i) {
-        double t = s + x[i];
-        c += (std::fabs(s) >= std::fabs(x[i])) ? (s - t) + x[i] : (x[i] - t) + s;
-        s = t;
-    }
-    return s + c;
-}
-
-fdm_status dev_alloc(fdm_handle* h, void** ptr, size_t bytes) {
-    *ptr = nullptr;
-    cudaError_t e = cudaMalloc(ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *ptr = nullptr;
-        return e == cudaErrorMemoryAllocation ? FDM_ERR_OOM : FDM_ERR_DEVICE;
-    }
-    h->owned.push_back(*ptr);
-    return FDM_OK;
-}
-
-#define CK(x)                                              \
-    do {                                                   \
-        cudaError_t e_ = (x);                              \
-        if (e_ != cudaSuccess) {                           \
-            cudaGetLastError();                            \
-            return FDM_ERR_DEVICE;                         \
-        }                                                  \
-    } while (0)
-
 template <typename T>
-fdm_status upload_twiddles(fdm_handle* h, void* dst, int n) {
+static fdm_status upload_twiddles(void* dst, int n, cudaStream_t s) {
     std::vector<T> tw(2 * (size_t)n);
     for (int m = 0; m < n; ++m) {
         double a = 2.0 * kPi * (double)m / (double)n;
         tw[2 * m] = (T)std::cos(a);
         tw[2 * m + 1] = (T)(-std::sin(a));
     }
-    CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    FDM_CK(cudaStreamSynchronize(s));
     return FDM_OK;
 }
 
 template <typename T>
-fdm_status create_impl(fdm_handle* h) {
-    Dev& d = h->d;
-    const fdm_params& p = d.p;
-    const size_t n = h->n;
+fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gated, bool with_spec2,
+                       cudaStream_t s) {
+    d = Dev{};
+    d.p = p;
+    d.count = count;
+    d.gated = gated;
+    const size_t n = (size_t)p.n1 * p.n2;
     d.geom = geometry<T>(p.n1, p.n2);
     if (d.geom.row_smem > 200 * 1024 || d.geom.col_smem > 200 * 1024) return FDM_ERR_INVALID_ARG;
-    CK(configure_kernels<T>());
+    FDM_CK(configure_kernels<T>());
     fdm_status st;
-    if ((st = dev_alloc(h, &d.phi[0], n * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, &d.phi[1], n * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, &d.tau, n * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, &d.spec, n * sizeof(T)))) return st;   // n1/2 * n2 complex
-    if ((st = dev_alloc(h, &d.spec2, n * sizeof(T)))) return st;
+    const size_t cn = (size_t)count * n;
+    if ((st = A.alloc(&d.phi[0], cn * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.phi[1], cn * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.tau, cn * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.spec, cn * sizeof(T)))) return st;   // n1/2 * n2 complex per instance
+    if (with_spec2 && (st = A.alloc(&d.spec2, n * sizeof(T)))) return st;
     const size_t nk = (size_t)(p.n1 / 2 + 1) * (p.n2 / 2 + 1);
-    if ((st = dev_alloc(h, &d.Kh, nk * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, &d.tw1, (size_t)p.n1 * 2 * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, &d.tw2, (size_t)p.n2 * 2 * sizeof(T)))) return st;
-    if ((st = dev_alloc(h, (void**)&d.row_partials, (size_t)d.geom.row_blocks * sizeof(double)))) return st;
+    if ((st = A.alloc(&d.Kh, nk * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.tw1, (size_t)p.n1 * 2 * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.tw2, (size_t)p.n2 * 2 * sizeof(T)))) return st;
+    if ((st = A.alloc((void**)&d.row_partials, (size_t)count * d.geom.row_blocks * sizeof(double)))) return st;
     d.red_blocks = red_blocks_for(n);
-    if ((st = dev_alloc(h, (void**)&d.red, (size_t)6 * d.red_blocks * sizeof(double)))) return st;
-    if ((st = dev_alloc(h, (void**)&d.sc, sizeof(fdm_dev_scalars)))) return st;
-    CK(cudaMemsetAsync(d.sc, 0, sizeof(fdm_dev_scalars), h->stream));
-    if ((st = upload_twiddles<T>(h, d.tw1, p.n1))) return st;
-    if ((st = upload_twiddles<T>(h, d.tw2, p.n2))) return st;
+    if ((st = A.alloc((void**)&d.red, (size_t)6 * d.red_blocks * sizeof(double)))) return st;
+    if ((st = A.alloc((void**)&d.sc, (size_t)count * sizeof(fdm_dev_scalars)))) return st;
+    FDM_CK(cudaMemsetAsync(d.sc, 0, (size_t)count * sizeof(fdm_dev_scalars), s));
+    FDM_CK(cudaMemsetAsync(d.phi[0], 0, cn * sizeof(T), s));
+    if ((st = upload_twiddles<T>(d.tw1, p.n1, s))) return st;
+    if ((st = upload_twiddles<T>(d.tw2, p.n2, s))) return st;
     // layer weights |chi-hat(k3)|^2, k3 in [0, nz/2] (Sec. 3.2.1 layer of nh voxels)
     std::vector<double> w3((size_t)p.nz / 2 + 1);
     for (int k3 = 0; k3 <= p.nz / 2; ++k3) {
@@ -152,92 +65,112 @@ fdm_status create_impl(fdm_handle* h) {
     }
     void* dw3 = nullptr;
     void* dK64 = nullptr;
-    if ((st = dev_alloc(h, &dw3, w3.size() * sizeof(double)))) return st;
-    if ((st = dev_alloc(h, &dK64, nk * sizeof(double)))) return st;
-    CK(cudaMemcpyAsync(dw3, w3.data(), w3.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if ((st = A.alloc(&dw3, w3.size() * sizeof(double)))) return st;
+    if ((st = A.alloc(&dK64, nk * sizeof(double)))) return st;
+    FDM_CK(cudaMemcpyAsync(dw3, w3.data(), w3.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     const double mu = p.E / (2.0 * (1.0 + p.nu));
-    launch_kernel_table((double*)dK64, p.n1, p.n2, p.nz, p.nh, mu, p.nu, (const double*)dw3, h->stream);
-    CK(cudaGetLastError());
-    launch_convert<T>((const double*)dK64, (T*)d.Kh, nk, 0.0, h->stream);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(h->stream));
-    // release the create-time temporaries
-    for (void* q : {dw3, dK64}) {
-        cudaFree(q);
-        for (size_t i = 0; i < h->owned.size(); ++i)
-            if (h->owned[i] == q) { h->owned.erase(h->owned.begin() + i); break; }
-    }
+    launch_kernel_table((double*)dK64, p.n1, p.n2, p.nz, p.nh, mu, p.nu, (const double*)dw3, s);
+    FDM_CK(cudaGetLastError());
+    launch_convert<T>((const double*)dK64, (T*)d.Kh, nk, 0.0, s);
+    FDM_CK(cudaGetLastError());
+    FDM_CK(cudaStreamSynchronize(s));
+    A.release(dw3);
+    A.release(dK64);
     return FDM_OK;
 }
 
-fdm_status reset_scalars(fdm_handle* h, double mean) {
-    fdm_dev_scalars s;
-    std::memset(&s, 0, sizeof(s));
-    s.phi_ref = h->d.phi_ref_host;
-    s.mean_up13 = mean;
-    host_loading(h->d.p, 0, mean, &s.eps_bar13, &s.sigma_bar13);
-    CK(cudaMemcpyAsync(h->d.sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    h->cur = 0;
-    h->next_phase = 0;
-    h->has_state = true;
-    return FDM_OK;
-}
+template fdm_status build_group<double>(Dev&, Arena&, const fdm_params&, int, int, bool, cudaStream_t);
+template fdm_status build_group<float>(Dev&, Arena&, const fdm_params&, int, int, bool, cudaStream_t);
 
-// upload a host FP64 field into a device buffer of the handle's type (minus offset)
-fdm_status upload_field(fdm_handle* h, void* dst, const double* src, double offset) {
-    if (!h->mixed) {
+fdm_status upload_field(void* dst, const double* src, size_t n, bool mixed, double offset, cudaStream_t s) {
+    if (!mixed) {
         if (offset == 0.0) {
-            CK(cudaMemcpyAsync(dst, src, h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            CK(cudaStreamSynchronize(h->stream));
+            FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, s));
+            FDM_CK(cudaStreamSynchronize(s));
             return FDM_OK;
         }
-        std::vector<double> t(h->n);
-        for (size_t i = 0; i < h->n; ++i) t[i] = src[i] - offset;
-        CK(cudaMemcpyAsync(dst, t.data(), h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        std::vector<double> t(n);
+        for (size_t i = 0; i < n; ++i) t[i] = src[i] - offset;
+        FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        FDM_CK(cudaStreamSynchronize(s));
         return FDM_OK;
     }
-    std::vector<float> t(h->n);
-    for (size_t i = 0; i < h->n; ++i) t[i] = (float)(src[i] - offset);
-    CK(cudaMemcpyAsync(dst, t.data(), h->n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    std::vector<float> t(n);
+    for (size_t i = 0; i < n; ++i) t[i] = (float)(src[i] - offset);
+    FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    FDM_CK(cudaStreamSynchronize(s));
     return FDM_OK;
 }
 
-fdm_status download_field(fdm_handle* h, double* dst, const void* src, double offset) {
-    if (!h->mixed) {
-        CK(cudaMemcpyAsync(dst, src, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+fdm_status download_field(double* dst, const void* src, size_t n, bool mixed, double offset, cudaStream_t s) {
+    if (!mixed) {
+        FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        FDM_CK(cudaStreamSynchronize(s));
         if (offset != 0.0)
-            for (size_t i = 0; i < h->n; ++i) dst[i] += offset;
+            for (size_t i = 0; i < n; ++i) dst[i] += offset;
         return FDM_OK;
     }
-    std::vector<float> t(h->n);
-    CK(cudaMemcpyAsync(t.data(), src, h->n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i < h->n; ++i) dst[i] = (double)t[i] + offset;
+    std::vector<float> t(n);
+    FDM_CK(cudaMemcpyAsync(t.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < n; ++i) dst[i] = (double)t[i] + offset;
     return FDM_OK;
 }
 
-fdm_status read_scalars(fdm_handle* h, fdm_dev_scalars* s) {
-    CK(cudaMemcpyAsync(s, h->d.sc, sizeof(*s), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nsteps, const std::vector<Dev*>& groups,
+                                const std::vector<int>& mixed) {
+    cudaGraph_t graph = nullptr;
+    FDM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nsteps; ++k)
+        for (size_t g = 0; g < groups.size(); ++g) {
+            if (mixed[g]) launch_step<float>(*groups[g], cap);
+            else launch_step<double>(*groups[g], cap);
+        }
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FDM_ERR_DEVICE;
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FDM_ERR_DEVICE;
+    }
     return FDM_OK;
 }
 
-fdm_status fill_info(fdm_handle* h, fdm_step_info* info) {
-    fdm_dev_scalars s;
-    fdm_status st = read_scalars(h, &s);
+fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& mixed) {
+    if (g.one) return FDM_OK;
+    if (!g.capture) FDM_CK(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
+    fdm_status st = capture_steps(&g.one, g.capture, 1, groups, mixed);
     if (st) return st;
-    Dev& d = h->d;
-    const void* phi = d.phi[h->cur];
-    if (h->mixed) launch_alpha_sums<float>(d, (const float*)phi, d.red, d.red_blocks, h->stream);
-    else launch_alpha_sums<double>(d, (const double*)phi, d.red, d.red_blocks, h->stream);
-    CK(cudaGetLastError());
+    return capture_steps(&g.many, g.capture, StepGraphs::kGraphSteps, groups, mixed);
+}
+
+fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s) {
+    while (nsteps >= StepGraphs::kGraphSteps) {
+        FDM_CK(cudaGraphLaunch(g.many, s));
+        nsteps -= StepGraphs::kGraphSteps;
+    }
+    for (; nsteps > 0; --nsteps) FDM_CK(cudaGraphLaunch(g.one, s));
+    return FDM_OK;
+}
+
+// FP64 sums over the staggered Nye components of one instance's current state (info)
+fdm_status instance_info(const Dev& d, int inst, bool mixed, cudaStream_t stream, fdm_step_info* info) {
+    fdm_dev_scalars s;
+    FDM_CK(cudaMemcpyAsync(&s, d.sc + inst, sizeof(s), cudaMemcpyDeviceToHost, stream));
+    FDM_CK(cudaStreamSynchronize(stream));
+    const size_t n = (size_t)d.p.n1 * d.p.n2;
+    const size_t e = mixed ? sizeof(float) : sizeof(double);
+    const void* phi = (const char*)d.phi[s.cur] + (size_t)inst * n * e;
+    if (mixed) launch_alpha_sums<float>(d, (const float*)phi, d.red, d.red_blocks, stream);
+    else launch_alpha_sums<double>(d, (const double*)phi, d.red, d.red_blocks, stream);
+    FDM_CK(cudaGetLastError());
     std::vector<double> part((size_t)6 * d.red_blocks);
-    CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    FDM_CK(cudaStreamSynchronize(stream));
     double sums[6];
     std::vector<double> col(d.red_blocks);
     for (int q = 0; q < 6; ++q) {
@@ -249,7 +182,7 @@ fdm_status fill_info(fdm_handle* h, fdm_step_info* info) {
     info->t = s.t;
     info->dt = s.dt;
     info->max_abs_v0 = s.max_abs_v0;
-    info->mean_up13 = s.phi_ref + sums[5] / (double)h->n;
+    info->mean_up13 = s.phi_ref + sums[5] / (double)n;
     host_loading(d.p, s.step, info->mean_up13, &info->eps_bar13, &info->sigma_bar13);
     info->sum_a12_pos = sums[0];
     info->sum_a12_neg = sums[1];
@@ -260,11 +193,50 @@ fdm_status fill_info(fdm_handle* h, fdm_step_info* info) {
     return FDM_OK;
 }
 
+}  // namespace fdm
+
+using namespace fdm;
+
+struct fdm_handle {
+    Dev d;
+    Arena arena;
+    StepGraphs graphs;
+    cudaStream_t stream;
+    int next_phase;          // next kernel of a partially enqueued step (0: none pending)
+    bool has_state;
+    bool mixed;
+    size_t n;                // n1 * n2
+    void* rd[4];             // readout buffers (type T, n each), allocated on first use
+};
+
+namespace {
+
+fdm_status reset_scalars(fdm_handle* h, double mean) {
+    fdm_dev_scalars s;
+    std::memset(&s, 0, sizeof(s));
+    s.phi_ref = h->d.phi_ref_host;
+    s.mean_up13 = mean;
+    s.cur = 0;
+    s.steps_left = -1;
+    host_loading(h->d.p, 0, mean, &s.eps_bar13, &s.sigma_bar13);
+    FDM_CK(cudaMemcpyAsync(h->d.sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    h->next_phase = 0;
+    h->has_state = true;
+    return FDM_OK;
+}
+
+fdm_status read_scalars(fdm_handle* h, fdm_dev_scalars* s) {
+    FDM_CK(cudaMemcpyAsync(s, h->d.sc, sizeof(*s), cudaMemcpyDeviceToHost, h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    return FDM_OK;
+}
+
 template <typename T>
 fdm_status ensure_readout(fdm_handle* h) {
     for (int i = 0; i < 4; ++i)
         if (!h->rd[i]) {
-            fdm_status st = dev_alloc(h, &h->rd[i], h->n * sizeof(T));
+            fdm_status st = h->arena.alloc(&h->rd[i], h->n * sizeof(T));
             if (st) return st;
         }
     return FDM_OK;
@@ -274,28 +246,31 @@ template <typename T>
 fdm_status read_fields_impl(fdm_handle* h, uint32_t mask, double* up13, double* a11, double* a12, double* tau,
                             double* v1, double* v2) {
     Dev& d = h->d;
-    const T* phi = (const T*)d.phi[h->cur];
+    fdm_dev_scalars sc;
     fdm_status st;
+    if ((st = read_scalars(h, &sc))) return st;
+    const T* phi = (const T*)d.phi[sc.cur];
+    const bool mx = h->mixed;
     if (mask & FDM_FIELD_UP13)
-        if ((st = download_field(h, up13, phi, d.phi_ref_host))) return st;
+        if ((st = download_field(up13, phi, h->n, mx, d.phi_ref_host, h->stream))) return st;
     if (mask & FDM_FIELD_TAU13)
-        if ((st = download_field(h, tau, d.tau, 0.0))) return st;
+        if ((st = download_field(tau, d.tau, h->n, mx, 0.0, h->stream))) return st;
     if (mask & (FDM_FIELD_ALPHA11 | FDM_FIELD_ALPHA12 | FDM_FIELD_V1 | FDM_FIELD_V2)) {
         if ((st = ensure_readout<T>(h))) return st;
         launch_alpha<T>(d, phi, (T*)h->rd[0], (T*)h->rd[1], h->stream);
-        CK(cudaGetLastError());
+        FDM_CK(cudaGetLastError());
         if (mask & FDM_FIELD_ALPHA11)
-            if ((st = download_field(h, a11, h->rd[0], 0.0))) return st;
+            if ((st = download_field(a11, h->rd[0], h->n, mx, 0.0, h->stream))) return st;
         if (mask & FDM_FIELD_ALPHA12)
-            if ((st = download_field(h, a12, h->rd[1], 0.0))) return st;
+            if ((st = download_field(a12, h->rd[1], h->n, mx, 0.0, h->stream))) return st;
         if (mask & (FDM_FIELD_V1 | FDM_FIELD_V2)) {
             launch_velocity<T>(d, (const T*)h->rd[0], (const T*)h->rd[1], (const T*)d.tau, phi, (T*)h->rd[2],
                                (T*)h->rd[3], h->stream);
-            CK(cudaGetLastError());
+            FDM_CK(cudaGetLastError());
             if (mask & FDM_FIELD_V1)
-                if ((st = download_field(h, v1, h->rd[2], 0.0))) return st;
+                if ((st = download_field(v1, h->rd[2], h->n, mx, 0.0, h->stream))) return st;
             if (mask & FDM_FIELD_V2)
-                if ((st = download_field(h, v2, h->rd[3], 0.0))) return st;
+                if ((st = download_field(v2, h->rd[3], h->n, mx, 0.0, h->stream))) return st;
         }
     }
     return FDM_OK;
@@ -327,8 +302,8 @@ void fdm_default_params(fdm_params* p) {
 }
 
 size_t fdm_device_bytes(const fdm_params* p) {
-    if (!valid(p)) return 0;
-    size_t n = (size_t)p->n1 * p->n2, e = elt(p);
+    if (!params_valid(p)) return 0;
+    size_t n = (size_t)p->n1 * p->n2, e = elt_size(p);
     size_t nk = (size_t)(p->n1 / 2 + 1) * (p->n2 / 2 + 1);
     return 5 * n * e + nk * e + (size_t)(p->n1 + p->n2) * 2 * e + 64 * 1024;
 }
@@ -336,22 +311,23 @@ size_t fdm_device_bytes(const fdm_params* p) {
 fdm_status fdm_create(const fdm_params* p, void* stream, fdm_handle** out) {
     if (!out) return FDM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!valid(p)) return FDM_ERR_INVALID_ARG;
+    if (!params_valid(p)) return FDM_ERR_INVALID_ARG;
     fdm_handle* h = new (std::nothrow) fdm_handle();
     if (!h) return FDM_ERR_OOM;
-    h->d.p = *p;
-    if (h->d.p.nz == 0) h->d.p.nz = p->n1;
+    fdm_params q = *p;
+    if (q.nz == 0) q.nz = p->n1;
     h->stream = (cudaStream_t)stream;
-    h->cur = 0;
+    h->next_phase = 0;
     h->has_state = false;
     h->mixed = p->precision == FDM_MIXED;
     h->n = (size_t)p->n1 * p->n2;
-    h->d.phi_ref_host = 0.0;
-    fdm_status st = h->mixed ? create_impl<float>(h) : create_impl<double>(h);
+    fdm_status st = h->mixed ? build_group<float>(h->d, h->arena, q, 1, 0, true, h->stream)
+                             : build_group<double>(h->d, h->arena, q, 1, 0, true, h->stream);
     if (st != FDM_OK) {
         fdm_destroy(h);
         return st;
     }
+    h->d.phi_ref_host = 0.0;
     *out = h;
     return FDM_OK;
 }
@@ -360,8 +336,9 @@ fdm_status fdm_set_plastic_distortion(fdm_handle* h, const double* up13) {
     if (!h || !up13) return FDM_ERR_INVALID_ARG;
     double mean = ksum(up13, h->n) / (double)h->n;
     if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
+    FDM_CK(cudaStreamSynchronize(h->stream));
     h->d.phi_ref_host = h->mixed ? mean : 0.0;
-    fdm_status st = upload_field(h, h->d.phi[0], up13, h->d.phi_ref_host);
+    fdm_status st = upload_field(h->d.phi[0], up13, h->n, h->mixed, h->d.phi_ref_host, h->stream);
     if (st) return st;
     return reset_scalars(h, mean);
 }
@@ -376,11 +353,12 @@ fdm_status fdm_set_density(fdm_handle* h, const double* a11, const double* a12, 
         amax = std::fmax(amax, std::fmax(std::fabs(a11[i]), std::fabs(a12[i])));
     }
     if (std::fabs(m11) > 1e-9 * amax || std::fabs(m12) > 1e-9 * amax) return FDM_ERR_NET_BURGERS;
+    FDM_CK(cudaStreamSynchronize(h->stream));
     Dev& d = h->d;
     fdm_status st;
     // stage alpha in the two state buffers (the old state is being replaced)
-    if ((st = upload_field(h, d.phi[0], a11, 0.0))) return st;
-    if ((st = upload_field(h, d.phi[1], a12, 0.0))) return st;
+    if ((st = upload_field(d.phi[0], a11, n, h->mixed, 0.0, h->stream))) return st;
+    if ((st = upload_field(d.phi[1], a12, n, h->mixed, 0.0, h->stream))) return st;
     double phi_ref = h->mixed ? mean_up13 : 0.0;
     const int nblk = d.red_blocks;
     if (h->mixed)
@@ -389,10 +367,10 @@ fdm_status fdm_set_density(fdm_handle* h, const double* a11, const double* a12, 
     else
         launch_curl_inverse<double>(d, (const double*)d.phi[0], (const double*)d.phi[1], (double*)d.phi[0],
                                     mean_up13, phi_ref, d.red, nblk, h->stream);
-    CK(cudaGetLastError());
+    FDM_CK(cudaGetLastError());
     std::vector<double> part((size_t)2 * nblk);
-    CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
     double num = 0.0, den = 0.0;
     for (int b = 0; b < nblk; ++b) { num += part[2 * b]; den += part[2 * b + 1]; }
     double res = den > 0.0 ? std::sqrt(num / den) : 0.0;
@@ -410,8 +388,8 @@ fdm_status fdm_set_clock(fdm_handle* h, int64_t step, double t) {
     if (st) return st;
     s.step = step;
     s.t = t;
-    CK(cudaMemcpyAsync(h->d.sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemcpyAsync(h->d.sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
     return FDM_OK;
 }
 
@@ -419,42 +397,33 @@ fdm_status fdm_static_solve(fdm_handle* h) {
     if (!h) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
     Dev& d = h->d;
-    if (h->mixed) launch_static<float>(d, (const float*)d.phi[h->cur], h->stream);
-    else launch_static<double>(d, (const double*)d.phi[h->cur], h->stream);
-    CK(cudaGetLastError());
+    if (h->mixed) launch_static<float>(d, h->stream);
+    else launch_static<double>(d, h->stream);
+    FDM_CK(cudaGetLastError());
     // the stencil kernel normally clears the running max; no step follows here
-    CK(cudaMemsetAsync(&d.sc->vmax_bits, 0, sizeof(unsigned long long), h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemsetAsync(&d.sc->vmax_bits, 0, sizeof(unsigned long long), h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
     return FDM_OK;
 }
 
 fdm_status fdm_enqueue_steps(fdm_handle* h, int32_t nsteps) {
     if (!h || nsteps < 0) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
-    Dev& d = h->d;
-    for (int32_t i = 0; i < nsteps; ++i) {
-        int nx = h->cur ^ 1;
-        if (h->mixed) launch_step<float>(d, (const float*)d.phi[h->cur], (float*)d.phi[nx], h->stream);
-        else launch_step<double>(d, (const double*)d.phi[h->cur], (double*)d.phi[nx], h->stream);
-        h->cur = nx;
-    }
-    CK(cudaGetLastError());
-    return FDM_OK;
+    if (nsteps == 0) return FDM_OK;
+    std::vector<Dev*> groups{&h->d};
+    std::vector<int> mixed{h->mixed ? 1 : 0};
+    fdm_status st = build_step_graphs(h->graphs, groups, mixed);
+    if (st) return st;
+    return replay_steps(h->graphs, nsteps, h->stream);
 }
 
 fdm_status fdm_enqueue_phase(fdm_handle* h, int32_t phase) {
     if (!h || phase < 0 || phase >= kKernelsPerStep) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || phase != h->next_phase) return FDM_ERR_STATE;
-    Dev& d = h->d;
-    int nx = h->cur ^ 1;
-    if (h->mixed) launch_phase<float>(d, phase, (const float*)d.phi[h->cur], (float*)d.phi[nx], h->stream);
-    else launch_phase<double>(d, phase, (const double*)d.phi[h->cur], (double*)d.phi[nx], h->stream);
-    CK(cudaGetLastError());
-    h->next_phase = phase + 1;
-    if (h->next_phase == kKernelsPerStep) {
-        h->next_phase = 0;
-        h->cur = nx;
-    }
+    if (h->mixed) launch_phase<float>(h->d, phase, h->stream);
+    else launch_phase<double>(h->d, phase, h->stream);
+    FDM_CK(cudaGetLastError());
+    h->next_phase = (phase + 1) % kKernelsPerStep;
     return FDM_OK;
 }
 
@@ -471,12 +440,10 @@ fdm_status fdm_step(fdm_handle* h, int32_t nsteps, fdm_step_info* info) {
     fdm_status st = fdm_enqueue_steps(h, nsteps);
     if (st) return st;
     if (info) {
-        if ((st = fill_info(h, info))) return st;
+        if ((st = instance_info(h->d, 0, h->mixed, h->stream, info))) return st;
         return info->status ? (fdm_status)info->status : FDM_OK;
     }
-    fdm_dev_scalars s;
-    if ((st = read_scalars(h, &s))) return st;
-    return s.status ? (fdm_status)s.status : FDM_OK;
+    return fdm_sync(h);
 }
 
 fdm_status fdm_read_fields(fdm_handle* h, uint32_t mask, double* up13, double* a11, double* a12, double* tau,
@@ -495,7 +462,7 @@ fdm_status fdm_read_fields(fdm_handle* h, uint32_t mask, double* up13, double* a
 fdm_status fdm_get_info(fdm_handle* h, fdm_step_info* info) {
     if (!h || !info) return FDM_ERR_INVALID_ARG;
     if (!h->has_state) return FDM_ERR_STATE;
-    return fill_info(h, info);
+    return instance_info(h->d, 0, h->mixed, h->stream, info);
 }
 
 int32_t fdm_kernels_per_step(const fdm_handle* h) {
@@ -507,7 +474,8 @@ void fdm_destroy(fdm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    for (void* q : h->owned) cudaFree(q);
+    h->graphs.destroy();
+    h->arena.free_all();
     delete h;
 }
 

@@ -1,0 +1,137 @@
+// fdm_host.h -- host-side helpers shared by the single-instance and batch C ABIs:
+// parameter validation, the loading law (Sec. 5.1), compensated sums, device buffers of a
+// group, host<->device field copies, CUDA graphs of whole steps.
+#pragma once
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fdm_internal.h"
+
+namespace fdm {
+
+#define FDM_CK(x)                          \
+    do {                                   \
+        cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) {           \
+            cudaGetLastError();            \
+            return FDM_ERR_DEVICE;         \
+        }                                  \
+    } while (0)
+
+inline bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+inline bool params_valid(const fdm_params* p) {
+    if (!p) return false;
+    if (!pow2_in(p->n1, 16, 4096) || !pow2_in(p->n2, 16, 4096)) return false;
+    int nz = p->nz == 0 ? p->n1 : p->nz;
+    if (nz < 1 || nz > 65536 || p->nh < 1 || p->nh > nz) return false;
+    if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return false;
+    if (!(p->E > 0.0) || !(p->nu > -1.0 && p->nu < 0.5)) return false;
+    if (p->velocity_mode != FDM_V_PRESCRIBED && p->velocity_mode != FDM_V_STRESS) return false;
+    if (!std::isfinite(p->v0) || !std::isfinite(p->mobility) || !std::isfinite(p->tau_y)) return false;
+    if (p->tau_y != 0.0 && !(p->beta > 0.0)) return false;
+    if (!(p->theta >= 1.0 && p->theta <= 2.0)) return false;
+    if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return false;
+    if (!std::isfinite(p->dt_max)) return false;
+    if (p->loading_mode < FDM_LOAD_STRESS || p->loading_mode > FDM_LOAD_ZERO_MEAN_STRESS) return false;
+    if (!std::isfinite(p->sigma_bar13) || !std::isfinite(p->eps_bar13_0) || !std::isfinite(p->eps_bar13_rate))
+        return false;
+    if (p->time_level != FDM_T_MIDPOINT && p->time_level != FDM_T_LITERAL) return false;
+    if (p->precision != FDM_FP64 && p->precision != FDM_MIXED) return false;
+    return true;
+}
+
+inline size_t elt_size(const fdm_params* p) { return p->precision == FDM_MIXED ? sizeof(float) : sizeof(double); }
+
+inline int red_blocks_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+// macroscopic loading state (Sec. 3.1.2 sigma-hat(0); Sec. 5.1), same law as the kernels
+inline void host_loading(const fdm_params& p, long long step, double mean, double* eps, double* sig) {
+    const double mu = p.E / (2.0 * (1.0 + p.nu));
+    const double frac = (double)p.nh / (double)p.nz;
+    if (p.loading_mode == FDM_LOAD_STRESS) {
+        *sig = p.sigma_bar13;
+        *eps = (p.sigma_bar13 + mu * frac * mean) / (2.0 * mu);
+    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP) {
+        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (double)step;
+        *sig = 2.0 * mu * (*eps) - mu * frac * mean;
+    } else {
+        *eps = 0.5 * frac * mean;
+        *sig = 0.0;
+    }
+}
+
+// Neumaier sum of host values
+inline double ksum(const double* x, size_t n) {
+    double s = 0.0, c = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        double t = s + x[i];
+        c += (std::fabs(s) >= std::fabs(x[i])) ? (s - t) + x[i] : (x[i] - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+// Device memory owned by one handle or batch; freed together.
+struct Arena {
+    std::vector<void*> owned;
+    fdm_status alloc(void** ptr, size_t bytes) {
+        *ptr = nullptr;
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return e == cudaErrorMemoryAllocation ? FDM_ERR_OOM : FDM_ERR_DEVICE;
+        }
+        owned.push_back(*ptr);
+        return FDM_OK;
+    }
+    void release(void* q) {
+        for (size_t i = 0; i < owned.size(); ++i)
+            if (owned[i] == q) {
+                cudaFree(q);
+                owned.erase(owned.begin() + (long)i);
+                return;
+            }
+    }
+    void free_all() {
+        for (void* q : owned) cudaFree(q);
+        owned.clear();
+    }
+};
+
+// Allocates and initialises the buffers of a group of `count` instances with parameters p
+// (nz resolved): state, spectra, the layer Green kernel K (Sec. 3.1.2/3.2.1) and twiddles.
+// with_spec2: second spectrum for field readouts (single instance).
+template <typename T>
+fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gated, bool with_spec2, cudaStream_t s);
+
+// Uploads a host FP64 field into a device buffer of type T (minus offset) / downloads it.
+fdm_status upload_field(void* dst, const double* src, size_t n, bool mixed, double offset, cudaStream_t s);
+fdm_status download_field(double* dst, const void* src, size_t n, bool mixed, double offset, cudaStream_t s);
+
+// A step of every group as CUDA graphs (1 and kGraphSteps steps), replayed on a stream.
+struct StepGraphs {
+    cudaGraphExec_t one = nullptr, many = nullptr;
+    cudaStream_t capture = nullptr;
+    static constexpr int kGraphSteps = 8;
+    void destroy() {
+        if (one) cudaGraphExecDestroy(one);
+        if (many) cudaGraphExecDestroy(many);
+        if (capture) cudaStreamDestroy(capture);
+        one = many = nullptr;
+        capture = nullptr;
+    }
+};
+
+fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& mixed);
+// scalars and FP64 Nye sums of instance `inst` of a group (synchronises `stream`)
+fdm_status instance_info(const Dev& d, int inst, bool mixed, cudaStream_t stream, fdm_step_info* info);
+fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s);
+
+}  // namespace fdm

@@ -17,6 +17,9 @@ struct fdm_dev_scalars {
     double t, dt, max_abs_v0;
     double mean_up13, eps_bar13, sigma_bar13;  // state at the start of the current step
     double phi_ref;                // mixed precision: U13 = phi_ref + stored value
+    int cur;                       // state buffer holding U13 (0 or 1); flipped by each step
+    int pad_;
+    long long steps_left;          // gated (batched) launches: steps this instance may still take
 };
 
 struct LaunchGeom {
@@ -26,28 +29,33 @@ struct LaunchGeom {
     int row_blocks, col_blocks;
 };
 
+// One group of `count` instances with identical parameters.  Every buffer holds `count`
+// consecutive instances (instance i at offset i * n, spectra at i * n/2 complex).
 struct Dev {
     fdm_params p;          // validated copy (nz resolved)
     LaunchGeom geom;
-    void* phi[2];          // double-buffered U13 (type T)
+    int count;             // instances in the group
+    int gated;             // step launches honour each instance's steps_left (batches)
+    void* phi[2];          // double-buffered U13 (type T); the current one is sc[i].cur
     void* tau;             // T
-    void* spec;            // cpx<T> [n1/2][n2]
-    void* spec2;           // cpx<T> [n1/2][n2]
+    void* spec;            // cpx<T> [n1/2][n2] per instance
+    void* spec2;           // cpx<T> [n1/2][n2] (single instance only; readouts)
     void* Kh;              // T [n1/2+1][n2/2+1]
     void* tw1;             // cpx<T> [n1]
     void* tw2;             // cpx<T> [n2]
-    double* row_partials;  // [row_blocks]
+    double* row_partials;  // [count][row_blocks]
     double* red;           // reduction partials [6 * red_blocks]
     int red_blocks;
-    fdm_dev_scalars* sc;
-    double phi_ref_host;
+    fdm_dev_scalars* sc;   // [count]
+    double phi_ref_host;   // single instance: host copy of sc[0].phi_ref
 };
 
 template <typename T> LaunchGeom geometry(int n1, int n2);
 template <typename T> cudaError_t configure_kernels();
-template <typename T> void launch_step(const Dev& d, const T* phi, T* phi_next, cudaStream_t s);
-template <typename T> void launch_phase(const Dev& d, int phase, const T* phi, T* phi_next, cudaStream_t s);
-template <typename T> void launch_static(const Dev& d, const T* phi, cudaStream_t s);
+// step launches read U13 from phi[sc[i].cur] of every instance and write the other buffer
+template <typename T> void launch_step(const Dev& d, cudaStream_t s);
+template <typename T> void launch_phase(const Dev& d, int phase, cudaStream_t s);
+template <typename T> void launch_static(const Dev& d, cudaStream_t s);
 template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);
 template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,

@@ -63,15 +63,45 @@ __device__ __forceinline__ void loading_state(const fdm_params& p, long long ste
 
 constexpr int kFftThreads = 512;  // threads per block of the FFT kernels
 
+// Instance addressing of the step kernels: a launch covers `count` instances (grid y, or z
+// for the stencil).  sc == nullptr marks a set-up launch (one instance, buffer 0, always
+// runs).  Otherwise instance i reads U13 from buffer sc[i].cur, and with gating on it runs
+// only while its step budget sc[i].steps_left is non-zero.  Read by thread 0 only and
+// broadcast, so that every thread of a block sees the same values.
+struct InstCtl {
+    fdm_dev_scalars* sc;
+    int gated;
+};
+
+__device__ __forceinline__ void inst_state(const InstCtl& c, int inst, int* run, int* cur) {
+    int r = 1, k = 0;
+    if (c.sc) {
+        const fdm_dev_scalars* si = c.sc + inst;
+        k = si->cur;
+        if (c.gated && si->steps_left == 0) r = 0;
+    }
+    *run = r;
+    *cur = k;
+}
+
 // ------------------------------------------------------------------ row forward (R2C)
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional per-block FP64 sum of
 // the loaded values (for <U13>).
 template <typename T>
-__global__ void __launch_bounds__(512) row_forward_kernel(const T* __restrict__ src, cpx<T>* __restrict__ spec,
+__global__ void __launch_bounds__(512) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1,
-                                                          double* __restrict__ row_partials) {
+                                                          double* row_partials, InstCtl ctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_run, s_cur;
+    const int inst = blockIdx.y;
+    if (threadIdx.x == 0) inst_state(ctl, inst, &s_run, &s_cur);
+    __syncthreads();
+    if (!s_run) return;
+    const size_t nn = (size_t)n1 * n2;
+    const T* src = (s_cur ? src1 : src0) + inst * nn;
+    spec += inst * (nn / 2);
+    if (row_partials) row_partials += (size_t)inst * gridDim.x;
     const int L = n1 >> 1;
     const int ld = L + 1;  // padded sequence stride (bank spread for the transposed store)
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -136,7 +166,8 @@ struct ColArgs {
     int mode;
     const double* row_partials;  // COL_K: per-row-block sums of U13 (nparts entries)
     int nparts;
-    fdm_dev_scalars* sc;         // COL_K: scalars (block 0 writes mean/eps/sigma)
+    fdm_dev_scalars* sc;         // COL_K: scalars of instance 0 (block 0 writes mean/eps/sigma)
+    int gated;                   // COL_K: honour the instances' step budgets
     T scl;                       // 1 / (n1 n2)
     T xi1_unit, xi2_unit;        // 2 pi / (n dx): xi = k~ * unit
 };
@@ -170,6 +201,19 @@ __global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>*
     cpx<T>* B = A + (size_t)C * ld;
     __shared__ double s_sigma;
     __shared__ double s_red[32];
+    __shared__ int s_run, s_cur;
+    const int inst = blockIdx.y;
+    if (threadIdx.x == 0) {
+        InstCtl ctl{a.mode == COL_K ? a.sc : nullptr, a.gated};
+        inst_state(ctl, inst, &s_run, &s_cur);
+    }
+    __syncthreads();
+    if (!s_run) return;
+    const size_t half_n = (size_t)n1 * n2 / 2;
+    in += inst * half_n;
+    out += inst * half_n;
+    fdm_dev_scalars* sci = a.sc ? a.sc + inst : nullptr;
+    const double* parts = a.row_partials ? a.row_partials + (size_t)inst * a.nparts : nullptr;
     const int kx0 = blockIdx.x * C;
     const cpx<T>* src = in + (size_t)kx0 * n2;
     {
@@ -188,19 +232,19 @@ __global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>*
         // <U13> from the row-block sums (fixed order, compensated per thread), then the
         // loading state of this step (Sec. 5.1)
         double s = 0.0, c = 0.0;
-        for (int i = threadIdx.x; a.row_partials && i < a.nparts; i += blockDim.x) {
-            double x = a.row_partials[i], t = s + x;
+        for (int i = threadIdx.x; parts && i < a.nparts; i += blockDim.x) {
+            double x = parts[i], t = s + x;
             c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
             s = t;
         }
         double tot = block_sum(s + c, s_red);
         if (threadIdx.x == 0) {
-            double mean = a.row_partials ? a.sc->phi_ref + tot / ((double)n1 * (double)n2) : a.sc->mean_up13;
+            double mean = parts ? sci->phi_ref + tot / ((double)n1 * (double)n2) : sci->mean_up13;
             double eps, sig;
-            loading_state(a.p, a.sc->step, mean, &eps, &sig);
-            a.sc->mean_up13 = mean;
-            a.sc->eps_bar13 = eps;
-            a.sc->sigma_bar13 = sig;
+            loading_state(a.p, sci->step, mean, &eps, &sig);
+            sci->mean_up13 = mean;
+            sci->eps_bar13 = eps;
+            sci->sigma_bar13 = sig;
             s_sigma = sig;
         }
     }
@@ -275,13 +319,15 @@ template <typename T>
 struct RowArgs {
     VelLaw<T> vel;
     int mode;
-    const void* phi;           // ROW_TAU with tau_y != 0: current U13 (type T)
-    fdm_dev_scalars* sc;
+    const void* phi0;          // ROW_TAU: the two state buffers (U13 is needed for friction)
+    const void* phi1;
+    fdm_dev_scalars* sc;       // ROW_TAU: scalars of instance 0
+    int gated;
     T offset;                  // ROW_PLAIN: added to every output value
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* __restrict__ spec, T* __restrict__ dst,
+__global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* spec, T* dst,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1, RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -290,6 +336,18 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* __restri
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* B = A + (size_t)R * ld;
     double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
+    __shared__ int s_run, s_cur;
+    const int inst = blockIdx.y;
+    if (threadIdx.x == 0) {
+        InstCtl ctl{a.mode == ROW_TAU ? a.sc : nullptr, a.gated};
+        inst_state(ctl, inst, &s_run, &s_cur);
+    }
+    __syncthreads();
+    if (!s_run) return;
+    const size_t nn = (size_t)n1 * n2;
+    spec += inst * (nn / 2);
+    dst += inst * nn;
+    fdm_dev_scalars* sci = (a.mode == ROW_TAU) ? a.sc + inst : nullptr;
     const int y0 = blockIdx.x * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     {
@@ -318,8 +376,9 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* __restri
     cpx<T>* z = smem_fft(A, B, L, R, ld, +1, tw1, n1);
     T vmax = T(0);
     bool bad = false;
-    const T* up = reinterpret_cast<const T*>(a.phi);
-    const double phi_ref = (a.sc && a.vel.friction) ? a.sc->phi_ref : 0.0;
+    const T* up = reinterpret_cast<const T*>(s_cur ? a.phi1 : a.phi0);
+    if (up) up += inst * nn;
+    const double phi_ref = (sci && a.vel.friction) ? sci->phi_ref : 0.0;
     const bool need_up = a.vel.friction != 0;
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
         int r = e >> lL, m = e & (L - 1);
@@ -346,7 +405,7 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* __restri
             unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
             bits = other > bits ? other : bits;
         }
-        if ((threadIdx.x & 31) == 0) atomicMax(&a.sc->vmax_bits, bits);
+        if ((threadIdx.x & 31) == 0) atomicMax(&sci->vmax_bits, bits);
     }
     (void)red;
 }
@@ -360,7 +419,8 @@ struct KnpArgs {
     double cfl, dx, dt_max;  // time-step rule (FP64)
     T h, theta;
     int time_level;
-    fdm_dev_scalars* sc;
+    fdm_dev_scalars* sc;     // scalars of instance 0
+    int gated;
 };
 
 // dt from the CFL rule |v0|max dt / dx = CFL (Sec. 4.3, Sec. 5.2), in FP64
@@ -376,39 +436,57 @@ __device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, dou
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* __restrict__ phi, const T* __restrict__ tau,
-                                                           T* __restrict__ out, int n1, int n2, KnpArgs<T> a) {
+__global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* phi0, const T* phi1, const T* __restrict__ tau0,
+                                                           int n1, int n2, KnpArgs<T> a) {
     __shared__ T tile[TY + 4][TX + 4];
     __shared__ T s_dt;
+    __shared__ int s_run, s_cur;
+    const int inst = blockIdx.z;
     const int tx = blockDim.x;  // TX, or n1 when n1 < TX
     const int bx = blockIdx.x * tx, by = blockIdx.y * TY;
     const int tid = threadIdx.y * tx + threadIdx.x;
+    fdm_dev_scalars* sc = a.sc + inst;
+    if (tid == 0) {
+        InstCtl ctl{a.sc, a.gated};
+        int run, cur;
+        inst_state(ctl, inst, &run, &cur);
+        s_run = run;
+        s_cur = cur;
+        if (run) {
+            // dt of this step from the max |v0| reduced by the previous kernel; the last block
+            // of this instance to read it advances the clock, flips the state buffer and clears
+            // the running max (every other block has read them by then: each reads before its
+            // fenced counter increment)
+            const double vmax = __longlong_as_double((long long)sc->vmax_bits);
+            const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
+            s_dt = T(dtd);
+            __threadfence();
+            const unsigned int total = gridDim.x * gridDim.y;
+            if (atomicAdd(&sc->done_count, 1u) == total - 1) {
+                __threadfence();
+                sc->step += 1;
+                sc->t += dtd;
+                sc->dt = dtd;
+                sc->max_abs_v0 = vmax;
+                if (!(dtd == dtd) || !(vmax == vmax) || isinf(dtd)) sc->status = FDM_ERR_NONFINITE;
+                sc->vmax_bits = 0ull;
+                sc->done_count = 0u;
+                sc->cur = cur ^ 1;
+                if (a.gated && sc->steps_left > 0) sc->steps_left -= 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_run) return;
+    const size_t nn = (size_t)n1 * n2;
+    const T* phi = (s_cur ? phi1 : phi0) + inst * nn;
+    T* out = const_cast<T*>(s_cur ? phi0 : phi1) + inst * nn;
+    const T* tau = tau0 + inst * nn;
     for (int ly = threadIdx.y; ly < TY + 4; ly += TY) {
         const int gy = (by + ly - 2) & (n2 - 1);
         for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
             const int gx = (bx + lx - 2) & (n1 - 1);
             tile[ly][lx] = phi[(size_t)gy * n1 + gx];
-        }
-    }
-    fdm_dev_scalars* sc = a.sc;
-    if (tid == 0) {
-        // dt of this step from the max |v0| reduced by the previous kernel; the last block to
-        // read it advances the clock and clears the running max for the next step (every
-        // other block has read it by then: each reads before its fenced counter increment)
-        const double vmax = __longlong_as_double((long long)sc->vmax_bits);
-        const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
-        s_dt = T(dtd);
-        __threadfence();
-        const unsigned int total = gridDim.x * gridDim.y;
-        if (atomicAdd(&sc->done_count, 1u) == total - 1) {
-            __threadfence();
-            sc->step += 1;
-            sc->t += dtd;
-            sc->dt = dtd;
-            sc->max_abs_v0 = vmax;
-            if (!(dtd == dtd) || !(vmax == vmax) || isinf(dtd)) sc->status = FDM_ERR_NONFINITE;
-            sc->vmax_bits = 0ull;
-            sc->done_count = 0u;
         }
     }
     __syncthreads();
@@ -594,14 +672,16 @@ cudaError_t configure_kernels() {
 }
 
 template <typename T>
-void launch_row_forward(const Dev& d, const T* src, cpx<T>* spec, double* partials, cudaStream_t s) {
+void launch_row_forward(const Dev& d, const T* src0, const T* src1, cpx<T>* spec, double* partials, InstCtl ctl,
+                        int count, cudaStream_t s) {
     const LaunchGeom& g = d.geom;
-    row_forward_kernel<T><<<g.row_blocks, kFftThreads, g.row_smem, s>>>(src, spec, d.p.n1, d.p.n2, g.R,
-                                                                (const cpx<T>*)d.tw1, partials);
+    dim3 grid(g.row_blocks, count);
+    row_forward_kernel<T><<<grid, kFftThreads, g.row_smem, s>>>(src0, src1, spec, d.p.n1, d.p.n2, g.R,
+                                                                (const cpx<T>*)d.tw1, partials, ctl);
 }
 
 template <typename T>
-void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, cudaStream_t s) {
+void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, int count, cudaStream_t s) {
     const LaunchGeom& g = d.geom;
     ColArgs<T> a;
     a.p = d.p;
@@ -609,29 +689,34 @@ void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with
     a.row_partials = with_mean ? d.row_partials : nullptr;
     a.nparts = g.row_blocks;
     a.sc = d.sc;
+    a.gated = d.gated;
     a.scl = T(1.0 / ((double)d.p.n1 * (double)d.p.n2));
     a.xi1_unit = T(6.283185307179586476925286766559 / ((double)d.p.n1 * d.p.dx));
     a.xi2_unit = T(6.283185307179586476925286766559 / ((double)d.p.n2 * d.p.dx));
-    col_pass_kernel<T><<<g.col_blocks, kFftThreads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
+    dim3 grid(g.col_blocks, count);
+    col_pass_kernel<T><<<grid, kFftThreads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
                                                              (const cpx<T>*)d.tw2, (const T*)d.Kh, a);
 }
 
 template <typename T>
-void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, const T* phi, double offset,
+void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, double offset, int count,
                         cudaStream_t s) {
     const LaunchGeom& g = d.geom;
     RowArgs<T> a;
     a.vel = make_vel<T>(d.p);
     a.mode = mode;
-    a.phi = phi;
+    a.phi0 = d.phi[0];
+    a.phi1 = d.phi[1];
     a.sc = d.sc;
+    a.gated = d.gated;
     a.offset = T(offset);
-    row_inverse_kernel<T><<<g.row_blocks, kFftThreads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
+    dim3 grid(g.row_blocks, count);
+    row_inverse_kernel<T><<<grid, kFftThreads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
                                                                 (const cpx<T>*)d.tw1, a);
 }
 
 template <typename T>
-void launch_knp(const Dev& d, const T* phi, const T* tau, T* out, cudaStream_t s) {
+void launch_knp(const Dev& d, cudaStream_t s) {
     KnpArgs<T> a;
     a.vel = make_vel<T>(d.p);
     a.cfl = d.p.cfl;
@@ -641,47 +726,48 @@ void launch_knp(const Dev& d, const T* phi, const T* tau, T* out, cudaStream_t s
     a.theta = T(d.p.theta);
     a.time_level = d.p.time_level;
     a.sc = d.sc;
+    a.gated = d.gated;
     const int tx = d.p.n1 < TX ? d.p.n1 : TX;
-    dim3 grid(d.p.n1 / tx, d.p.n2 / TY), block(tx, TY);
-    knp_step_kernel<T><<<grid, block, 0, s>>>(phi, tau, out, d.p.n1, d.p.n2, a);
+    dim3 grid(d.p.n1 / tx, d.p.n2 / TY, d.count), block(tx, TY);
+    knp_step_kernel<T><<<grid, block, 0, s>>>((const T*)d.phi[0], (const T*)d.phi[1], (const T*)d.tau,
+                                              d.p.n1, d.p.n2, a);
 }
 
-// one full step: static solve with U^n (Sec. 3.1.1) then transport
+// one kernel of a step for every instance of the group (Sec. 3.1.1: static solve with U^n,
+// then transport); U^n is buffer sc[i].cur of instance i
 template <typename T>
-void launch_phase(const Dev& d, int phase, const T* phi, T* phi_next, cudaStream_t s) {
+void launch_phase(const Dev& d, int phase, cudaStream_t s) {
     cpx<T>* spec = (cpx<T>*)d.spec;
-    T* tau = (T*)d.tau;
+    InstCtl ctl{d.sc, d.gated};
     switch (phase) {
-        case 0: launch_row_forward<T>(d, phi, spec, d.row_partials, s); break;
-        case 1: launch_col<T>(d, spec, spec, COL_K, true, s); break;
-        case 2: launch_row_inverse<T>(d, spec, tau, ROW_TAU, phi, 0.0, s); break;
-        default: launch_knp<T>(d, phi, tau, phi_next, s); break;
+        case 0: launch_row_forward<T>(d, (const T*)d.phi[0], (const T*)d.phi[1], spec, d.row_partials, ctl, d.count, s); break;
+        case 1: launch_col<T>(d, spec, spec, COL_K, true, d.count, s); break;
+        case 2: launch_row_inverse<T>(d, spec, (T*)d.tau, ROW_TAU, 0.0, d.count, s); break;
+        default: launch_knp<T>(d, s); break;
     }
 }
 
 template <typename T>
-void launch_step(const Dev& d, const T* phi, T* phi_next, cudaStream_t s) {
-    for (int ph = 0; ph < kKernelsPerStep; ++ph) launch_phase<T>(d, ph, phi, phi_next, s);
+void launch_step(const Dev& d, cudaStream_t s) {
+    for (int ph = 0; ph < kKernelsPerStep; ++ph) launch_phase<T>(d, ph, s);
 }
 
-// static solve only: tau for the current state (also refreshes max|v0| without stepping)
+// static solve only: tau for the current state of every instance
 template <typename T>
-void launch_static(const Dev& d, const T* phi, cudaStream_t s) {
-    cpx<T>* spec = (cpx<T>*)d.spec;
-    launch_row_forward<T>(d, phi, spec, d.row_partials, s);
-    launch_col<T>(d, spec, spec, COL_K, true, s);
-    launch_row_inverse<T>(d, spec, (T*)d.tau, ROW_TAU, phi, 0.0, s);
+void launch_static(const Dev& d, cudaStream_t s) {
+    for (int ph = 0; ph < kKernelsPerStep - 1; ++ph) launch_phase<T>(d, ph, s);
 }
 
 template <typename T>
 void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s) {
     cpx<T>* spec = (cpx<T>*)d.spec;
     cpx<T>* spec2 = (cpx<T>*)d.spec2;
-    launch_row_forward<T>(d, phi, spec, nullptr, s);
-    launch_col<T>(d, spec, spec2, COL_DERIV1, false, s);
-    launch_row_inverse<T>(d, spec2, a12, ROW_PLAIN, nullptr, 0.0, s);
-    launch_col<T>(d, spec, spec2, COL_DERIV2N, false, s);
-    launch_row_inverse<T>(d, spec2, a11, ROW_PLAIN, nullptr, 0.0, s);
+    InstCtl none{nullptr, 0};
+    launch_row_forward<T>(d, phi, phi, spec, nullptr, none, 1, s);
+    launch_col<T>(d, spec, spec2, COL_DERIV1, false, 1, s);
+    launch_row_inverse<T>(d, spec2, a12, ROW_PLAIN, 0.0, 1, s);
+    launch_col<T>(d, spec, spec2, COL_DERIV2N, false, 1, s);
+    launch_row_inverse<T>(d, spec2, a11, ROW_PLAIN, 0.0, 1, s);
 }
 
 template <typename T>
@@ -691,16 +777,17 @@ void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, d
     cpx<T>* spec2 = (cpx<T>*)d.spec2;
     // a11 / a12 may be the state buffers; the result goes through tau (free here)
     cpx<T>* tmp = (cpx<T>*)d.tau;
-    launch_row_forward<T>(d, a11, spec, nullptr, s);
-    launch_row_forward<T>(d, a12, spec2, nullptr, s);
-    launch_col<T>(d, spec, spec, COL_FWD, false, s);
-    launch_col<T>(d, spec2, spec2, COL_FWD, false, s);
+    InstCtl none{nullptr, 0};
+    launch_row_forward<T>(d, a11, a11, spec, nullptr, none, 1, s);
+    launch_row_forward<T>(d, a12, a12, spec2, nullptr, none, 1, s);
+    launch_col<T>(d, spec, spec, COL_FWD, false, 1, s);
+    launch_col<T>(d, spec2, spec2, COL_FWD, false, 1, s);
     CurlArgs c;
     c.dx = d.p.dx;
     c.mean_up13 = mean_up13 - phi_ref;
     curl_inverse_kernel<T><<<nblk, 256, 0, s>>>(spec, spec2, tmp, d.p.n1, d.p.n2, c, partials);
-    launch_col<T>(d, tmp, spec, COL_INV, false, s);
-    launch_row_inverse<T>(d, spec, phi_out, ROW_PLAIN, nullptr, 0.0, s);
+    launch_col<T>(d, tmp, spec, COL_INV, false, 1, s);
+    launch_row_inverse<T>(d, spec, phi_out, ROW_PLAIN, 0.0, 1, s);
 }
 
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
@@ -736,9 +823,9 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
 #define FDM_INST(T)                                                                                         \
     template LaunchGeom geometry<T>(int, int);                                                              \
     template cudaError_t configure_kernels<T>();                                                            \
-    template void launch_step<T>(const Dev&, const T*, T*, cudaStream_t);                                   \
-    template void launch_phase<T>(const Dev&, int, const T*, T*, cudaStream_t);                             \
-    template void launch_static<T>(const Dev&, const T*, cudaStream_t);                                     \
+    template void launch_step<T>(const Dev&, cudaStream_t);                                                 \
+    template void launch_phase<T>(const Dev&, int, cudaStream_t);                                           \
+    template void launch_static<T>(const Dev&, cudaStream_t);                                               \
     template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \

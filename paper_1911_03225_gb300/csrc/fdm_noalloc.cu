@@ -104,13 +104,15 @@ extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma
     cudaStream_t s = (cudaStream_t)stream;
 
     Dev d{};
+    d.count = 1;
+    d.gated = 0;
     d.p = *p;
     d.p.nz = nz;
     d.p.velocity_mode = FDM_V_PRESCRIBED;   // tau13 only: no celerity law needed
     d.p.loading_mode = FDM_LOAD_STRESS;     // mean of tau13 = the given macroscopic stress
     d.p.sigma_bar13 = sigma_bar13;
     d.geom = geometry<double>(p->n1, p->n2);
-    d.phi[0] = const_cast<double*>(d_up13);
+    d.phi[0] = const_cast<double*>(d_up13);   // buffer 0 is current (scalars start at zero)
     d.phi[1] = nullptr;
     d.tau = d_tau13;
     d.spec = base + kOffSpec;
@@ -132,7 +134,7 @@ extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma
     noalloc_tables_kernel<<<8, 256, 0, s>>>(base + kOffTw1, p->n1, base + kOffTw2, p->n2, base + kOffW3, nz, p->nh);
     const double mu = p->E / (2.0 * (1.0 + p->nu));
     launch_kernel_table(base + kOffK, p->n1, p->n2, nz, p->nh, mu, p->nu, base + kOffW3, s);
-    launch_static<double>(d, d_up13, s);
+    launch_static<double>(d, s);
     if (cudaGetLastError() != cudaSuccess) return FDM_ERR_DEVICE;
     return FDM_OK;
 }

@@ -1,0 +1,107 @@
+"""Batched instances and the continuous-batching server: every instance's result must be the
+same as when it runs alone (the kernels are deterministic, so equality is exact), and the
+batched FP64 result must match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_03225_gb300 import FDM, Batch, Params, inputs
+from paper_1911_03225_gb300 import binding as B
+from paper_1911_03225_gb300.serve import Request, Server, poisson_arrivals
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def coupled(n, precision=B.FP64):
+    return Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_rate=1e-4,
+                  cfl=0.4, theta=1.0, precision=precision)
+
+
+def alone(p, up0, steps):
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        info = sim.step(steps)
+        return sim.read_fields("up13", "tau13"), info
+
+
+def test_batch_equals_single_runs_with_uneven_sizes_and_budgets():
+    specs = [(64, B.FP64, 0, 30), (128, B.MIXED, 1, 17), (64, B.FP64, 2, 9), (32, B.MIXED, 3, 30),
+             (128, B.FP64, 4, 25), (64, B.MIXED, 5, 0)]
+    params = [coupled(n, prec) for n, prec, _, _ in specs]
+    ups = [inputs.random_up(n, seed=s, ell=8.0) for n, _, s, _ in specs]
+    with Batch(params) as b:
+        assert b.launches_per_step() == 4 * 5   # (64,FP64) x2 share a group
+        for i, (n, prec, s, steps) in enumerate(specs):
+            b.set_plastic_distortion(i, ups[i])
+            b.set_budget(i, steps)
+        b.enqueue_steps(12)
+        left = b.sync()
+        assert list(left) == [max(st - 12, 0) for *_, st in specs]
+        b.enqueue_steps(20)
+        assert (b.sync() == 0).all()
+        got = [b.read_fields(i, "up13", "tau13") for i in range(len(specs))]
+        infos = [b.info(i) for i in range(len(specs))]
+    for i, (n, prec, s, steps) in enumerate(specs):
+        assert infos[i].step == steps
+        if steps == 0:
+            np.testing.assert_allclose(got[i]["up13"], ups[i], atol=1e-6 if prec == B.MIXED else 0)
+            continue
+        ref, info = alone(params[i], ups[i], steps)
+        np.testing.assert_array_equal(got[i]["up13"], ref["up13"])
+        np.testing.assert_array_equal(got[i]["tau13"], ref["tau13"])
+        assert infos[i].t == info.t
+
+
+def test_batched_fp64_matches_oracle():
+    n, steps = 64, 40
+    params = [coupled(n), coupled(n)]
+    ups = [inputs.random_up(n, seed=11, ell=6.0), inputs.random_up(n, seed=12, ell=6.0)]
+    with Batch(params) as b:
+        for i in range(2):
+            b.set_plastic_distortion(i, ups[i])
+            b.set_budget(i, steps)
+        b.enqueue_steps(steps)
+        b.sync()
+        got = [b.read_fields(i, "up13")["up13"] for i in range(2)]
+    op = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=1, eps_bar13_rate=1e-4, cfl=0.4, theta=1.0)
+    for i in range(2):
+        ref, rc = oracle.run(op, ups[i], steps)
+        assert np.linalg.norm(got[i] - ref.up13) / np.linalg.norm(ref.up13) < 1e-11
+
+
+def test_served_results_equal_alone_runs():
+    """Requests of different sizes, lengths and precisions arrive over time; the server
+    admits them into free slots while others run.  Each result equals its solo run."""
+    rng = np.random.default_rng(5)
+    sizes = [32, 64, 128]
+    reqs = []
+    arr = poisson_arrivals(200.0, 14, seed=9)
+    for k in range(14):
+        n = int(rng.choice(sizes))
+        prec = B.FP64 if k % 2 == 0 else B.MIXED
+        reqs.append(Request(rid=k, n=n, steps=int(rng.integers(5, 60)), precision=prec, arrival=float(arr[k]),
+                            up13=inputs.random_up(n, seed=100 + k, ell=6.0)))
+    base = coupled(32)
+    classes = {(n, p): 2 for n in sizes for p in (B.FP64, B.MIXED)}
+    srv = Server(base, classes, hbm_budget=40e6, tick_steps=4)
+    try:
+        results, stats = srv.run(reqs)
+    finally:
+        srv.close()
+    assert stats["completed"] == len(reqs)
+    assert stats["p99_latency_s"] >= stats["p50_latency_s"] > 0
+    by_id = {r.rid: r for r in results}
+    for k in (0, 1, 2, 5, 8):
+        r = reqs[k]
+        ref, info = alone(Params(**{**base.__dict__, "n1": r.n, "n2": r.n, "precision": r.precision}), r.up13, r.steps)
+        np.testing.assert_array_equal(by_id[k].up13, ref["up13"])
+        assert by_id[k].t == info.t
