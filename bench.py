@@ -62,6 +62,33 @@ def bytes_per_cell(elt):
 KNP_FLOPS_PER_CELL = 380
 
 
+def kernel_source_hash():
+    """sha256 (first 16 hex) of the CUDA sources; profile figures are valid only for it."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1911_03225_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, precision, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries under profiles/,
+    or None when absent or taken on different kernel sources."""
+    import glob
+    sha = kernel_source_hash()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(f):
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split()[1:])
+            if (kv.get("kernel") == kernel and kv.get("precision") == precision and int(kv.get("n", 0)) == n
+                    and kv.get("source") == sha):
+                return int(kv["bytes"])
+    return None
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -243,7 +270,8 @@ def run_ours(args, world, rank, local):
                 "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = None
+    roof["traffic"] = profiled_traffic(dom, primary, n)
+    roof["algorithmic_bytes"] = r["bpc"][dom] * cells
     roof["hbm_frac_of_step"] = (sum(r["bpc"].values()) * cells / (r["total_ms"] / K / 1e3) / 1e9) / hbm_peak
 
     # end to end through the public API with host buffers (rank-local)
@@ -265,9 +293,22 @@ def run_ours(args, world, rank, local):
 
     extra = {}
     for prec, rr in results.items():
+        d = rr["dominant"]
+        d_ms = rr["phase_ms"][d]
+        if d == "knp_step":
+            pk = FP64_NOMINAL_GFLOPS if prec == "fp64" else FP32_PEAK_GFLOPS
+            rl = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (d_ms / 1e3) / 1e9, "peak": pk,
+                  "unit": "GFLOP/s"}
+        else:
+            rl = {"bound": "hbm", "achieved": rr["bpc"][d] * cells / (d_ms / 1e3) / 1e9, "peak": hbm_peak,
+                  "unit": "GB/s"}
+        rl["frac"] = rl["achieved"] / rl["peak"]
+        rl["kernel"] = d
+        rl["traffic"] = profiled_traffic(d, prec, n)
         extra[prec] = {"value": cells * K * world / (rr["total_ms"] / 1e3),
                        "ms_per_step": rr["total_ms"] / K,
                        "phase_ms": {k: round(v, 5) for k, v in rr["phase_ms"].items()},
+                       "roofline": rl,
                        "t_end": rr["info"].t, "clocks": rr["clocks"]}
 
     if rank == 0:
