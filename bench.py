@@ -37,10 +37,10 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x 2 (FMA) x max SM c
 
 
 def workload_params(n, precision):
-    from paper_1911_03225_gb300.binding import Params, V_STRESS, LOAD_STRAIN_RAMP, FP64, MIXED
+    from paper_1911_03225_gb300.binding import Params, V_STRESS, LOAD_STRAIN_RAMP, FP64, MIXED, DF64
     return Params(n1=n, n2=n, velocity_mode=V_STRESS, mobility=1.0, loading_mode=LOAD_STRAIN_RAMP,
                   eps_bar13_rate=1e-4, cfl=0.4, theta=1.0, E=1.0, nu=0.3,
-                  precision=MIXED if precision == "mixed" else FP64)
+                  precision={"mixed": MIXED, "df64": DF64}.get(precision, FP64))
 
 
 def workload_input(n, seed):
@@ -233,7 +233,7 @@ def run_ours(args, world, rank, local):
     up0 = workload_input(n, seed=rank)
 
     results = {}
-    for prec in ([args.precision] if args.precision != "both" else ["fp64", "mixed"]):
+    for prec in ([args.precision] if args.precision != "all" else ["fp64", "df64", "mixed"]):
         p = workload_params(n, prec)
         sim = FDM(p, stream=stream.cuda_stream)
         sim.set_plastic_distortion(up0)
@@ -248,18 +248,18 @@ def run_ours(args, world, rank, local):
             barrier(world)
         info = sim.info()
         t_max = max_over_ranks(total_ms, world)
-        elt = 8 if prec == "fp64" else 4
+        elt = 4 if prec == "mixed" else 8
         phase_mean = {ph: sum(v) / len(v) for ph, v in per_phase.items()}
         dom = max(phase_mean, key=phase_mean.get)
         bpc = bytes_per_cell(elt)
         results[prec] = {"total_ms": t_max, "phase_ms": phase_mean, "dominant": dom,
                          "clocks": clk.summary(), "info": info, "bpc": bpc, "sim": sim}
 
-    primary = args.precision if args.precision != "both" else "fp64"
+    primary = args.precision if args.precision != "all" else "fp64"
     r = results[primary]
     value = cells * K * world / (r["total_ms"] / 1e3)
     dom = r["dominant"]
-    elt = 8 if primary == "fp64" else 4
+    elt = 4 if primary == "mixed" else 8
     dom_ms = r["phase_ms"][dom]
     if dom == "knp_step" and primary == "fp64":
         roof = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (dom_ms / 1e3) / 1e9,
@@ -508,7 +508,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048)
-    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--precision", default="all", choices=["fp64", "df64", "mixed", "all"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="coupled", choices=["coupled", "batched", "serve"])

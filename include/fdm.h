@@ -51,7 +51,7 @@ typedef enum {
 
 enum { FDM_V_PRESCRIBED = 0, FDM_V_STRESS = 1 };
 enum { FDM_LOAD_STRESS = 0, FDM_LOAD_STRAIN_RAMP = 1, FDM_LOAD_ZERO_MEAN_STRESS = 2 };
-enum { FDM_FP64 = 0, FDM_MIXED = 1 };
+enum { FDM_FP64 = 0, FDM_MIXED = 1, FDM_DF64 = 2 };
 enum { FDM_T_MIDPOINT = 0, FDM_T_LITERAL = 1 };
 
 /* Problem parameters (dimensionless, Sec. 3.2.1). */
@@ -74,8 +74,12 @@ typedef struct {
     double eps_bar13_0;      /* FDM_LOAD_STRAIN_RAMP: eps_bar13 = eps_bar13_0 + rate * step   */
     double eps_bar13_rate;
     int32_t time_level;      /* FDM_T_MIDPOINT (default) or FDM_T_LITERAL (Sec. 3.2.2 Step 3) */
-    int32_t precision;       /* FDM_FP64, or FDM_MIXED: FP32 fields/FFT/stencil with the mean
-                                plastic slip, loading, dt and conserved sums in FP64          */
+    int32_t precision;       /* FDM_FP64: native FP64 throughout.
+                                FDM_MIXED: FP32 fields/FFT/stencil with the mean plastic slip,
+                                loading, dt and conserved sums in FP64.
+                                FDM_DF64: fields/FFT/stencil in double-word arithmetic (two
+                                FP32 words, ~48-bit significand, on the FP32 pipes), scalars
+                                in FP64; FP64 accuracy class at FP32-pipe speed             */
 } fdm_params;
 
 /* Scalars after the last step of a call.  The sums are over all nodes of the staggered

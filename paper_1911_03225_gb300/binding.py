@@ -28,7 +28,7 @@ FDM_ERR_TOO_LARGE = 9
 
 V_PRESCRIBED, V_STRESS = 0, 1
 LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS = 0, 1, 2
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 T_MIDPOINT, T_LITERAL = 0, 1
 
 FIELD_UP13, FIELD_ALPHA11, FIELD_ALPHA12, FIELD_TAU13, FIELD_V1, FIELD_V2 = 1, 2, 4, 8, 16, 32

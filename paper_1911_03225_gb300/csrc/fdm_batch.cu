@@ -5,6 +5,7 @@
 #include <new>
 #include <vector>
 
+#include "fdm_df.cuh"
 #include "fdm_host.h"
 
 using namespace fdm;
@@ -12,7 +13,7 @@ using namespace fdm;
 struct fdm_batch {
     struct Group {
         Dev d;
-        bool mixed;
+        int prec;
         std::vector<int> members;      // batch indices of the group's instances
         std::vector<double> phi_ref;   // per instance (mixed precision offset)
     };
@@ -82,7 +83,7 @@ fdm_status fdm_batch_create(int32_t count, const fdm_params* params, void* strea
             keys.push_back(q);
             b->groups.emplace_back();
             g = (int)keys.size() - 1;
-            b->groups[g].mixed = q.precision == FDM_MIXED;
+            b->groups[g].prec = q.precision;
         }
         b->group_of[i] = g;
         b->local_of[i] = (int)b->groups[g].members.size();
@@ -91,8 +92,8 @@ fdm_status fdm_batch_create(int32_t count, const fdm_params* params, void* strea
     for (size_t g = 0; g < b->groups.size(); ++g) {
         auto& G = b->groups[g];
         const int c = (int)G.members.size();
-        fdm_status st = G.mixed ? build_group<float>(G.d, b->arena, keys[g], c, 1, false, b->stream)
-                                : build_group<double>(G.d, b->arena, keys[g], c, 1, false, b->stream);
+        fdm_status st = FDM_OK;
+        FDM_DISPATCH(G.prec, st = build_group<T>(G.d, b->arena, keys[g], c, 1, false, b->stream));
         if (st != FDM_OK) {
             fdm_batch_destroy(b);
             return st;
@@ -111,9 +112,9 @@ fdm_status fdm_batch_set_plastic_distortion(fdm_batch* b, int32_t i, const doubl
     double mean = ksum(up13, n) / (double)n;
     if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
     FDM_CK(cudaStreamSynchronize(b->stream));
-    const double ref = G.mixed ? mean : 0.0;
-    const size_t e = G.mixed ? sizeof(float) : sizeof(double);
-    fdm_status st = upload_field((char*)G.d.phi[0] + (size_t)j * n * e, up13, n, G.mixed, ref, b->stream);
+    const double ref = G.prec != FDM_FP64 ? mean : 0.0;
+    const size_t e = elt_size(&G.d.p);
+    fdm_status st = upload_field((char*)G.d.phi[0] + (size_t)j * n * e, up13, n, G.prec, ref, b->stream);
     if (st) return st;
     fdm_dev_scalars s;
     std::memset(&s, 0, sizeof(s));
@@ -146,12 +147,12 @@ fdm_status fdm_batch_enqueue_steps(fdm_batch* b, int32_t nsteps) {
     if (!b || nsteps < 0) return FDM_ERR_INVALID_ARG;
     if (nsteps == 0) return FDM_OK;
     std::vector<Dev*> devs;
-    std::vector<int> mixed;
+    std::vector<int> prec;
     for (auto& G : b->groups) {
         devs.push_back(&G.d);
-        mixed.push_back(G.mixed ? 1 : 0);
+        prec.push_back(G.prec);
     }
-    fdm_status st = build_step_graphs(b->graphs, devs, mixed);
+    fdm_status st = build_step_graphs(b->graphs, devs, prec);
     if (st) return st;
     return replay_steps(b->graphs, nsteps, b->stream);
 }
@@ -176,7 +177,7 @@ fdm_status fdm_batch_get_info(fdm_batch* b, int32_t i, fdm_step_info* info) {
     if (!index_ok(b, i) || !info) return FDM_ERR_INVALID_ARG;
     if (!b->has_state[i]) return FDM_ERR_STATE;
     auto& G = b->groups[b->group_of[i]];
-    return instance_info(G.d, b->local_of[i], G.mixed, b->stream, info);
+    return instance_info(G.d, b->local_of[i], G.prec, b->stream, info);
 }
 
 fdm_status fdm_batch_read_fields(fdm_batch* b, int32_t i, uint32_t mask, double* up13, double* tau13) {
@@ -187,17 +188,17 @@ fdm_status fdm_batch_read_fields(fdm_batch* b, int32_t i, uint32_t mask, double*
     auto& G = b->groups[b->group_of[i]];
     const int j = b->local_of[i];
     const size_t n = (size_t)G.d.p.n1 * G.d.p.n2;
-    const size_t e = G.mixed ? sizeof(float) : sizeof(double);
+    const size_t e = elt_size(&G.d.p);
     fdm_dev_scalars s;
     FDM_CK(cudaMemcpyAsync(&s, G.d.sc + j, sizeof(s), cudaMemcpyDeviceToHost, b->stream));
     FDM_CK(cudaStreamSynchronize(b->stream));
     fdm_status st;
     if (mask & FDM_FIELD_UP13)
-        if ((st = download_field(up13, (char*)G.d.phi[s.cur] + (size_t)j * n * e, n, G.mixed, G.phi_ref[j],
+        if ((st = download_field(up13, (char*)G.d.phi[s.cur] + (size_t)j * n * e, n, G.prec, G.phi_ref[j],
                                  b->stream)))
             return st;
     if (mask & FDM_FIELD_TAU13)
-        if ((st = download_field(tau13, (char*)G.d.tau + (size_t)j * n * e, n, G.mixed, 0.0, b->stream)))
+        if ((st = download_field(tau13, (char*)G.d.tau + (size_t)j * n * e, n, G.prec, 0.0, b->stream)))
             return st;
     return FDM_OK;
 }

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "fdm_df.cuh"
 #include "fdm_host.h"
 
 namespace fdm {
@@ -81,51 +82,63 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
 
 template fdm_status build_group<double>(Dev&, Arena&, const fdm_params&, int, int, bool, cudaStream_t);
 template fdm_status build_group<float>(Dev&, Arena&, const fdm_params&, int, int, bool, cudaStream_t);
+template fdm_status build_group<df>(Dev&, Arena&, const fdm_params&, int, int, bool, cudaStream_t);
 
-fdm_status upload_field(void* dst, const double* src, size_t n, bool mixed, double offset, cudaStream_t s) {
-    if (!mixed) {
-        if (offset == 0.0) {
-            FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, s));
-            FDM_CK(cudaStreamSynchronize(s));
-            return FDM_OK;
-        }
-        std::vector<double> t(n);
-        for (size_t i = 0; i < n; ++i) t[i] = src[i] - offset;
-        FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+fdm_status upload_field(void* dst, const double* src, size_t n, int prec, double offset, cudaStream_t s) {
+    if (prec == FDM_FP64 && offset == 0.0) {
+        FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, s));
         FDM_CK(cudaStreamSynchronize(s));
         return FDM_OK;
     }
-    std::vector<float> t(n);
-    for (size_t i = 0; i < n; ++i) t[i] = (float)(src[i] - offset);
-    FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (prec == FDM_MIXED) {
+        std::vector<float> t(n);
+        for (size_t i = 0; i < n; ++i) t[i] = (float)(src[i] - offset);
+        FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+        FDM_CK(cudaStreamSynchronize(s));
+        return FDM_OK;
+    }
+    if (prec == FDM_DF64) {
+        std::vector<df> t(n);
+        for (size_t i = 0; i < n; ++i) t[i] = df(src[i] - offset);
+        FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(df), cudaMemcpyHostToDevice, s));
+        FDM_CK(cudaStreamSynchronize(s));
+        return FDM_OK;
+    }
+    std::vector<double> t(n);
+    for (size_t i = 0; i < n; ++i) t[i] = src[i] - offset;
+    FDM_CK(cudaMemcpyAsync(dst, t.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
     FDM_CK(cudaStreamSynchronize(s));
     return FDM_OK;
 }
 
-fdm_status download_field(double* dst, const void* src, size_t n, bool mixed, double offset, cudaStream_t s) {
-    if (!mixed) {
-        FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+fdm_status download_field(double* dst, const void* src, size_t n, int prec, double offset, cudaStream_t s) {
+    if (prec == FDM_MIXED) {
+        std::vector<float> t(n);
+        FDM_CK(cudaMemcpyAsync(t.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, s));
         FDM_CK(cudaStreamSynchronize(s));
-        if (offset != 0.0)
-            for (size_t i = 0; i < n; ++i) dst[i] += offset;
+        for (size_t i = 0; i < n; ++i) dst[i] = (double)t[i] + offset;
         return FDM_OK;
     }
-    std::vector<float> t(n);
-    FDM_CK(cudaMemcpyAsync(t.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (prec == FDM_DF64) {
+        std::vector<df> t(n);
+        FDM_CK(cudaMemcpyAsync(t.data(), src, n * sizeof(df), cudaMemcpyDeviceToHost, s));
+        FDM_CK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < n; ++i) dst[i] = (double)t[i] + offset;
+        return FDM_OK;
+    }
+    FDM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     FDM_CK(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < n; ++i) dst[i] = (double)t[i] + offset;
+    if (offset != 0.0)
+        for (size_t i = 0; i < n; ++i) dst[i] += offset;
     return FDM_OK;
 }
 
 static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nsteps, const std::vector<Dev*>& groups,
-                                const std::vector<int>& mixed) {
+                                const std::vector<int>& prec) {
     cudaGraph_t graph = nullptr;
     FDM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < nsteps; ++k)
-        for (size_t g = 0; g < groups.size(); ++g) {
-            if (mixed[g]) launch_step<float>(*groups[g], cap);
-            else launch_step<double>(*groups[g], cap);
-        }
+        for (size_t g = 0; g < groups.size(); ++g) FDM_DISPATCH(prec[g], launch_step<T>(*groups[g], cap));
     cudaError_t e = cudaStreamEndCapture(cap, &graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -140,12 +153,12 @@ static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nste
     return FDM_OK;
 }
 
-fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& mixed) {
+fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& prec) {
     if (g.one) return FDM_OK;
     if (!g.capture) FDM_CK(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
-    fdm_status st = capture_steps(&g.one, g.capture, 1, groups, mixed);
+    fdm_status st = capture_steps(&g.one, g.capture, 1, groups, prec);
     if (st) return st;
-    return capture_steps(&g.many, g.capture, StepGraphs::kGraphSteps, groups, mixed);
+    return capture_steps(&g.many, g.capture, StepGraphs::kGraphSteps, groups, prec);
 }
 
 fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s) {
@@ -158,15 +171,14 @@ fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s) {
 }
 
 // FP64 sums over the staggered Nye components of one instance's current state (info)
-fdm_status instance_info(const Dev& d, int inst, bool mixed, cudaStream_t stream, fdm_step_info* info) {
+fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, fdm_step_info* info) {
     fdm_dev_scalars s;
     FDM_CK(cudaMemcpyAsync(&s, d.sc + inst, sizeof(s), cudaMemcpyDeviceToHost, stream));
     FDM_CK(cudaStreamSynchronize(stream));
     const size_t n = (size_t)d.p.n1 * d.p.n2;
-    const size_t e = mixed ? sizeof(float) : sizeof(double);
+    const size_t e = elt_size(&d.p);
     const void* phi = (const char*)d.phi[s.cur] + (size_t)inst * n * e;
-    if (mixed) launch_alpha_sums<float>(d, (const float*)phi, d.red, d.red_blocks, stream);
-    else launch_alpha_sums<double>(d, (const double*)phi, d.red, d.red_blocks, stream);
+    FDM_DISPATCH(prec, launch_alpha_sums<T>(d, (const T*)phi, d.red, d.red_blocks, stream));
     FDM_CK(cudaGetLastError());
     std::vector<double> part((size_t)6 * d.red_blocks);
     FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -204,7 +216,7 @@ struct fdm_handle {
     cudaStream_t stream;
     int next_phase;          // next kernel of a partially enqueued step (0: none pending)
     bool has_state;
-    bool mixed;
+    int prec;                // FDM_FP64, FDM_MIXED or FDM_DF64
     size_t n;                // n1 * n2
     void* rd[4];             // readout buffers (type T, n each), allocated on first use
 };
@@ -250,7 +262,7 @@ fdm_status read_fields_impl(fdm_handle* h, uint32_t mask, double* up13, double* 
     fdm_status st;
     if ((st = read_scalars(h, &sc))) return st;
     const T* phi = (const T*)d.phi[sc.cur];
-    const bool mx = h->mixed;
+    const int mx = h->prec;
     if (mask & FDM_FIELD_UP13)
         if ((st = download_field(up13, phi, h->n, mx, d.phi_ref_host, h->stream))) return st;
     if (mask & FDM_FIELD_TAU13)
@@ -319,10 +331,10 @@ fdm_status fdm_create(const fdm_params* p, void* stream, fdm_handle** out) {
     h->stream = (cudaStream_t)stream;
     h->next_phase = 0;
     h->has_state = false;
-    h->mixed = p->precision == FDM_MIXED;
+    h->prec = p->precision;
     h->n = (size_t)p->n1 * p->n2;
-    fdm_status st = h->mixed ? build_group<float>(h->d, h->arena, q, 1, 0, true, h->stream)
-                             : build_group<double>(h->d, h->arena, q, 1, 0, true, h->stream);
+    fdm_status st = FDM_OK;
+    FDM_DISPATCH(h->prec, st = build_group<T>(h->d, h->arena, q, 1, 0, true, h->stream));
     if (st != FDM_OK) {
         fdm_destroy(h);
         return st;
@@ -337,8 +349,9 @@ fdm_status fdm_set_plastic_distortion(fdm_handle* h, const double* up13) {
     double mean = ksum(up13, h->n) / (double)h->n;
     if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
     FDM_CK(cudaStreamSynchronize(h->stream));
-    h->d.phi_ref_host = h->mixed ? mean : 0.0;
-    fdm_status st = upload_field(h->d.phi[0], up13, h->n, h->mixed, h->d.phi_ref_host, h->stream);
+    // FP32 and double-word storage hold U13 minus its mean (the scheme is offset equivariant)
+    h->d.phi_ref_host = h->prec != FDM_FP64 ? mean : 0.0;
+    fdm_status st = upload_field(h->d.phi[0], up13, h->n, h->prec, h->d.phi_ref_host, h->stream);
     if (st) return st;
     return reset_scalars(h, mean);
 }
@@ -357,16 +370,12 @@ fdm_status fdm_set_density(fdm_handle* h, const double* a11, const double* a12, 
     Dev& d = h->d;
     fdm_status st;
     // stage alpha in the two state buffers (the old state is being replaced)
-    if ((st = upload_field(d.phi[0], a11, n, h->mixed, 0.0, h->stream))) return st;
-    if ((st = upload_field(d.phi[1], a12, n, h->mixed, 0.0, h->stream))) return st;
-    double phi_ref = h->mixed ? mean_up13 : 0.0;
+    if ((st = upload_field(d.phi[0], a11, n, h->prec, 0.0, h->stream))) return st;
+    if ((st = upload_field(d.phi[1], a12, n, h->prec, 0.0, h->stream))) return st;
+    double phi_ref = h->prec != FDM_FP64 ? mean_up13 : 0.0;
     const int nblk = d.red_blocks;
-    if (h->mixed)
-        launch_curl_inverse<float>(d, (const float*)d.phi[0], (const float*)d.phi[1], (float*)d.phi[0], mean_up13,
-                                   phi_ref, d.red, nblk, h->stream);
-    else
-        launch_curl_inverse<double>(d, (const double*)d.phi[0], (const double*)d.phi[1], (double*)d.phi[0],
-                                    mean_up13, phi_ref, d.red, nblk, h->stream);
+    FDM_DISPATCH(h->prec, launch_curl_inverse<T>(d, (const T*)d.phi[0], (const T*)d.phi[1], (T*)d.phi[0], mean_up13,
+                                                 phi_ref, d.red, nblk, h->stream));
     FDM_CK(cudaGetLastError());
     std::vector<double> part((size_t)2 * nblk);
     FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -397,8 +406,7 @@ fdm_status fdm_static_solve(fdm_handle* h) {
     if (!h) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
     Dev& d = h->d;
-    if (h->mixed) launch_static<float>(d, h->stream);
-    else launch_static<double>(d, h->stream);
+    FDM_DISPATCH(h->prec, launch_static<T>(d, h->stream));
     FDM_CK(cudaGetLastError());
     // the stencil kernel normally clears the running max; no step follows here
     FDM_CK(cudaMemsetAsync(&d.sc->vmax_bits, 0, sizeof(unsigned long long), h->stream));
@@ -411,8 +419,8 @@ fdm_status fdm_enqueue_steps(fdm_handle* h, int32_t nsteps) {
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
     if (nsteps == 0) return FDM_OK;
     std::vector<Dev*> groups{&h->d};
-    std::vector<int> mixed{h->mixed ? 1 : 0};
-    fdm_status st = build_step_graphs(h->graphs, groups, mixed);
+    std::vector<int> prec{h->prec};
+    fdm_status st = build_step_graphs(h->graphs, groups, prec);
     if (st) return st;
     return replay_steps(h->graphs, nsteps, h->stream);
 }
@@ -420,8 +428,7 @@ fdm_status fdm_enqueue_steps(fdm_handle* h, int32_t nsteps) {
 fdm_status fdm_enqueue_phase(fdm_handle* h, int32_t phase) {
     if (!h || phase < 0 || phase >= kKernelsPerStep) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || phase != h->next_phase) return FDM_ERR_STATE;
-    if (h->mixed) launch_phase<float>(h->d, phase, h->stream);
-    else launch_phase<double>(h->d, phase, h->stream);
+    FDM_DISPATCH(h->prec, launch_phase<T>(h->d, phase, h->stream));
     FDM_CK(cudaGetLastError());
     h->next_phase = (phase + 1) % kKernelsPerStep;
     return FDM_OK;
@@ -440,7 +447,7 @@ fdm_status fdm_step(fdm_handle* h, int32_t nsteps, fdm_step_info* info) {
     fdm_status st = fdm_enqueue_steps(h, nsteps);
     if (st) return st;
     if (info) {
-        if ((st = instance_info(h->d, 0, h->mixed, h->stream, info))) return st;
+        if ((st = instance_info(h->d, 0, h->prec, h->stream, info))) return st;
         return info->status ? (fdm_status)info->status : FDM_OK;
     }
     return fdm_sync(h);
@@ -455,14 +462,15 @@ fdm_status fdm_read_fields(fdm_handle* h, uint32_t mask, double* up13, double* a
         ((mask & FDM_FIELD_V1) && !v1) || ((mask & FDM_FIELD_V2) && !v2))
         return FDM_ERR_INVALID_ARG;
     if (!h->has_state) return FDM_ERR_STATE;
-    return h->mixed ? read_fields_impl<float>(h, mask, up13, a11, a12, tau, v1, v2)
-                    : read_fields_impl<double>(h, mask, up13, a11, a12, tau, v1, v2);
+    fdm_status st = FDM_OK;
+    FDM_DISPATCH(h->prec, st = read_fields_impl<T>(h, mask, up13, a11, a12, tau, v1, v2));
+    return st;
 }
 
 fdm_status fdm_get_info(fdm_handle* h, fdm_step_info* info) {
     if (!h || !info) return FDM_ERR_INVALID_ARG;
     if (!h->has_state) return FDM_ERR_STATE;
-    return instance_info(h->d, 0, h->mixed, h->stream, info);
+    return instance_info(h->d, 0, h->prec, h->stream, info);
 }
 
 int32_t fdm_kernels_per_step(const fdm_handle* h) {

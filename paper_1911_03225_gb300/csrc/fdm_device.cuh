@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "fdm_df.cuh"
+
 namespace fdm {
 
 template <typename T> struct cpx { T x, y; };
@@ -175,6 +177,8 @@ __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 // 1/x for x != 0
 __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+// sqrt(x) for x >= 0
+template <typename T> __device__ __forceinline__ T tsqrt(T x) { return (x > T(0)) ? x * trsqrt(x) : T(0); }
 
 // ---------------------------------------------------------------------------------
 // Kurganov-Noelle-Petrova update of one node (Sec. 3.2.3 Steps 1-4; readings G1-G7).
@@ -209,7 +213,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_le
     T px[2] = {(xs[0].D - T(0.5) * xs[0].S) * inv_h, (xs[1].D + T(0.5) * xs[1].S) * inv_h};
     T qy[2] = {(ys[0].D - T(0.5) * ys[0].S) * inv_h, (ys[1].D + T(0.5) * ys[1].S) * inv_h};
     // Step 2: one-sided speeds over the four pairs (dH/dp = v0 p / |(p,q)|, 0 at the origin)
-    T ap = 0, am = 0, bp = 0, bm = 0;
+    T ap = T(0), am = T(0), bp = T(0), bm = T(0);
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll

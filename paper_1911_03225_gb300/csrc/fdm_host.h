@@ -38,7 +38,7 @@ inline bool params_valid(const fdm_params* p) {
     if (!std::isfinite(p->sigma_bar13) || !std::isfinite(p->eps_bar13_0) || !std::isfinite(p->eps_bar13_rate))
         return false;
     if (p->time_level != FDM_T_MIDPOINT && p->time_level != FDM_T_LITERAL) return false;
-    if (p->precision != FDM_FP64 && p->precision != FDM_MIXED) return false;
+    if (p->precision != FDM_FP64 && p->precision != FDM_MIXED && p->precision != FDM_DF64) return false;
     return true;
 }
 
@@ -111,9 +111,10 @@ struct Arena {
 template <typename T>
 fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gated, bool with_spec2, cudaStream_t s);
 
-// Uploads a host FP64 field into a device buffer of type T (minus offset) / downloads it.
-fdm_status upload_field(void* dst, const double* src, size_t n, bool mixed, double offset, cudaStream_t s);
-fdm_status download_field(double* dst, const void* src, size_t n, bool mixed, double offset, cudaStream_t s);
+// Uploads a host FP64 field into a device buffer of precision `prec` (FDM_FP64, FDM_MIXED,
+// FDM_DF64), minus offset / downloads it, adding offset back.
+fdm_status upload_field(void* dst, const double* src, size_t n, int prec, double offset, cudaStream_t s);
+fdm_status download_field(double* dst, const void* src, size_t n, int prec, double offset, cudaStream_t s);
 
 // A step of every group as CUDA graphs (1 and kGraphSteps steps), replayed on a stream.
 struct StepGraphs {
@@ -129,9 +130,9 @@ struct StepGraphs {
     }
 };
 
-fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& mixed);
+fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& prec);
 // scalars and FP64 Nye sums of instance `inst` of a group (synchronises `stream`)
-fdm_status instance_info(const Dev& d, int inst, bool mixed, cudaStream_t stream, fdm_step_info* info);
+fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, fdm_step_info* info);
 fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s);
 
 }  // namespace fdm

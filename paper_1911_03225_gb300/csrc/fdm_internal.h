@@ -70,4 +70,14 @@ void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, 
 
 constexpr int kKernelsPerStep = 4;
 
+struct df;  // double-word type (fdm_df.cuh)
+
+// Runs BODY with T bound to the storage/arithmetic type of precision PREC.
+#define FDM_DISPATCH(PREC, BODY)                                      \
+    do {                                                              \
+        if ((PREC) == FDM_MIXED) { using T = float; BODY; }           \
+        else if ((PREC) == FDM_DF64) { using T = ::fdm::df; BODY; }   \
+        else { using T = double; BODY; }                              \
+    } while (0)
+
 }  // namespace fdm

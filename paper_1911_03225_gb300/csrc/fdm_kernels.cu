@@ -557,7 +557,7 @@ __global__ void curl_inverse_kernel(const cpx<T>* __restrict__ sa, const cpx<T>*
         cpx<T> za = sa[i], zb = sb[i];
         if (kx > 0) {
             double xi1 = xi_of(kx, n1, c.dx);
-            double ar = za.x, ai = za.y, br = zb.x, bi = zb.y;
+            double ar = (double)za.x, ai = (double)za.y, br = (double)zb.x, bi = (double)zb.y;
             double dr = xi1 * ar + o2 * br, di = xi1 * ai + o2 * bi;
             num += 2.0 * (dr * dr + di * di);
             den += 2.0 * (xi1 * xi1 + o2 * o2) * (ar * ar + ai * ai + br * br + bi * bi);
@@ -629,7 +629,7 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
                                 VelLaw<T> p, double phi_ref) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T c = celerity(p, tau[i], phi[i], phi_ref);
-        T m = sqrt(a11[i] * a11[i] + a12[i] * a12[i]);
+        T m = tsqrt(a11[i] * a11[i] + a12[i] * a12[i]);
         if (m > T(0)) { v1[i] = c * a12[i] / m; v2[i] = -c * a11[i] / m; }
         else { v1[i] = T(0); v2[i] = T(0); }
     }
@@ -835,5 +835,6 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
                                      cudaStream_t);
 FDM_INST(double)
 FDM_INST(float)
+FDM_INST(df)
 
 }  // namespace fdm

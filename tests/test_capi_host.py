@@ -42,7 +42,7 @@ def test_default_params(lib):
 @pytest.mark.parametrize("field,value", [
     ("n1", 48), ("n1", 8), ("n2", 8192), ("nh", 0), ("nh", 300), ("dx", 0.0), ("nu", 0.5),
     ("theta", 0.5), ("theta", 2.5), ("cfl", 0.0), ("cfl", 1.5), ("velocity_mode", 7),
-    ("loading_mode", 3), ("time_level", 2), ("precision", 2), ("E", -1.0)])
+    ("loading_mode", 3), ("time_level", 2), ("precision", 3), ("E", -1.0)])
 def test_invalid_params_rejected_without_device(lib, field, value):
     p = binding.default_params(64, 64)
     setattr(p, field, value)
