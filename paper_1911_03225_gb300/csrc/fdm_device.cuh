@@ -177,6 +177,9 @@ __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 // 1/x for x != 0
 __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+// x / 2 (exact)
+__device__ __forceinline__ float thalf(float x) { return 0.5f * x; }
+__device__ __forceinline__ double thalf(double x) { return 0.5 * x; }
 // sqrt(x) for x >= 0
 template <typename T> __device__ __forceinline__ T tsqrt(T x) { return (x > T(0)) ? x * trsqrt(x) : T(0); }
 
@@ -196,22 +199,40 @@ struct Side {  // one-dimensional limited quadratic on the cell on one side of t
     T S;  // limited second difference on that cell
 };
 
+// x times the limiter parameter theta.  A hardware float or double product is cheapest; a
+// double-word product is not, so theta = 1 or 2 is applied there as an exact scaling.
+__device__ __forceinline__ float theta_mul(float x, float theta, int) { return theta * x; }
+__device__ __forceinline__ double theta_mul(double x, double theta, int) { return theta * x; }
+__device__ __forceinline__ df theta_mul(df x, df theta, int theta_code) {
+    if (theta_code == 1) return x;
+    if (theta_code == 2) return scale2(x, 2.0f);
+    return theta * x;
+}
+
+// The update in cell units: with h the cell size, gradients are carried as h * grad (the
+// first differences themselves), displacements as d / h, and the time step as dt / h.  The
+// one-sided speeds depend only on the gradient's direction, so they are unchanged; every
+// formula of Steps 1-4 then holds with h = 1 and dt replaced by dt / h.
 template <typename T, typename F>
-__device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_level) {
-    const T inv_h = T(1) / h;
-    const T inv_h2 = inv_h * inv_h;
+__device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code, int time_level) {
     const T f0 = f(0, 0);
-    // Step 1: limited second differences along x1 and x2
+    // Step 1: first differences and limited second differences along x1 and x2
     T dxm3 = f(-1, 0) - f(-2, 0), dxm1 = f0 - f(-1, 0), dxp1 = f(1, 0) - f0, dxp3 = f(2, 0) - f(1, 0);
     T dym3 = f(0, -1) - f(0, -2), dym1 = f0 - f(0, -1), dyp1 = f(0, 1) - f0, dyp3 = f(0, 2) - f(0, 1);
     Side<T> xs[2], ys[2];  // [0] = + side, [1] = - side
-    xs[0].D = dxp1; xs[0].S = minmod3(theta * (dxp3 - dxp1), T(0.5) * (dxp3 - dxm1), theta * (dxp1 - dxm1));
-    xs[1].D = dxm1; xs[1].S = minmod3(theta * (dxp1 - dxm1), T(0.5) * (dxp1 - dxm3), theta * (dxm1 - dxm3));
-    ys[0].D = dyp1; ys[0].S = minmod3(theta * (dyp3 - dyp1), T(0.5) * (dyp3 - dym1), theta * (dyp1 - dym1));
-    ys[1].D = dym1; ys[1].S = minmod3(theta * (dyp1 - dym1), T(0.5) * (dyp1 - dym3), theta * (dym1 - dym3));
-    // one-sided derivatives at the node
-    T px[2] = {(xs[0].D - T(0.5) * xs[0].S) * inv_h, (xs[1].D + T(0.5) * xs[1].S) * inv_h};
-    T qy[2] = {(ys[0].D - T(0.5) * ys[0].S) * inv_h, (ys[1].D + T(0.5) * ys[1].S) * inv_h};
+    {
+        const T c = theta_mul(dxp1 - dxm1, theta, theta_code);  // shared by both limiters
+        xs[0].D = dxp1; xs[0].S = minmod3(theta_mul(dxp3 - dxp1, theta, theta_code), thalf(dxp3 - dxm1), c);
+        xs[1].D = dxm1; xs[1].S = minmod3(c, thalf(dxp1 - dxm3), theta_mul(dxm1 - dxm3, theta, theta_code));
+    }
+    {
+        const T c = theta_mul(dyp1 - dym1, theta, theta_code);
+        ys[0].D = dyp1; ys[0].S = minmod3(theta_mul(dyp3 - dyp1, theta, theta_code), thalf(dyp3 - dym1), c);
+        ys[1].D = dym1; ys[1].S = minmod3(c, thalf(dyp1 - dym3), theta_mul(dym1 - dym3, theta, theta_code));
+    }
+    // one-sided derivatives at the node (times h)
+    T px[2] = {xs[0].D - thalf(xs[0].S), xs[1].D + thalf(xs[1].S)};
+    T qy[2] = {ys[0].D - thalf(ys[0].S), ys[1].D + thalf(ys[1].S)};
     // Step 2: one-sided speeds over the four pairs (dH/dp = v0 p / |(p,q)|, 0 at the origin)
     T ap = T(0), am = T(0), bp = T(0), bm = T(0);
 #pragma unroll
@@ -232,41 +253,51 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt, T h, T theta, int time_le
     if (bp - bm > T(0)) { ny[0] = -bm; ny[1] = bp; dyw = bp - bm; }
     else { ny[0] = T(0.5); ny[1] = T(0.5); dyw = T(1); }
     const T inv_w = trcp(dxw * dyw);
-    // Step 3: values at the four intermediate points (G2, G3)
+    const T vdt = v0 * dt_h;                 // v0 dt / h
+    const T half_dt = thalf(dt_h);
+    // Step 3: values at the four intermediate points (G2, G3).  Along each direction the
+    // limited quadratic on the side's cell, in cell units: with e the displacement / h and
+    // sg = -1 on the + side, +1 on the - side,  X(e) = D e + S e (e + sg) / 2 and
+    // h X'(e) = D + S (e + sg / 2).
+    T Y[2], dY[2], ey[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        ey[t] = (t == 0 ? bp : bm) * dt_h;
+        const T sgn = (t == 0) ? T(-1) : T(1);
+        Y[t] = ys[t].D * ey[t] + thalf(ys[t].S * ey[t] * (ey[t] + sgn));
+        dY[t] = ys[t].D + ys[t].S * (ey[t] + thalf(sgn));
+    }
     T acc = T(0);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const int cx = (s == 0) ? 1 : -1;
-        const T ddx = (s == 0 ? ap : am) * dt;
+        const T ex = (s == 0 ? ap : am) * dt_h;
         const T Dx = xs[s].D, Sx = xs[s].S;
-        const T sgx = (s == 0) ? T(-1) : T(1);  // dx (dx -+ h)
-        const T X = Dx * ddx * inv_h + Sx * ddx * (ddx + sgx * h) * (T(0.5) * inv_h2);
-        const T dX = Dx * inv_h + Sx * (T(2) * ddx + sgx * h) * (T(0.5) * inv_h2);
+        const T sgn = (s == 0) ? T(-1) : T(1);
+        const T X = Dx * ex + thalf(Sx * ex * (ex + sgn));
+        const T dX = Dx + Sx * (ex + thalf(sgn));
+        const T fx = f(cx, 0);
         T accs = T(0);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int cy = (t == 0) ? 1 : -1;
-            const T ddy = (t == 0 ? bp : bm) * dt;
-            const T Dy = ys[t].D, Sy = ys[t].S;
-            const T sgy = (t == 0) ? T(-1) : T(1);
-            const T Y = Dy * ddy * inv_h + Sy * ddy * (ddy + sgy * h) * (T(0.5) * inv_h2);
-            const T dY = Dy * inv_h + Sy * (T(2) * ddy + sgy * h) * (T(0.5) * inv_h2);
-            const T cross = (f(cx, cy) - f(cx, 0) - f(0, cy) + f0) * T(cx * cy) * inv_h2;
-            const T val = f0 + X + Y + cross * ddx * ddy;
-            T p = dX + cross * ddy;
-            T q = dY + cross * ddx;
+            // mixed second difference of the quadrant cell (h^2 times the bilinear cross term)
+            const T mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
+            const T cross = (cx * cy > 0) ? mixed : -mixed;
+            const T val = f0 + X + Y[t] + cross * ex * ey[t];
+            T p = dX + cross * ey[t];
+            T q = dY[t] + cross * ex;
             if (time_level == 0) {
                 T r2 = p * p + q * q;
                 T gx = T(0), gy = T(0);
                 if (r2 > T(0)) { T vr = v0 * trsqrt(r2); gx = vr * p; gy = vr * q; }
-                T hxx = Sx * inv_h2, hyy = Sy * inv_h2;
-                T np = p - T(0.5) * dt * (hxx * gx + cross * gy);
-                T nq = q - T(0.5) * dt * (cross * gx + hyy * gy);
+                const T np = p - half_dt * (Sx * gx + cross * gy);
+                const T nq = q - half_dt * (cross * gx + ys[t].S * gy);
                 p = np; q = nq;
             }
             const T s2 = p * p + q * q;
-            const T g = (s2 > T(0)) ? s2 * trsqrt(s2) : T(0);   // |grad|
-            const T psi = val - dt * v0 * g;
+            const T g = (s2 > T(0)) ? s2 * trsqrt(s2) : T(0);   // h |grad|
+            const T psi = val - vdt * g;
             accs += ny[t] * psi;
         }
         acc += nx[s] * accs;

@@ -4,8 +4,11 @@
 // executes FP32 at 58x the FP64 rate, so FP64-accurate kernels run faster on this type than
 // on native doubles.  Building blocks, all from the published literature:
 //   TwoSum (Knuth, TAOCP vol. 2), FastTwoSum (Dekker 1971), TwoProd with an FMA;
-//   double-word + double-word, "accurate" version (Joldes, Muller, Popescu, ACM TOMS 2017,
-//   Algorithm 6; relative error <= 3 u^2, u = 2^-24);
+//   double-word + double-word (Joldes, Muller, Popescu, ACM TOMS 2017): the "sloppy"
+//   version (their Algorithm 5, 11 flops), whose error is a few u^2 (|x| + |y|) (u = 2^-24)
+//   -- relative when the signs agree, absolute under cancellation.  Every
+//   value this library adds already carries a representation error of u^2 times its own
+//   magnitude, so the 20-flop relative-error version buys no accuracy here;
 //   double-word x double-word (same paper, Algorithm 12; <= 5 u^2) and
 //   double-word x float (Algorithm 9);
 //   reciprocal and reciprocal square root by one Newton step on the double word from a
@@ -62,13 +65,11 @@ __host__ __device__ __forceinline__ void two_prod(float a, float b, float& p, fl
 }
 
 __host__ __device__ __forceinline__ df operator+(df x, df y) {
-    float sh, sl, th, tl, vh, vl, zh, zl;
+    float sh, sl, zh, zl;
     two_sum(x.hi, y.hi, sh, sl);
-    two_sum(x.lo, y.lo, th, tl);
-    float c = DF_ADD(sl, th);
-    fast_two_sum(sh, c, vh, vl);
-    float w = DF_ADD(tl, vl);
-    fast_two_sum(vh, w, zh, zl);
+    float v = DF_ADD(x.lo, y.lo);
+    float w = DF_ADD(sl, v);
+    fast_two_sum(sh, w, zh, zl);
     return df(zh, zl);
 }
 __host__ __device__ __forceinline__ df operator-(df x) { return df(-x.hi, -x.lo); }
@@ -138,11 +139,15 @@ __host__ __device__ __forceinline__ df df_rsqrt(df x) {
     return df(s, t);
 }
 
+// exact scaling by a power of two (no rounding for normal values)
+__host__ __device__ __forceinline__ df scale2(df x, float p2) { return df(DF_MUL(x.hi, p2), DF_MUL(x.lo, p2)); }
+
 // precision-typed helpers used by the generic kernels
 __host__ __device__ __forceinline__ df tmin(df a, df b) { return (b < a) ? b : a; }
 __host__ __device__ __forceinline__ df tmax(df a, df b) { return (b > a) ? b : a; }
 __host__ __device__ __forceinline__ df tabs(df a) { return (a.hi < 0.f) ? -a : a; }
 __host__ __device__ __forceinline__ df trsqrt(df x) { return df_rsqrt(x); }
 __host__ __device__ __forceinline__ df trcp(df x) { return df_rcp(x); }
+__host__ __device__ __forceinline__ df thalf(df x) { return scale2(x, 0.5f); }
 
 }  // namespace fdm

@@ -417,7 +417,8 @@ template <typename T>
 struct KnpArgs {
     VelLaw<T> vel;
     double cfl, dx, dt_max;  // time-step rule (FP64)
-    T h, theta;
+    T theta;
+    int theta_code;          // 1 or 2 when theta is exactly that (exact scaling), else 0
     int time_level;
     fdm_dev_scalars* sc;     // scalars of instance 0
     int gated;
@@ -435,15 +436,27 @@ __device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, dou
     return dtd;
 }
 
+// resident blocks per SM the register allocation must allow (FP64 needs more registers),
+// and nodes per thread stacked along x2 (amortises the block's load phases and halo)
+template <typename T> struct KnpOcc { static constexpr int value = 4; static constexpr int npt = 4; };
+template <> struct KnpOcc<double> { static constexpr int value = 2; static constexpr int npt = 2; };
+template <> struct KnpOcc<df> { static constexpr int value = 3; static constexpr int npt = 2; };
+
+// grid (n1 / tx, n2 / (TY npt), instances); block (tx, TY); thread (i, j) updates the
+// nodes (bx + i, by + j + k TY), k < npt
 template <typename T>
-__global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* phi0, const T* phi1, const T* __restrict__ tau0,
-                                                           int n1, int n2, KnpArgs<T> a) {
-    __shared__ T tile[TY + 4][TX + 4];
+__global__ void __launch_bounds__(TX * TY, KnpOcc<T>::value) knp_step_kernel(const T* phi0, const T* phi1,
+                                                                             const T* __restrict__ tau0,
+                                                                             int n1, int n2, int npt,
+                                                                             KnpArgs<T> a) {
+    constexpr int NPT = KnpOcc<T>::npt;
+    __shared__ T tile[TY * NPT + 4][TX + 4];
     __shared__ T s_dt;
     __shared__ int s_run, s_cur;
     const int inst = blockIdx.z;
     const int tx = blockDim.x;  // TX, or n1 when n1 < TX
-    const int bx = blockIdx.x * tx, by = blockIdx.y * TY;
+    const int rows = TY * npt;
+    const int bx = blockIdx.x * tx, by = blockIdx.y * rows;
     const int tid = threadIdx.y * tx + threadIdx.x;
     fdm_dev_scalars* sc = a.sc + inst;
     if (tid == 0) {
@@ -459,7 +472,7 @@ __global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* phi0, const 
             // fenced counter increment)
             const double vmax = __longlong_as_double((long long)sc->vmax_bits);
             const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
-            s_dt = T(dtd);
+            s_dt = T(dtd / a.dx);   // the node update works in cell units (dt / h)
             __threadfence();
             const unsigned int total = gridDim.x * gridDim.y;
             if (atomicAdd(&sc->done_count, 1u) == total - 1) {
@@ -482,7 +495,7 @@ __global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* phi0, const 
     const T* phi = (s_cur ? phi1 : phi0) + inst * nn;
     T* out = const_cast<T*>(s_cur ? phi0 : phi1) + inst * nn;
     const T* tau = tau0 + inst * nn;
-    for (int ly = threadIdx.y; ly < TY + 4; ly += TY) {
+    for (int ly = threadIdx.y; ly < rows + 4; ly += TY) {
         const int gy = (by + ly - 2) & (n2 - 1);
         for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
             const int gx = (bx + lx - 2) & (n1 - 1);
@@ -491,13 +504,18 @@ __global__ void __launch_bounds__(TX * TY) knp_step_kernel(const T* phi0, const 
     }
     __syncthreads();
     const T dt = s_dt;
-    const int x = bx + threadIdx.x, y = by + threadIdx.y;
-    const int lx = threadIdx.x + 2, ly = threadIdx.y + 2;
-    const T up = tile[ly][lx];
+    const int x = bx + threadIdx.x;
+    const int lx = threadIdx.x + 2;
     const double phi_ref = a.vel.friction ? sc->phi_ref : 0.0;
-    const T v0 = celerity(a.vel, tau[(size_t)y * n1 + x], up, phi_ref);
-    auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
-    out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.h, a.theta, a.time_level);
+#pragma unroll 1
+    for (int k = 0; k < npt; ++k) {
+        const int y = by + threadIdx.y + k * TY;
+        const int ly = threadIdx.y + k * TY + 2;
+        const T up = tile[ly][lx];
+        const T v0 = celerity(a.vel, tau[(size_t)y * n1 + x], up, phi_ref);
+        auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
+        out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
+    }
 }
 
 // ------------------------------------------------------------------ set-up / readout helpers
@@ -722,15 +740,17 @@ void launch_knp(const Dev& d, cudaStream_t s) {
     a.cfl = d.p.cfl;
     a.dx = d.p.dx;
     a.dt_max = d.p.dt_max;
-    a.h = T(d.p.dx);
     a.theta = T(d.p.theta);
+    a.theta_code = d.p.theta == 1.0 ? 1 : (d.p.theta == 2.0 ? 2 : 0);
     a.time_level = d.p.time_level;
     a.sc = d.sc;
     a.gated = d.gated;
     const int tx = d.p.n1 < TX ? d.p.n1 : TX;
-    dim3 grid(d.p.n1 / tx, d.p.n2 / TY, d.count), block(tx, TY);
+    int npt = KnpOcc<T>::npt;
+    while (npt > 1 && d.p.n2 < TY * npt) npt >>= 1;
+    dim3 grid(d.p.n1 / tx, d.p.n2 / (TY * npt), d.count), block(tx, TY);
     knp_step_kernel<T><<<grid, block, 0, s>>>((const T*)d.phi[0], (const T*)d.phi[1], (const T*)d.tau,
-                                              d.p.n1, d.p.n2, a);
+                                              d.p.n1, d.p.n2, npt, a);
 }
 
 // one kernel of a step for every instance of the group (Sec. 3.1.1: static solve with U^n,
