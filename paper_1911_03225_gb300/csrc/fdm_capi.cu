@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "fdm_df.cuh"
+#include "fdm_device.cuh"
 #include "fdm_host.h"
 
 namespace fdm {
@@ -22,6 +22,29 @@ static fdm_status upload_twiddles(void* dst, int n, cudaStream_t s) {
         tw[2 * m] = (T)std::cos(a);
         tw[2 * m + 1] = (T)(-std::sin(a));
     }
+    FDM_CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    return FDM_OK;
+}
+
+// per-pass twiddle tables of an L-point transform (layout: see pass_table_len)
+template <typename T>
+static fdm_status upload_pass_twiddles(void* dst, int L, cudaStream_t s) {
+    const int len = pass_table_len(L);
+    std::vector<T> tw(2 * (size_t)len);
+    int off = 0, Ns = 1;
+    auto emit = [&](int R) {
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                double a = 2.0 * kPi * (double)r * (double)k / ((double)Ns * R);
+                tw[2 * (size_t)(off + (r - 1) * Ns + k)] = (T)std::cos(a);
+                tw[2 * (size_t)(off + (r - 1) * Ns + k) + 1] = (T)(-std::sin(a));
+            }
+        off += (R - 1) * Ns;
+    };
+    while (Ns * 8 <= L) { emit(8); Ns *= 8; }
+    if (Ns * 4 == L) emit(4);
+    else if (Ns * 2 == L) emit(2);
     FDM_CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     FDM_CK(cudaStreamSynchronize(s));
     return FDM_OK;
@@ -49,6 +72,8 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     if ((st = A.alloc(&d.Kh, nk * sizeof(T)))) return st;
     if ((st = A.alloc(&d.tw1, (size_t)p.n1 * 2 * sizeof(T)))) return st;
     if ((st = A.alloc(&d.tw2, (size_t)p.n2 * 2 * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.pt1, (size_t)(pass_table_len(p.n1 / 2) + 1) * 2 * sizeof(T)))) return st;
+    if ((st = A.alloc(&d.pt2, (size_t)(pass_table_len(p.n2) + 1) * 2 * sizeof(T)))) return st;
     if ((st = A.alloc((void**)&d.row_partials, (size_t)count * d.geom.row_blocks * sizeof(double)))) return st;
     d.red_blocks = red_blocks_for(n);
     if ((st = A.alloc((void**)&d.red, (size_t)6 * d.red_blocks * sizeof(double)))) return st;
@@ -57,6 +82,8 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     FDM_CK(cudaMemsetAsync(d.phi[0], 0, cn * sizeof(T), s));
     if ((st = upload_twiddles<T>(d.tw1, p.n1, s))) return st;
     if ((st = upload_twiddles<T>(d.tw2, p.n2, s))) return st;
+    if ((st = upload_pass_twiddles<T>(d.pt1, p.n1 / 2, s))) return st;
+    if ((st = upload_pass_twiddles<T>(d.pt2, p.n2, s))) return st;
     // layer weights |chi-hat(k3)|^2, k3 in [0, nz/2] (Sec. 3.2.1 layer of nh voxels)
     std::vector<double> w3((size_t)p.nz / 2 + 1);
     for (int k3 = 0; k3 <= p.nz / 2; ++k3) {

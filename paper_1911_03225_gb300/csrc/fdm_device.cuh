@@ -1,6 +1,6 @@
 // fdm_device.cuh -- device-side building blocks of the GB300 FDM library:
-// complex arithmetic, a batched shared-memory Stockham FFT (radix 4 with one radix-2
-// pass for odd log2 L), the real<->half-complex twists, and the per-node
+// complex arithmetic, a batched in-place shared-memory Stockham FFT (radix 8, then one
+// radix-4 or radix-2 pass), the real<->half-complex twists, and the per-node
 // Kurganov-Noelle-Petrova update (Sec. 3.2.2-3.2.3 of arXiv 1911.03225).
 #pragma once
 #include <cstdint>
@@ -62,70 +62,86 @@ template <typename T> struct Dft<T, 8> {
     }
 };
 
-// One Stockham autosort pass of radix R (Govindaraju et al., SC'08 formulation) over nseq
-// sequences of length L: for j in [0, L/R), k = j mod Ns,
-//   v_r = in[j + r L/R] w^(r k),  w = exp(sign 2 pi i / (Ns R)),  v = DFT_R(v),
-//   out[(j - k) R + k + r Ns] = v_r.
-template <typename T, int R>
-__device__ __forceinline__ void stockham_pass(const cpx<T>* in, cpx<T>* out, int L, int nseq, int ld, int Ns,
-                                              int sign, const cpx<T>* __restrict__ tw, int tw_len) {
-    const int q = L / R;
-    const int lq = 31 - __clz(q);  // q is a power of two: shifts instead of divisions
-    const int items = nseq * q;
-    const int stride = tw_len / (Ns * R);
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int s = it >> lq, j = it & (q - 1);
-        const int k = j & (Ns - 1);
-        const cpx<T>* src = in + (size_t)s * ld;
-        cpx<T>* dst = out + (size_t)s * ld;
-        cpx<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * q];
-        if (Ns > 1) {
-            const int m = k * stride;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, r * m, sign));
-        }
-        Dft<T, R>::run(v, sign);
-        const int d = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[d + r * Ns] = v[r];
-    }
+// Shared-memory position of element i of a sequence: the low 4 index bits are XORed with
+// bits 4..7, a permutation inside each aligned group of 16 that makes both the unit-stride
+// reads and the strided writes of every Stockham pass touch distinct banks.
+__host__ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
+// sequence stride for L elements (one extra slot so that rows start on different banks)
+__host__ __device__ __forceinline__ int padded_len(int L) { return L + 1; }
+
+// Twiddles of the in-place FFT, one table per pass: for the pass of radix R at sub-length Ns,
+// entry (r - 1) * Ns + k holds exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns, so that a warp
+// reads consecutive k.  Passes: radix 8 while Ns * 8 <= L, then one radix-4 or radix-2 pass.
+// pass_table_len(L) = total entries for all passes of an L-point transform.
+__host__ __device__ __forceinline__ int pass_table_len(int L) {
+    int n = 0, Ns = 1;
+    while (Ns * 8 <= L) { n += 7 * Ns; Ns *= 8; }
+    if (Ns * 4 == L) n += 3 * Ns;
+    else if (Ns * 2 == L) n += Ns;
+    return n;
 }
 
-// Batched FFT in shared memory: nseq sequences of length L (power of two, 2..8192),
-// sequence s at a[s * ld]; b is scratch of the same shape.  Unnormalised; sign -1 forward,
-// +1 inverse.  tw: table of length tw_len (a multiple of L) of exp(-2 pi i m / tw_len).
-// Radix-8 passes, then one radix-4 or radix-2 pass for the remaining factor.  Must be
-// called by all threads of the block.  Returns the buffer holding the result (a or b).
+// Batched in-place FFT in shared memory: Stockham autosort passes (Govindaraju et al., SC'08)
+// of radix R over nseq sequences of length L.  For j in [0, L/R), k = j mod Ns:
+//   v_r = a[j + r L/R] w^(r k),  w = exp(sign 2 pi i / (Ns R)),  v = DFT_R(v),
+//   a[(j - k) R + k + r Ns] = v_r.
+// Each thread keeps its butterflies' values in registers between the read and the write of a
+// pass (a barrier in between), so one shared buffer suffices and twice as many blocks fit
+// on an SM as with a ping-pong pair.  Unnormalised; sign -1 forward, +1 inverse.
+// Requires blockDim.x * 8 >= nseq * L: a thread owns at most one radix-8 butterfly per pass
+// (two radix-4 or four radix-2 butterflies in the last pass).  Element i of sequence s at
+// a[s * ld + swz(i)].  pt: the pass twiddle tables (pass_table_len(L) entries).  Must be
+// called by all threads of the block.
+template <typename T, int R, int PER>
+__device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int ld, int Ns, int sign,
+                                                 const cpx<T>* __restrict__ ptw) {
+    const int q = L / R;
+    const int lq = 31 - __clz(q);
+    const int items = nseq * q;
+    cpx<T> v[PER][R];
+    int base[PER], d[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int it = threadIdx.x + u * blockDim.x;
+        if (it >= items) continue;
+        const int s = it >> lq, j = it & (q - 1);
+        const int k = j & (Ns - 1);
+        base[u] = s * ld;
+        d[u] = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u][r] = a[base[u] + swz(j + r * q)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], twiddle(ptw, (r - 1) * Ns + k, sign));
+        }
+        Dft<T, R>::run(v[u], sign);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        if (threadIdx.x + u * blockDim.x >= items) continue;
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[base[u] + swz(d[u] + r * Ns)] = v[u][r];
+    }
+    __syncthreads();
+}
+
 template <typename T>
-__device__ cpx<T>* smem_fft(cpx<T>* a, cpx<T>* b, int L, int nseq, int ld, int sign,
-                            const cpx<T>* __restrict__ tw, int tw_len) {
-    cpx<T>* in = a;
-    cpx<T>* out = b;
+__device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, int sign, const cpx<T>* __restrict__ pt) {
     int Ns = 1;
     while (Ns * 8 <= L) {
-        stockham_pass<T, 8>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
-        __syncthreads();
-        cpx<T>* t = in; in = out; out = t;
+        stockham_pass_ip<T, 8, 1>(a, L, nseq, ld, Ns, sign, pt);
+        pt += 7 * Ns;
         Ns *= 8;
     }
-    if (Ns * 4 == L) {
-        stockham_pass<T, 4>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
-        __syncthreads();
-        cpx<T>* t = in; in = out; out = t;
-    } else if (Ns * 2 == L) {
-        stockham_pass<T, 2>(in, out, L, nseq, ld, Ns, sign, tw, tw_len);
-        __syncthreads();
-        cpx<T>* t = in; in = out; out = t;
-    }
-    return in;
+    if (Ns * 4 == L) stockham_pass_ip<T, 4, 2>(a, L, nseq, ld, Ns, sign, pt);
+    else if (Ns * 2 == L) stockham_pass_ip<T, 2, 4>(a, L, nseq, ld, Ns, sign, pt);
 }
 
 // ---------------------------------------------------------------------------------
 // Real row of n reals <-> packed half spectrum of n/2 complex: P0 = X0 + i X_{n/2},
 // P_k = X_k (1 <= k < n/2), from / to the n/2-point complex FFT of z_m = x_2m + i x_2m+1.
-// Z, P: one sequence each (L = n/2 entries).  W^k = exp(-2 pi i k / n) = tw_n[k].
+// Z, P: one padded sequence each (L = n/2 entries).  W^k = exp(-2 pi i k / n) = tw_n[k].
 // ---------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void r2c_twist_pair(const cpx<T>* Z, cpx<T>* P, int L, int k,
@@ -135,13 +151,13 @@ __device__ __forceinline__ void r2c_twist_pair(const cpx<T>* Z, cpx<T>* P, int L
         P[0] = mk(z0.x + z0.y, z0.x - z0.y);
         return;
     }
-    cpx<T> A = Z[k], B = conj(Z[L - k]);
+    cpx<T> A = Z[swz(k)], B = conj(Z[swz(L - k)]);
     cpx<T> E = scale(A + B, T(0.5));
     cpx<T> D = scale(A - B, T(0.5));
     cpx<T> O = mk(D.y, -D.x);          // -i (A - B) / 2
     cpx<T> WO = cmul(tw_n[k], O);
-    P[k] = E + WO;
-    if (2 * k != L) P[L - k] = conj(E - WO);
+    P[swz(k)] = E + WO;
+    if (2 * k != L) P[swz(L - k)] = conj(E - WO);
 }
 
 template <typename T>
@@ -152,11 +168,11 @@ __device__ __forceinline__ void c2r_twist_pair(const cpx<T>* P, cpx<T>* Z, int L
         Z[0] = mk(p0.x + p0.y, p0.x - p0.y);
         return;
     }
-    cpx<T> Xk = P[k], Xc = conj(P[L - k]);
+    cpx<T> Xk = P[swz(k)], Xc = conj(P[swz(L - k)]);
     cpx<T> E = Xk + Xc;
     cpx<T> O = cmul(Xk - Xc, conj(tw_n[k]));  // times V^k = exp(+2 pi i k / n)
-    Z[k] = mk(E.x - O.y, E.y + O.x);          // E + i O
-    if (2 * k != L) Z[L - k] = mk(E.x + O.y, -E.y + O.x);  // conj(E) + i conj(O)
+    Z[swz(k)] = mk(E.x - O.y, E.y + O.x);          // E + i O
+    if (2 * k != L) Z[swz(L - k)] = mk(E.x + O.y, -E.y + O.x);  // conj(E) + i conj(O)
 }
 
 // ---------------------------------------------------------------------------------

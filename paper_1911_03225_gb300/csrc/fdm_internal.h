@@ -27,6 +27,7 @@ struct LaunchGeom {
     int C;             // spectral columns per block of the column kernel
     size_t row_smem, col_smem;
     int row_blocks, col_blocks;
+    int row_threads, col_threads;  // threads per block of the row / column FFT kernels
 };
 
 // One group of `count` instances with identical parameters.  Every buffer holds `count`
@@ -41,8 +42,10 @@ struct Dev {
     void* spec;            // cpx<T> [n1/2][n2] per instance
     void* spec2;           // cpx<T> [n1/2][n2] (single instance only; readouts)
     void* Kh;              // T [n1/2+1][n2/2+1]
-    void* tw1;             // cpx<T> [n1]
+    void* tw1;             // cpx<T> [n1]: exp(-2 pi i m / n1), for the real/half-complex twists
     void* tw2;             // cpx<T> [n2]
+    void* pt1;             // cpx<T> pass twiddle tables of the n1/2-point row transform
+    void* pt2;             // cpx<T> pass twiddle tables of the n2-point column transform
     double* row_partials;  // [count][row_blocks]
     double* red;           // reduction partials [6 * red_blocks]
     int red_blocks;

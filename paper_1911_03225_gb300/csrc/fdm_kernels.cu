@@ -61,7 +61,6 @@ __device__ __forceinline__ void loading_state(const fdm_params& p, long long ste
     }
 }
 
-constexpr int kFftThreads = 512;  // threads per block of the FFT kernels
 
 // Instance addressing of the step kernels: a launch covers `count` instances (grid y, or z
 // for the stencil).  sc == nullptr marks a set-up launch (one instance, buffer 0, always
@@ -88,9 +87,10 @@ __device__ __forceinline__ void inst_state(const InstCtl& c, int inst, int* run,
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional per-block FP64 sum of
 // the loaded values (for <U13>).
 template <typename T>
-__global__ void __launch_bounds__(512) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
+__global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1,
+                                                          const cpx<T>* __restrict__ pt1,
                                                           double* row_partials, InstCtl ctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_run, s_cur;
@@ -103,10 +103,9 @@ __global__ void __launch_bounds__(512) row_forward_kernel(const T* src0, const T
     spec += inst * (nn / 2);
     if (row_partials) row_partials += (size_t)inst * gridDim.x;
     const int L = n1 >> 1;
-    const int ld = L + 1;  // padded sequence stride (bank spread for the transposed store)
-    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
-    cpx<T>* B = A + (size_t)R * ld;
-    double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
+    const int ld = padded_len(L);  // padded sequence stride (bank spread for the transposed store)
+    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);                 // R * ld elements
+    double* red = reinterpret_cast<double*>(A + (size_t)R * ld);     // 32 doubles after them
     const int y0 = blockIdx.x * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     T acc = T(0), comp = T(0);  // compensated (Kahan) per-thread sum in the field's type
@@ -127,7 +126,7 @@ __global__ void __launch_bounds__(512) row_forward_kernel(const T* src0, const T
                 T t = acc + y;
                 comp = (t - acc) - y;
                 acc = t;
-                A[(e >> lL) * ld + (e & (L - 1))] = v[u];
+                A[(e >> lL) * ld + swz(e & (L - 1))] = v[u];
             }
         }
     }
@@ -136,17 +135,16 @@ __global__ void __launch_bounds__(512) row_forward_kernel(const T* src0, const T
         if (threadIdx.x == 0) row_partials[blockIdx.x] = s;
     }
     __syncthreads();
-    cpx<T>* Z = smem_fft(A, B, L, R, ld, -1, tw1, n1);
-    cpx<T>* P = (Z == A) ? B : A;
+    smem_fft_ip(A, L, R, ld, -1, pt1);
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
         int r = e / half, k = e - r * half;  // half = L/2 + 1 is not a power of two
-        r2c_twist_pair(Z + r * ld, P + r * ld, L, k, tw1);
+        r2c_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
     }
     __syncthreads();
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
         int kx = e >> lR, r = e & (R - 1);
-        spec[(size_t)kx * n2 + y0 + r] = P[r * ld + kx];
+        spec[(size_t)kx * n2 + y0 + r] = A[r * ld + swz(kx)];
     }
 }
 
@@ -191,14 +189,14 @@ __device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
+__global__ void __launch_bounds__(1024) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
                                                        int n1, int n2, int C,
-                                                       const cpx<T>* __restrict__ tw2, const T* __restrict__ Kh,
+                                                       const cpx<T>* __restrict__ pt2, const T* __restrict__ Kh,
                                                        ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ld = n2;
+    const int ld = padded_len(n2);
+    const int ln2 = 31 - __clz(n2);
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
-    cpx<T>* B = A + (size_t)C * ld;
     __shared__ double s_sigma;
     __shared__ double s_red[32];
     __shared__ int s_run, s_cur;
@@ -224,8 +222,10 @@ __global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>*
             for (int u = 0; u < 4; ++u)
                 if (e0 + u * step < total) v[u] = src[e0 + u * step];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e0 + u * step < total) A[e0 + u * step] = v[u];
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * step;
+                if (e < total) A[(e >> ln2) * ld + swz(e & (n2 - 1))] = v[u];
+            }
         }
     }
     if (a.mode == COL_K && kx0 == 0) {
@@ -249,37 +249,40 @@ __global__ void __launch_bounds__(512) col_pass_kernel(const cpx<T>* in, cpx<T>*
         }
     }
     __syncthreads();
-    cpx<T>* res = A;
-    if (a.mode != COL_INV) res = smem_fft(A, B, n2, C, ld, -1, tw2, n2);
-    cpx<T>* oth = (res == A) ? B : A;
+    if (a.mode != COL_INV) smem_fft_ip(A, n2, C, ld, -1, pt2);
     if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N) {
-        const int ln2 = 31 - __clz(n2);
-        for (int e = threadIdx.x; e < C * n2; e += blockDim.x) {
-            int c = e >> ln2, ky = e & (n2 - 1);
-            int kx = kx0 + c;
-            cpx<T> z = res[c * ld + ky];
-            cpx<T> o;
+        // in place: a thread owns the pair (ky, n2 - ky) of one column
+        const int hp = n2 / 2 + 1;
+        for (int e = threadIdx.x; e < C * hp; e += blockDim.x) {
+            const int c = e / hp, ky = e - c * hp;
+            const int kyr = (n2 - ky) & (n2 - 1);
+            const int kx = kx0 + c;
+            cpx<T>* col = A + c * ld;
+            const cpx<T> z = col[swz(ky)], zr = col[swz(kyr)];
+            cpx<T> o, orr;
             if (kx > 0) {
                 o = cmul(col_multiplier<T>(a, Kh, kx, ky, n1, n2), z);
+                orr = cmul(col_multiplier<T>(a, Kh, kx, kyr, n1, n2), zr);
             } else {
                 // packed column: z = C0 + i CN (C0, CN transforms of the real columns kx = 0
                 // and kx = n1/2); multiply each by its own symbol and repack:
-                // out = (m0 + mN)/2 z(ky) + (m0 - mN)/2 conj(z(-ky))
+                // out(ky) = (m0 + mN)/2 z(ky) + (m0 - mN)/2 conj(z(-ky))
                 cpx<T> m0 = col_multiplier<T>(a, Kh, 0, ky, n1, n2);
                 cpx<T> mN = col_multiplier<T>(a, Kh, n1 / 2, ky, n1, n2);
-                cpx<T> zr = conj(res[c * ld + ((n2 - ky) & (n2 - 1))]);
-                o = cmul(scale(m0 + mN, T(0.5)), z) + cmul(scale(m0 - mN, T(0.5)), zr);
+                o = cmul(scale(m0 + mN, T(0.5)), z) + cmul(scale(m0 - mN, T(0.5)), conj(zr));
+                cpx<T> m0r = col_multiplier<T>(a, Kh, 0, kyr, n1, n2);
+                cpx<T> mNr = col_multiplier<T>(a, Kh, n1 / 2, kyr, n1, n2);
+                orr = cmul(scale(m0r + mNr, T(0.5)), zr) + cmul(scale(m0r - mNr, T(0.5)), conj(z));
                 if (ky == 0 && a.mode == COL_K) o.x = T(s_sigma);  // macroscopic stress
             }
-            oth[c * ld + ky] = o;
+            col[swz(ky)] = o;
+            if (kyr != ky) col[swz(kyr)] = orr;
         }
         __syncthreads();
-        res = oth;
-        oth = (res == A) ? B : A;
     }
-    if (a.mode != COL_FWD) res = smem_fft(res, oth, n2, C, ld, +1, tw2, n2);
+    if (a.mode != COL_FWD) smem_fft_ip(A, n2, C, ld, +1, pt2);
     cpx<T>* dst = out + (size_t)kx0 * n2;
-    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = res[e];
+    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = A[(e >> ln2) * ld + swz(e & (n2 - 1))];
 }
 
 // ------------------------------------------------------------------ row inverse (C2R)
@@ -327,15 +330,15 @@ struct RowArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* spec, T* dst,
+__global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T* dst,
                                                           int n1, int n2, int R,
-                                                          const cpx<T>* __restrict__ tw1, RowArgs<T> a) {
+                                                          const cpx<T>* __restrict__ tw1,
+                                                          const cpx<T>* __restrict__ pt1, RowArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = n1 >> 1;
-    const int ld = L + 1;
+    const int ld = padded_len(L);
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
-    cpx<T>* B = A + (size_t)R * ld;
-    double* red = reinterpret_cast<double*>(B + (size_t)R * ld);
+    double* red = reinterpret_cast<double*>(A + (size_t)R * ld);
     __shared__ int s_run, s_cur;
     const int inst = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* spec, T*
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 int e = e0 + u * step;
-                if (e < total) B[(e & (R - 1)) * ld + (e >> lR)] = v[u];
+                if (e < total) A[(e & (R - 1)) * ld + swz(e >> lR)] = v[u];
             }
         }
     }
@@ -370,10 +373,11 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* spec, T*
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
         int r = e / half, k = e - r * half;
-        c2r_twist_pair(B + r * ld, A + r * ld, L, k, tw1);
+        c2r_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
     }
     __syncthreads();
-    cpx<T>* z = smem_fft(A, B, L, R, ld, +1, tw1, n1);
+    smem_fft_ip(A, L, R, ld, +1, pt1);
+    const cpx<T>* z = A;
     T vmax = T(0);
     bool bad = false;
     const T* up = reinterpret_cast<const T*>(s_cur ? a.phi1 : a.phi0);
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const cpx<T>* spec, T*
     const bool need_up = a.vel.friction != 0;
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
         int r = e >> lL, m = e & (L - 1);
-        cpx<T> v = z[r * ld + m];
+        cpx<T> v = z[r * ld + swz(m)];
         size_t o = (size_t)(y0 + r) * n1 + 2 * m;
         if (a.mode == ROW_TAU) {
             T u0 = T(0), u1 = T(0);
@@ -655,10 +659,11 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
 
 // ------------------------------------------------------------------ launchers
 static int pick_rows(int n1, int n2, size_t elt) {
-    // rows per block: as many as fit 48 KB per buffer, at most 16, at least 1
-    size_t per_row = (size_t)(n1 / 2 + 1) * 2 * elt;
+    // rows per block: as many as fit 40 KB of shared memory (one buffer), at most 16, and at
+    // most 8192 points (1024 threads)
+    size_t per_row = (size_t)padded_len(n1 / 2) * 2 * elt;
     int R = 1;
-    while (R < 16 && (size_t)(2 * R) * per_row <= 48 * 1024 && 2 * R <= n2) R *= 2;
+    while (R < 16 && (size_t)(2 * R) * per_row <= 40 * 1024 && 2 * R <= n2 && 2 * R * (n1 / 2) <= 8192) R *= 2;
     return R;
 }
 static int pick_cols(int n1, int n2) {
@@ -672,21 +677,29 @@ LaunchGeom geometry(int n1, int n2) {
     LaunchGeom g;
     g.R = pick_rows(n1, n2, sizeof(T));
     g.C = pick_cols(n1, n2);
-    g.row_smem = (size_t)2 * g.R * (n1 / 2 + 1) * sizeof(cpx<T>) + 32 * sizeof(double);
-    g.col_smem = (size_t)2 * g.C * n2 * sizeof(cpx<T>);
+    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>) + 32 * sizeof(double);
+    g.col_smem = (size_t)g.C * padded_len(n2) * sizeof(cpx<T>);
     g.row_blocks = n2 / g.R;
     g.col_blocks = (n1 / 2) / g.C;
+    // the in-place FFT needs at least one thread per radix-8 butterfly; at least a warp
+    g.row_threads = g.R * (n1 / 2) / 8 < 32 ? 32 : g.R * (n1 / 2) / 8;
+    g.col_threads = g.C * n2 / 8 < 32 ? 32 : g.C * n2 / 8;
     return g;
 }
 
 template <typename T>
 cudaError_t configure_kernels() {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(row_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(row_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(col_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // the FFT kernels live on shared memory: allow large dynamic allocations and ask for the
+    // largest shared-memory carveout so that several blocks stay resident per SM
+    const void* fns[3] = {(const void*)row_forward_kernel<T>, (const void*)row_inverse_kernel<T>,
+                          (const void*)col_pass_kernel<T>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -694,8 +707,9 @@ void launch_row_forward(const Dev& d, const T* src0, const T* src1, cpx<T>* spec
                         int count, cudaStream_t s) {
     const LaunchGeom& g = d.geom;
     dim3 grid(g.row_blocks, count);
-    row_forward_kernel<T><<<grid, kFftThreads, g.row_smem, s>>>(src0, src1, spec, d.p.n1, d.p.n2, g.R,
-                                                                (const cpx<T>*)d.tw1, partials, ctl);
+    row_forward_kernel<T><<<grid, g.row_threads, g.row_smem, s>>>(src0, src1, spec, d.p.n1, d.p.n2, g.R,
+                                                                (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1,
+                                                                partials, ctl);
 }
 
 template <typename T>
@@ -712,8 +726,8 @@ void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with
     a.xi1_unit = T(6.283185307179586476925286766559 / ((double)d.p.n1 * d.p.dx));
     a.xi2_unit = T(6.283185307179586476925286766559 / ((double)d.p.n2 * d.p.dx));
     dim3 grid(g.col_blocks, count);
-    col_pass_kernel<T><<<grid, kFftThreads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
-                                                             (const cpx<T>*)d.tw2, (const T*)d.Kh, a);
+    col_pass_kernel<T><<<grid, g.col_threads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
+                                                             (const cpx<T>*)d.pt2, (const T*)d.Kh, a);
 }
 
 template <typename T>
@@ -729,8 +743,8 @@ void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, doub
     a.gated = d.gated;
     a.offset = T(offset);
     dim3 grid(g.row_blocks, count);
-    row_inverse_kernel<T><<<grid, kFftThreads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
-                                                                (const cpx<T>*)d.tw1, a);
+    row_inverse_kernel<T><<<grid, g.row_threads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
+                                                                (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1, a);
 }
 
 template <typename T>

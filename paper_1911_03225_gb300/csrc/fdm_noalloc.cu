@@ -9,6 +9,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "fdm_device.cuh"
 #include "fdm_internal.h"
 
 namespace fdm {
@@ -23,12 +24,14 @@ constexpr size_t kOffSpec = 0;                                              // n
 constexpr size_t kOffK = kOffSpec + round_up((size_t)kMaxSide * kMaxSide);  // (n1/2+1)(n2/2+1)
 constexpr size_t kOffTw1 = kOffK + round_up((size_t)(kMaxSide / 2 + 1) * (kMaxSide / 2 + 1));
 constexpr size_t kOffTw2 = kOffTw1 + round_up((size_t)2 * kMaxSide);
-constexpr size_t kOffW3 = kOffTw2 + round_up((size_t)2 * kMaxSide);
+constexpr size_t kOffPt1 = kOffTw2 + round_up((size_t)2 * kMaxSide);  // pass tables (< side entries)
+constexpr size_t kOffPt2 = kOffPt1 + round_up((size_t)2 * kMaxSide);
+constexpr size_t kOffW3 = kOffPt2 + round_up((size_t)2 * kMaxSide);
 constexpr size_t kOffPart = kOffW3 + round_up((size_t)kMaxNz / 2 + 1);
 constexpr size_t kOffSc = kOffPart + round_up((size_t)kMaxSide);
 constexpr size_t kScratchDoubles = kOffSc + round_up(sizeof(fdm_dev_scalars) / sizeof(double) + 1);
 
-// The scratch (about 700 KB).  In host code this name is only a stand-in for the device
+// The scratch (about 710 KB).  In host code this name is only a stand-in for the device
 // symbol; kernels get its device address from cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -52,6 +55,25 @@ __global__ void noalloc_tables_kernel(double* tw1, int n1, double* tw2, int n2, 
                 w3[i] = (sn * sn) / (sd * sd);
             }
         }
+    }
+}
+
+// per-pass twiddle tables of an L-point transform (entry layout as in pass_table_len)
+__global__ void noalloc_pass_table_kernel(double* pt, int L) {
+    const int len = pass_table_len(L);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        int off = 0, Ns = 1, R = 8;
+        while (true) {
+            R = (Ns * 8 <= L) ? 8 : (Ns * 4 == L ? 4 : 2);
+            if (i < off + (R - 1) * Ns) break;
+            off += (R - 1) * Ns;
+            Ns *= R;
+        }
+        const int r = (i - off) / Ns + 1, k = (i - off) % Ns;
+        double sn, cs;
+        sincospi(2.0 * (double)r * (double)k / ((double)Ns * R), &sn, &cs);
+        pt[2 * i] = cs;
+        pt[2 * i + 1] = -sn;
     }
 }
 
@@ -120,6 +142,8 @@ extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma
     d.Kh = base + kOffK;
     d.tw1 = base + kOffTw1;
     d.tw2 = base + kOffTw2;
+    d.pt1 = base + kOffPt1;
+    d.pt2 = base + kOffPt2;
     d.row_partials = base + kOffPart;
     d.red = nullptr;
     d.red_blocks = 0;
@@ -132,6 +156,8 @@ extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma
         return FDM_ERR_DEVICE;
     }
     noalloc_tables_kernel<<<8, 256, 0, s>>>(base + kOffTw1, p->n1, base + kOffTw2, p->n2, base + kOffW3, nz, p->nh);
+    noalloc_pass_table_kernel<<<1, 256, 0, s>>>(base + kOffPt1, p->n1 / 2);
+    noalloc_pass_table_kernel<<<1, 256, 0, s>>>(base + kOffPt2, p->n2);
     const double mu = p->E / (2.0 * (1.0 + p->nu));
     launch_kernel_table(base + kOffK, p->n1, p->n2, nz, p->nh, mu, p->nu, base + kOffW3, s);
     launch_static<double>(d, s);
