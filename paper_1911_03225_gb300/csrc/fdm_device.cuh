@@ -196,8 +196,22 @@ __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
 // x / 2 (exact)
 __device__ __forceinline__ float thalf(float x) { return 0.5f * x; }
 __device__ __forceinline__ double thalf(double x) { return 0.5 * x; }
+// x > 0 (false for zero and NaN)
+template <typename T> __device__ __forceinline__ bool tpos(T x) { return x > T(0); }
 // sqrt(x) for x >= 0
-template <typename T> __device__ __forceinline__ T tsqrt(T x) { return (x > T(0)) ? x * trsqrt(x) : T(0); }
+template <typename T> __device__ __forceinline__ T tsqrt(T x) { return tpos(x) ? x * trsqrt(x) : T(0); }
+
+// ---------------------------------------------------------------------------------
+// Decisions on doubles made on their bit patterns.  GB300's FP64 pipe retires 2 lanes per
+// SM per clock against 64 for the integer pipe, and comparisons, min/max and sign tests
+// occupy it like an FMA, so the FP64 path takes them on integers.  With the sign bit
+// cleared, the bits of a double order like its magnitude (NaN above infinity).
+// ---------------------------------------------------------------------------------
+constexpr unsigned long long kMagBits = 0x7fffffffffffffffull, kInfBits = 0x7ff0000000000000ull;
+__device__ __forceinline__ unsigned long long ubits(double x) { return (unsigned long long)__double_as_longlong(x); }
+// nonzero magnitude up to infinity: x is neither +-0 nor NaN
+__device__ __forceinline__ bool mag_ok(unsigned long long m) { return m - 1ull < kInfBits; }
+__device__ __forceinline__ bool tpos(double x) { return mag_ok(ubits(x)); }   // bits in [1, +inf]
 
 // ---------------------------------------------------------------------------------
 // Kurganov-Noelle-Petrova update of one node (Sec. 3.2.3 Steps 1-4; readings G1-G7).
@@ -208,6 +222,30 @@ template <typename T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
     if (a < T(0) && b < T(0) && c < T(0)) return tmax(a, tmax(b, c));
     return T(0);
 }
+// the same function on bit patterns: when a, b, c are nonzero, not NaN and of one sign, the
+// one of least magnitude; else 0
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+    const unsigned long long ua = ubits(a), ub = ubits(b), uc = ubits(c);
+    const unsigned long long ma = ua & kMagBits, mb = ub & kMagBits, mc = uc & kMagBits;
+    const bool ok = ((((ua ^ ub) | (ua ^ uc)) >> 63) == 0) && mag_ok(ma) && mag_ok(mb) && mag_ok(mc);
+    double r = (mb < ma) ? b : a;
+    const unsigned long long mr = (mb < ma) ? mb : ma;
+    r = (mc < mr) ? c : r;
+    return ok ? r : 0.0;
+}
+
+// one-sided speeds: ap = max(ap, h), am = min(am, h) for ap >= 0 >= am, NaN ignored
+template <typename T> __device__ __forceinline__ void speed_range(T h, T& ap, T& am) {
+    ap = tmax(ap, h);
+    am = tmin(am, h);
+}
+__device__ __forceinline__ void speed_range(double h, double& ap, double& am) {
+    const unsigned long long u = ubits(h), m = u & kMagBits;
+    if (mag_ok(m)) {
+        if ((u >> 63) == 0) { if (m > ubits(ap)) ap = h; }
+        else if (m > (ubits(am) & kMagBits)) am = h;
+    }
+}
 
 template <typename T>
 struct Side {  // one-dimensional limited quadratic on the cell on one side of the node
@@ -215,10 +253,13 @@ struct Side {  // one-dimensional limited quadratic on the cell on one side of t
     T S;  // limited second difference on that cell
 };
 
-// x times the limiter parameter theta.  A hardware float or double product is cheapest; a
-// double-word product is not, so theta = 1 or 2 is applied there as an exact scaling.
+// x times the limiter parameter theta.  A float product is cheapest; on the FP64 pipe and in
+// double words theta = 1 is skipped, and double words apply theta = 2 as an exact scaling.
 __device__ __forceinline__ float theta_mul(float x, float theta, int) { return theta * x; }
-__device__ __forceinline__ double theta_mul(double x, double theta, int) { return theta * x; }
+__device__ __forceinline__ double theta_mul(double x, double theta, int theta_code) {
+    if (theta_code == 1) return x;
+    return theta * x;
+}
 __device__ __forceinline__ df theta_mul(df x, df theta, int theta_code) {
     if (theta_code == 1) return x;
     if (theta_code == 2) return scale2(x, 2.0f);
@@ -258,19 +299,21 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
             T p = px[s], q = qy[t];
             T r2 = p * p + q * q;
             T Hp = T(0), Hq = T(0);
-            if (r2 > T(0)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
-            ap = tmax(ap, Hp); am = tmin(am, Hp);
-            bp = tmax(bp, Hq); bm = tmin(bm, Hq);
+            if (tpos(r2)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
+            speed_range(Hp, ap, am);
+            speed_range(Hq, bp, bm);
         }
     // Step 4 weights (G1, G5): w(s,t) = nx[s] ny[t] / (dxw dyw), one reciprocal
     T nx[2], ny[2], dxw, dyw;
-    if (ap - am > T(0)) { nx[0] = -am; nx[1] = ap; dxw = ap - am; }
+    dxw = ap - am;
+    if (tpos(dxw)) { nx[0] = -am; nx[1] = ap; }
     else { nx[0] = T(0.5); nx[1] = T(0.5); dxw = T(1); }
-    if (bp - bm > T(0)) { ny[0] = -bm; ny[1] = bp; dyw = bp - bm; }
+    dyw = bp - bm;
+    if (tpos(dyw)) { ny[0] = -bm; ny[1] = bp; }
     else { ny[0] = T(0.5); ny[1] = T(0.5); dyw = T(1); }
     const T inv_w = trcp(dxw * dyw);
     const T vdt = v0 * dt_h;                 // v0 dt / h
-    const T half_dt = thalf(dt_h);
+    const T hvdt = thalf(vdt);               // v0 dt / (2 h)
     // Step 3: values at the four intermediate points (G2, G3).  Along each direction the
     // limited quadratic on the side's cell, in cell units: with e the displacement / h and
     // sg = -1 on the + side, +1 on the - side,  X(e) = D e + S e (e + sg) / 2 and
@@ -304,15 +347,17 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
             T p = dX + cross * ey[t];
             T q = dY[t] + cross * ex;
             if (time_level == 0) {
-                T r2 = p * p + q * q;
-                T gx = T(0), gy = T(0);
-                if (r2 > T(0)) { T vr = v0 * trsqrt(r2); gx = vr * p; gy = vr * q; }
-                const T np = p - half_dt * (Sx * gx + cross * gy);
-                const T nq = q - half_dt * (cross * gx + ys[t].S * gy);
-                p = np; q = nq;
+                // (p, q) -= dt/2 Hess grad_(p,q) H, grad H = v0 (p, q) / |(p, q)|
+                const T r2 = p * p + q * q;
+                if (tpos(r2)) {
+                    const T w = hvdt * trsqrt(r2);
+                    const T np = p - w * (Sx * p + cross * q);
+                    const T nq = q - w * (cross * p + ys[t].S * q);
+                    p = np; q = nq;
+                }
             }
             const T s2 = p * p + q * q;
-            const T g = (s2 > T(0)) ? s2 * trsqrt(s2) : T(0);   // h |grad|
+            const T g = tpos(s2) ? s2 * trsqrt(s2) : T(0);   // h |grad|
             const T psi = val - vdt * g;
             accs += ny[t] * psi;
         }

@@ -12,6 +12,8 @@
 //
 // One step = row_forward (R2C of every row, transposed store) -> col_pass (FFT along x2,
 // multiply by K, inverse FFT along x2) -> row_inverse (C2R, tau and max|v0|) -> knp_step.
+#include <type_traits>
+
 #include "fdm_device.cuh"
 #include "fdm_internal.h"
 
@@ -313,8 +315,8 @@ template <typename T> VelLaw<T> make_vel(const fdm_params& p) {
 template <typename T>
 __device__ __forceinline__ T celerity(const VelLaw<T>& v, T tau, T up, double phi_ref) {
     if (v.mode == FDM_V_PRESCRIBED) return v.v0;
-    T fr = T(0);
-    if (v.friction) fr = T(v.tau_y * cos(((double)up + phi_ref) / v.beta));
+    if (!v.friction) return -(v.mobility * tau);
+    const T fr = T(v.tau_y * cos(((double)up + phi_ref) / v.beta));
     return v.mobility * (fr - tau);
 }
 
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
     const cpx<T>* z = A;
     T vmax = T(0);
     bool bad = false;
+    unsigned long long vbits = 0ull;  // FP64: max of |v0| as magnitude bits (a NaN wins)
     const T* up = reinterpret_cast<const T*>(s_cur ? a.phi1 : a.phi0);
     if (up) up += inst * nn;
     const double phi_ref = (sci && a.vel.friction) ? sci->phi_ref : 0.0;
@@ -392,8 +395,14 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
             T u0 = T(0), u1 = T(0);
             if (need_up) { u0 = up[o]; u1 = up[o + 1]; }
             T c0 = celerity(a.vel, v.x, u0, phi_ref), c1 = celerity(a.vel, v.y, u1, phi_ref);
-            vmax = tmax(vmax, tmax(tabs(c0), tabs(c1)));
-            bad |= (c0 != c0) || (c1 != c1);
+            if constexpr (std::is_same<T, double>::value) {
+                const unsigned long long m0 = ubits(c0) & kMagBits, m1 = ubits(c1) & kMagBits;
+                vbits = m0 > vbits ? m0 : vbits;
+                vbits = m1 > vbits ? m1 : vbits;
+            } else {
+                vmax = tmax(vmax, tmax(tabs(c0), tabs(c1)));
+                bad |= (c0 != c0) || (c1 != c1);
+            }
             dst[o] = v.x;
             dst[o + 1] = v.y;
         } else {
@@ -403,7 +412,8 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
     }
     if (a.mode == ROW_TAU) {
         // NaN-aware block max through the bit pattern of |v| (max is exact in any precision)
-        unsigned long long bits = bad ? 0x7ff8000000000000ull : abs_bits((double)vmax);
+        unsigned long long bits = vbits;
+        if constexpr (!std::is_same<T, double>::value) bits = bad ? 0x7ff8000000000000ull : abs_bits((double)vmax);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
