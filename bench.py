@@ -253,7 +253,8 @@ def run_ours(args, world, rank, local):
         dom = max(phase_mean, key=phase_mean.get)
         bpc = bytes_per_cell(elt)
         results[prec] = {"total_ms": t_max, "phase_ms": phase_mean, "dominant": dom,
-                         "clocks": clk.summary(), "info": info, "bpc": bpc, "sim": sim}
+                         "clocks": clk.summary(), "info": info, "bpc": bpc, "sim": sim,
+                         "launch": sim.launch_config()}
 
     primary = args.precision if args.precision != "all" else "fp64"
     r = results[primary]
@@ -308,7 +309,7 @@ def run_ours(args, world, rank, local):
         extra[prec] = {"value": cells * K * world / (rr["total_ms"] / 1e3),
                        "ms_per_step": rr["total_ms"] / K,
                        "phase_ms": {k: round(v, 5) for k, v in rr["phase_ms"].items()},
-                       "roofline": rl,
+                       "roofline": rl, "launch": rr["launch"],
                        "t_end": rr["info"].t, "clocks": rr["clocks"]}
 
     if rank == 0:
@@ -321,7 +322,8 @@ def run_ours(args, world, rank, local):
                                    "RMS|alpha|=0.1, M=1, E=1, nu=0.3, strain ramp 1e-4/step, CFL 0.4, "
                                    "minmod" % (n, n),
                        "n": n, "precision": primary, "l2": "flushed (256 MiB write) before every timed step",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "launch": r["launch"]},
             "roofline": roof,
             "clocks": r["clocks"],
             "e2e": e2e,

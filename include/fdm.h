@@ -80,7 +80,23 @@ typedef struct {
                                 FDM_DF64: fields/FFT/stencil in double-word arithmetic (two
                                 FP32 words, ~48-bit significand, on the FP32 pipes), scalars
                                 in FP64; FP64 accuracy class at FP32-pipe speed             */
+    int32_t autotune;        /* 1: at creation, time the candidate launch shapes of the step
+                                kernels on this GPU and keep the fastest (cached per device,
+                                precision, grid and instance count for the process); 0: fixed
+                                heuristic shapes.  Every shape computes bit-identical values. */
 } fdm_params;
+
+/* Launch shapes of the step kernels of a handle (or of a batch instance's group). */
+typedef struct {
+    int32_t rows_per_block;      /* rows of U13 per block of the row FFT kernels               */
+    int32_t cols_per_block;      /* spectral columns per block of the column kernel            */
+    int32_t stencil_block_rows;  /* stencil block: 32 x stencil_block_rows threads             */
+    int32_t stencil_nodes;       /* nodes per stencil thread, stacked along x2                 */
+    int32_t stencil_min_blocks;  /* blocks per SM the stencil's register budget keeps resident */
+    int32_t tuned;               /* 1: chosen by timing on this GPU, 0: heuristic              */
+    double kernel_us[4];         /* tuned: best measured time of each step kernel (row forward,
+                                    column pass, row inverse, stencil) in microseconds; else 0 */
+} fdm_launch_config;
 
 /* Scalars after the last step of a call.  The sums are over all nodes of the staggered
  * Nye components a12 = (U_{j+1,k} - U_{jk})/dx, a11 = -(U_{j,k+1} - U_{jk})/dx; the total
@@ -108,7 +124,7 @@ enum {
 
 /* Fills p with the defaults: nz = 0, nh = 4, dx = 1, E = 1, nu = 0.3, prescribed v0 = 1,
  * M = 1, tau_y = 0, beta = 1, theta = 1, cfl = 0.5, dt_max = 0, stress loading 0,
- * midpoint time level, FP64.  n1 = n2 = 0 (must be set). */
+ * midpoint time level, FP64, autotune = 1.  n1 = n2 = 0 (must be set). */
 void fdm_default_params(fdm_params *p);
 
 /* Bytes of device memory a handle with these parameters holds (0 if invalid). */
@@ -171,6 +187,22 @@ fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
 
+/* Launch shapes the handle's step kernels use (see fdm_params.autotune). */
+fdm_status fdm_get_launch_config(const fdm_handle *h, fdm_launch_config *cfg);
+
+/* Pins the launch shapes (e.g. a configuration stored from an earlier run): rows and
+ * columns per block and the stencil's (block rows, nodes, min blocks) must be one of the
+ * candidates of this grid and precision (FDM_ERR_INVALID_ARG otherwise; tuned and
+ * kernel_us are ignored).  Waits for the stream; FDM_ERR_STATE while a step is partially
+ * enqueued.  Results are the same for every shape. */
+fdm_status fdm_set_launch_config(fdm_handle *h, const fdm_launch_config *cfg);
+
+/* The configurations the autotuner times for these parameters (no GPU needed): entry i
+ * pairs the i-th candidate of each kernel, cycling through the shorter lists, so that every
+ * candidate of every kernel appears.  Writes min(count, max) entries to out (may be NULL
+ * when max is 0) and returns count, or 0 for invalid parameters. */
+int32_t fdm_launch_candidates(const fdm_params *p, fdm_launch_config *out, int32_t max);
+
 /* Static solve that allocates no device memory (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate -- e.g. a process whose HBM is already
  * fully handed out to other buffers, or an embedding that forbids allocations outside its
@@ -231,6 +263,9 @@ fdm_status fdm_batch_read_fields(fdm_batch *b, int32_t i, uint32_t mask, double 
 
 /* Kernel launches one batched step issues (kernels per step x groups). */
 int32_t fdm_batch_launches_per_step(const fdm_batch *b);
+
+/* Launch shapes of the group holding instance i. */
+fdm_status fdm_batch_get_launch_config(const fdm_batch *b, int32_t i, fdm_launch_config *cfg);
 
 /* Frees everything; NULL-safe. */
 void fdm_batch_destroy(fdm_batch *b);

@@ -43,7 +43,8 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_static_solve_noalloc", "fdm_batch_create", "fdm_batch_device_bytes",
            "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget", "fdm_batch_enqueue_steps",
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
-           "fdm_batch_destroy"]
+           "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
+           "fdm_set_launch_config", "fdm_launch_candidates"]
 
 
 class CParams(C.Structure):
@@ -56,7 +57,20 @@ class CParams(C.Structure):
                 ("loading_mode", C.c_int32),
                 ("sigma_bar13", C.c_double), ("eps_bar13_0", C.c_double),
                 ("eps_bar13_rate", C.c_double),
-                ("time_level", C.c_int32), ("precision", C.c_int32)]
+                ("time_level", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32)]
+
+
+class CLaunchConfig(C.Structure):
+    _fields_ = [("rows_per_block", C.c_int32), ("cols_per_block", C.c_int32),
+                ("stencil_block_rows", C.c_int32), ("stencil_nodes", C.c_int32),
+                ("stencil_min_blocks", C.c_int32), ("tuned", C.c_int32),
+                ("kernel_us", C.c_double * 4)]
+
+
+def _launch_config(c: CLaunchConfig) -> dict:
+    d = {f: getattr(c, f) for f, _ in CLaunchConfig._fields_ if f != "kernel_us"}
+    d["kernel_us"] = [float(x) for x in c.kernel_us]
+    return d
 
 
 class CStepInfo(C.Structure):
@@ -92,6 +106,7 @@ class Params:
     eps_bar13_rate: float = 0.0
     time_level: int = T_MIDPOINT
     precision: int = FP64
+    autotune: int = 1
 
     def to_c(self) -> CParams:
         return CParams(**asdict(self))
@@ -164,6 +179,14 @@ def load():
     lib.fdm_batch_launches_per_step.restype = C.c_int32
     lib.fdm_batch_destroy.argtypes = [H]
     lib.fdm_batch_destroy.restype = None
+    lib.fdm_get_launch_config.argtypes = [H, C.POINTER(CLaunchConfig)]
+    lib.fdm_get_launch_config.restype = C.c_int
+    lib.fdm_batch_get_launch_config.argtypes = [H, C.c_int32, C.POINTER(CLaunchConfig)]
+    lib.fdm_batch_get_launch_config.restype = C.c_int
+    lib.fdm_set_launch_config.argtypes = [H, C.POINTER(CLaunchConfig)]
+    lib.fdm_set_launch_config.restype = C.c_int
+    lib.fdm_launch_candidates.argtypes = [C.POINTER(CParams), C.POINTER(CLaunchConfig), C.c_int32]
+    lib.fdm_launch_candidates.restype = C.c_int32
     for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
                  "fdm_batch_enqueue_steps", "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields"):
         getattr(lib, name).restype = C.c_int
@@ -310,6 +333,20 @@ class FDM:
     def kernels_per_step(self) -> int:
         return int(self.lib.fdm_kernels_per_step(self.h))
 
+    def launch_config(self) -> dict:
+        """Launch shapes of the step kernels (autotuned or heuristic)."""
+        c = CLaunchConfig()
+        _check(self.lib.fdm_get_launch_config(self.h, C.byref(c)), "fdm_get_launch_config")
+        return _launch_config(c)
+
+    def set_launch_config(self, cfg: dict):
+        """Pin the launch shapes (keys as returned by ``launch_config``)."""
+        c = CLaunchConfig()
+        for f, _ in CLaunchConfig._fields_:
+            if f in cfg and f not in ("kernel_us", "tuned"):
+                setattr(c, f, int(cfg[f]))
+        _check(self.lib.fdm_set_launch_config(self.h, C.byref(c)), "fdm_set_launch_config")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.fdm_destroy(self.h)
@@ -333,6 +370,16 @@ def _params_array(params):
     for i, p in enumerate(params):
         arr[i] = p.to_c()
     return arr
+
+
+def launch_candidates(params: "Params") -> list:
+    """The launch configurations the autotuner times for these parameters (no GPU needed)."""
+    lib = load()
+    cp = params.to_c()
+    n = int(lib.fdm_launch_candidates(C.byref(cp), None, 0))
+    arr = (CLaunchConfig * max(n, 1))()
+    lib.fdm_launch_candidates(C.byref(cp), arr, n)
+    return [_launch_config(arr[i]) for i in range(n)]
 
 
 def batch_device_bytes(params) -> int:
@@ -394,6 +441,12 @@ class Batch:
 
     def launches_per_step(self) -> int:
         return int(self.lib.fdm_batch_launches_per_step(self.h))
+
+    def launch_config(self, i: int) -> dict:
+        """Launch shapes of the group holding instance i."""
+        c = CLaunchConfig()
+        _check(self.lib.fdm_batch_get_launch_config(self.h, i, C.byref(c)), "fdm_batch_get_launch_config")
+        return _launch_config(c)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,6 +1,6 @@
 """Compile the CUDA library ``libfdm_gb300.so`` (sm_103a) in-tree with nvcc.
 
-The two translation units are compiled in parallel and linked into one shared library
+The translation units are compiled in parallel and linked into one shared library
 with a static CUDA runtime; the C ABI is declared in ``include/fdm.h``.
 """
 import os
@@ -9,7 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfdm_gb300.so")
-SOURCES = ["fdm_kernels.cu", "fdm_capi.cu", "fdm_batch.cu", "fdm_noalloc.cu"]
+SOURCES = ["fdm_kernels.cu", "fdm_tune.cu", "fdm_capi.cu", "fdm_batch.cu", "fdm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 

@@ -40,7 +40,7 @@ bool same_params(const fdm_params& a, const fdm_params& b) {
            a.tau_y == b.tau_y && a.beta == b.beta && a.theta == b.theta && a.cfl == b.cfl &&
            a.dt_max == b.dt_max && a.loading_mode == b.loading_mode && a.sigma_bar13 == b.sigma_bar13 &&
            a.eps_bar13_0 == b.eps_bar13_0 && a.eps_bar13_rate == b.eps_bar13_rate &&
-           a.time_level == b.time_level && a.precision == b.precision;
+           a.time_level == b.time_level && a.precision == b.precision && a.autotune == b.autotune;
 }
 
 bool index_ok(const fdm_batch* b, int32_t i) { return b && i >= 0 && i < b->count; }
@@ -205,6 +205,13 @@ fdm_status fdm_batch_read_fields(fdm_batch* b, int32_t i, uint32_t mask, double*
 
 int32_t fdm_batch_launches_per_step(const fdm_batch* b) {
     return b ? (int32_t)(kKernelsPerStep * b->groups.size()) : 0;
+}
+
+fdm_status fdm_batch_get_launch_config(const fdm_batch* b, int32_t i, fdm_launch_config* cfg) {
+    if (!index_ok(b, i) || !cfg) return FDM_ERR_INVALID_ARG;
+    const fdm_batch::Group& G = b->groups[b->group_of[i]];
+    FDM_DISPATCH(G.prec, launch_config<T>(G.d.geom, cfg));
+    return FDM_OK;
 }
 
 void fdm_batch_destroy(fdm_batch* b) {

@@ -74,7 +74,7 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     if ((st = A.alloc(&d.tw2, (size_t)p.n2 * 2 * sizeof(T)))) return st;
     if ((st = A.alloc(&d.pt1, (size_t)(pass_table_len(p.n1 / 2) + 1) * 2 * sizeof(T)))) return st;
     if ((st = A.alloc(&d.pt2, (size_t)(pass_table_len(p.n2) + 1) * 2 * sizeof(T)))) return st;
-    if ((st = A.alloc((void**)&d.row_partials, (size_t)count * d.geom.row_blocks * sizeof(double)))) return st;
+    if ((st = A.alloc((void**)&d.row_partials, (size_t)count * p.n2 * sizeof(double)))) return st;
     d.red_blocks = red_blocks_for(n);
     if ((st = A.alloc((void**)&d.red, (size_t)6 * d.red_blocks * sizeof(double)))) return st;
     if ((st = A.alloc((void**)&d.sc, (size_t)count * sizeof(fdm_dev_scalars)))) return st;
@@ -104,6 +104,13 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     FDM_CK(cudaStreamSynchronize(s));
     A.release(dw3);
     A.release(dK64);
+    if (p.autotune) {
+        // times the candidate launch shapes on this group's buffers, then clears them again
+        FDM_CK(autotune_group<T>(d, s));
+        FDM_CK(cudaMemsetAsync(d.sc, 0, (size_t)count * sizeof(fdm_dev_scalars), s));
+        FDM_CK(cudaMemsetAsync(d.phi[0], 0, cn * sizeof(T), s));
+        FDM_CK(cudaStreamSynchronize(s));
+    }
     return FDM_OK;
 }
 
@@ -332,6 +339,7 @@ void fdm_default_params(fdm_params* p) {
     p->mobility = 1.0;
     p->tau_y = 0.0;
     p->beta = 1.0;
+    p->autotune = 1;
     p->theta = 1.0;
     p->cfl = 0.5;
     p->dt_max = 0.0;
@@ -344,7 +352,7 @@ size_t fdm_device_bytes(const fdm_params* p) {
     if (!params_valid(p)) return 0;
     size_t n = (size_t)p->n1 * p->n2, e = elt_size(p);
     size_t nk = (size_t)(p->n1 / 2 + 1) * (p->n2 / 2 + 1);
-    return 5 * n * e + nk * e + (size_t)(p->n1 + p->n2) * 2 * e + 64 * 1024;
+    return 5 * n * e + nk * e + (size_t)(p->n1 + p->n2) * 4 * e + (size_t)p->n2 * sizeof(double) + 64 * 1024;
 }
 
 fdm_status fdm_create(const fdm_params* p, void* stream, fdm_handle** out) {
@@ -503,6 +511,32 @@ fdm_status fdm_get_info(fdm_handle* h, fdm_step_info* info) {
 int32_t fdm_kernels_per_step(const fdm_handle* h) {
     (void)h;
     return kKernelsPerStep;
+}
+
+fdm_status fdm_get_launch_config(const fdm_handle* h, fdm_launch_config* cfg) {
+    if (!h || !cfg) return FDM_ERR_INVALID_ARG;
+    FDM_DISPATCH(h->prec, launch_config<T>(h->d.geom, cfg));
+    return FDM_OK;
+}
+
+int32_t fdm_launch_candidates(const fdm_params* p, fdm_launch_config* out, int32_t max) {
+    if (!params_valid(p) || max < 0 || (max > 0 && !out)) return 0;
+    int count = 0;
+    FDM_DISPATCH(p->precision, count = launch_candidates<T>(*p, out, max));
+    return count;
+}
+
+fdm_status fdm_set_launch_config(fdm_handle* h, const fdm_launch_config* cfg) {
+    if (!h || !cfg) return FDM_ERR_INVALID_ARG;
+    if (h->next_phase != 0) return FDM_ERR_STATE;
+    bool ok = false;
+    LaunchGeom g{};
+    FDM_DISPATCH(h->prec, ok = geometry_from_config<T>(h->d.p, *cfg, &g));
+    if (!ok) return FDM_ERR_INVALID_ARG;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    h->graphs.destroy();   // captured with the old shapes
+    h->d.geom = g;
+    return FDM_OK;
 }
 
 void fdm_destroy(fdm_handle* h) {

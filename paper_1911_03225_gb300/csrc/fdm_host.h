@@ -39,6 +39,50 @@ inline bool params_valid(const fdm_params* p) {
         return false;
     if (p->time_level != FDM_T_MIDPOINT && p->time_level != FDM_T_LITERAL) return false;
     if (p->precision != FDM_FP64 && p->precision != FDM_MIXED && p->precision != FDM_DF64) return false;
+    if (p->autotune != 0 && p->autotune != 1) return false;
+    return true;
+}
+
+// launch shapes of a group, as reported by the C ABI
+template <typename T>
+inline void launch_config(const LaunchGeom& g, fdm_launch_config* c) {
+    std::memset(c, 0, sizeof(*c));
+    c->rows_per_block = g.R;
+    c->cols_per_block = g.C;
+    knp_shape_info<T>(g.knp_shape, &c->stencil_block_rows, &c->stencil_nodes, &c->stencil_min_blocks);
+    c->tuned = g.tuned;
+    for (int k = 0; k < kKernelsPerStep; ++k) c->kernel_us[k] = g.tuned ? g.kernel_us[k] : 0.0;
+}
+
+// the configurations the autotuner times (candidate i of each kernel, cycling)
+template <typename T>
+inline int launch_candidates(const fdm_params& p, fdm_launch_config* out, int max) {
+    int Rs[8], Cs[8];
+    const int nR = row_candidates<T>(p.n1, p.n2, Rs, 8), nC = col_candidates<T>(p.n1, p.n2, Cs, 8);
+    if (nR == 0 || nC == 0) return 0;
+    int n = nR > nC ? nR : nC;
+    if (kKnpShapes > n) n = kKnpShapes;
+    for (int i = 0; i < n && i < max; ++i)
+        launch_config<T>(geometry<T>(p.n1, p.n2, Rs[i % nR], Cs[i % nC], i % kKnpShapes), &out[i]);
+    return n;
+}
+
+// launch shapes from a configuration, if it names candidates of this grid and precision
+template <typename T>
+inline bool geometry_from_config(const fdm_params& p, const fdm_launch_config& c, LaunchGeom* g) {
+    int Rs[8], Cs[8];
+    const int nR = row_candidates<T>(p.n1, p.n2, Rs, 8), nC = col_candidates<T>(p.n1, p.n2, Cs, 8);
+    bool r_ok = false, c_ok = false;
+    for (int i = 0; i < nR; ++i) r_ok = r_ok || Rs[i] == c.rows_per_block;
+    for (int i = 0; i < nC; ++i) c_ok = c_ok || Cs[i] == c.cols_per_block;
+    int shape = -1;
+    for (int k = 0; k < kKnpShapes && shape < 0; ++k) {
+        int ty, npt, minb;
+        knp_shape_info<T>(k, &ty, &npt, &minb);
+        if (ty == c.stencil_block_rows && npt == c.stencil_nodes && minb == c.stencil_min_blocks) shape = k;
+    }
+    if (!r_ok || !c_ok || shape < 0) return false;
+    *g = geometry<T>(p.n1, p.n2, c.rows_per_block, c.cols_per_block, shape);
     return true;
 }
 

@@ -22,12 +22,18 @@ struct fdm_dev_scalars {
     long long steps_left;          // gated (batched) launches: steps this instance may still take
 };
 
+constexpr int kKernelsPerStep = 4;
+constexpr int kKnpShapes = 4;  // stencil block shapes per precision (shape 0 = default)
+
 struct LaunchGeom {
     int R;             // rows per block of the row kernels
     int C;             // spectral columns per block of the column kernel
     size_t row_smem, col_smem;
     int row_blocks, col_blocks;
     int row_threads, col_threads;  // threads per block of the row / column FFT kernels
+    int knp_shape;     // stencil block shape, index in [0, kKnpShapes)
+    int tuned;         // chosen by the autotuner
+    double kernel_us[kKernelsPerStep];  // tuned: best time of each step kernel
 };
 
 // One group of `count` instances with identical parameters.  Every buffer holds `count`
@@ -46,14 +52,25 @@ struct Dev {
     void* tw2;             // cpx<T> [n2]
     void* pt1;             // cpx<T> pass twiddle tables of the n1/2-point row transform
     void* pt2;             // cpx<T> pass twiddle tables of the n2-point column transform
-    double* row_partials;  // [count][row_blocks]
+    double* row_partials;  // [count][n2]: FP64 sum of each row of U13
     double* red;           // reduction partials [6 * red_blocks]
     int red_blocks;
     fdm_dev_scalars* sc;   // [count]
     double phi_ref_host;   // single instance: host copy of sc[0].phi_ref
 };
 
-template <typename T> LaunchGeom geometry(int n1, int n2);
+// Launch shapes: R rows per row-kernel block and C columns per column-kernel block (0:
+// heuristic choice), stencil shape index.  Candidate lists hold every valid R or C.
+template <typename T> LaunchGeom geometry(int n1, int n2, int R = 0, int C = 0, int knp_shape = 0);
+template <typename T> int row_candidates(int n1, int n2, int* out, int max);
+template <typename T> int col_candidates(int n1, int n2, int* out, int max);
+template <typename T> void knp_shape_info(int shape, int* ty, int* npt, int* minb);
+// Times the candidate shapes on the group's buffers (their contents are overwritten) and
+// stores the fastest in d.geom; results are cached per device, precision, grid, instance
+// count and scheme variant.  Leaves the scalars of every instance zeroed.
+template <typename T> cudaError_t autotune_group(Dev& d, cudaStream_t s);
+// fill U13 (buffer 0 of every instance) with a smooth synthetic field with kinks
+template <typename T> void launch_tune_fill(const Dev& d, cudaStream_t s);
 template <typename T> cudaError_t configure_kernels();
 // step launches read U13 from phi[sc[i].cur] of every instance and write the other buffer
 template <typename T> void launch_step(const Dev& d, cudaStream_t s);
@@ -70,8 +87,6 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
                      cudaStream_t s);
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
                          cudaStream_t s);
-
-constexpr int kKernelsPerStep = 4;
 
 struct df;  // double-word type (fdm_df.cuh)
 

@@ -85,9 +85,16 @@ __device__ __forceinline__ void inst_state(const InstCtl& c, int inst, int* run,
     *cur = k;
 }
 
+// Neumaier step s + x with compensation c (FP64; the magnitude test on bit patterns)
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+    const double t = s + x;
+    c += ((ubits(s) & kMagBits) >= (ubits(x) & kMagBits)) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 // ------------------------------------------------------------------ row forward (R2C)
-// grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional per-block FP64 sum of
-// the loaded values (for <U13>).
+// grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional FP64 sum of each row
+// (for <U13>), in an order fixed by the row alone, so that results do not depend on R.
 template <typename T>
 __global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
                                                           int n1, int n2, int R,
@@ -103,14 +110,12 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const 
     const size_t nn = (size_t)n1 * n2;
     const T* src = (s_cur ? src1 : src0) + inst * nn;
     spec += inst * (nn / 2);
-    if (row_partials) row_partials += (size_t)inst * gridDim.x;
+    if (row_partials) row_partials += (size_t)inst * n2;
     const int L = n1 >> 1;
     const int ld = padded_len(L);  // padded sequence stride (bank spread for the transposed store)
-    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);                 // R * ld elements
-    double* red = reinterpret_cast<double*>(A + (size_t)R * ld);     // 32 doubles after them
+    cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);  // R * ld elements
     const int y0 = blockIdx.x * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
-    T acc = T(0), comp = T(0);  // compensated (Kahan) per-thread sum in the field's type
     const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
     const int total = R * L, step = blockDim.x;
     for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
@@ -123,20 +128,27 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const 
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int e = e0 + u * step;
-            if (e < total) {
-                T y = (v[u].x + v[u].y) - comp;
+            if (e < total) A[(e >> lL) * ld + swz(e & (L - 1))] = v[u];
+        }
+    }
+    __syncthreads();
+    if (row_partials) {
+        // one warp per row: lane l sums the pairs l, l + 32, ... (compensated, in the field's
+        // type), then a fixed FP64 butterfly over the lanes
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = threadIdx.x >> 5; r < R; r += nw) {
+            T acc = T(0), comp = T(0);
+            for (int m = lane; m < L; m += 32) {
+                const cpx<T> v = A[r * ld + swz(m)];
+                T y = (v.x + v.y) - comp;
                 T t = acc + y;
                 comp = (t - acc) - y;
                 acc = t;
-                A[(e >> lL) * ld + swz(e & (L - 1))] = v[u];
             }
+            const double rs = warp_sum((double)acc - (double)comp);
+            if (lane == 0) row_partials[y0 + r] = rs;
         }
     }
-    if (row_partials) {
-        double s = block_sum((double)acc - (double)comp, red);
-        if (threadIdx.x == 0) row_partials[blockIdx.x] = s;
-    }
-    __syncthreads();
     smem_fft_ip(A, L, R, ld, -1, pt1);
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
@@ -158,13 +170,14 @@ __global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const 
 //   COL_DERIV2N   alpha11-hat = -i xi2 U-hat (odd symbol, 0 at the x2 Nyquist index)
 //   COL_FWD       forward transform only (no normalisation)
 //   COL_INV       inverse transform only
+constexpr int kRedLanes = 256;  // lanes of the <U13> reduction in the column kernel
 enum ColMode { COL_K = 0, COL_DERIV1 = 1, COL_DERIV2N = 2, COL_FWD = 3, COL_INV = 4 };
 
 template <typename T>
 struct ColArgs {
     fdm_params p;
     int mode;
-    const double* row_partials;  // COL_K: per-row-block sums of U13 (nparts entries)
+    const double* row_partials;  // COL_K: per-row sums of U13 (nparts = n2 entries)
     int nparts;
     fdm_dev_scalars* sc;         // COL_K: scalars of instance 0 (block 0 writes mean/eps/sigma)
     int gated;                   // COL_K: honour the instances' step budgets
@@ -200,7 +213,7 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const cpx<T>* in, cpx<T>
     const int ln2 = 31 - __clz(n2);
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     __shared__ double s_sigma;
-    __shared__ double s_red[32];
+    __shared__ double s_red[kRedLanes];
     __shared__ int s_run, s_cur;
     const int inst = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -231,15 +244,21 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const cpx<T>* in, cpx<T>
         }
     }
     if (a.mode == COL_K && kx0 == 0) {
-        // <U13> from the row-block sums (fixed order, compensated per thread), then the
-        // loading state of this step (Sec. 5.1)
-        double s = 0.0, c = 0.0;
-        for (int i = threadIdx.x; parts && i < a.nparts; i += blockDim.x) {
-            double x = parts[i], t = s + x;
-            c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-            s = t;
+        // <U13> from the row sums, then the loading state of this step (Sec. 5.1).  The
+        // order is fixed by n2 alone: kRedLanes compensated lane sums over a stride, then a
+        // fixed tree (results do not depend on the launch shape)
+        for (int v = threadIdx.x; v < kRedLanes; v += blockDim.x) {
+            double s = 0.0, c = 0.0;
+            for (int i = v; parts && i < a.nparts; i += kRedLanes) neumaier_add(s, c, parts[i]);
+            s_red[v] = s + c;
         }
-        double tot = block_sum(s + c, s_red);
+        __syncthreads();
+        double tot = 0.0;
+        if (threadIdx.x < 32) {
+            double s = 0.0, c = 0.0;
+            for (int v = threadIdx.x; v < kRedLanes; v += 32) neumaier_add(s, c, s_red[v]);
+            tot = warp_sum(s + c);
+        }
         if (threadIdx.x == 0) {
             double mean = parts ? sci->phi_ref + tot / ((double)n1 * (double)n2) : sci->mean_up13;
             double eps, sig;
@@ -340,7 +359,6 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
     const int L = n1 >> 1;
     const int ld = padded_len(L);
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
-    double* red = reinterpret_cast<double*>(A + (size_t)R * ld);
     __shared__ int s_run, s_cur;
     const int inst = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -421,11 +439,10 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
         }
         if ((threadIdx.x & 31) == 0) atomicMax(&sci->vmax_bits, bits);
     }
-    (void)red;
 }
 
 // ------------------------------------------------------------------ KNP stencil
-constexpr int TX = 32, TY = 8;
+constexpr int TX = 32;  // stencil block width (threads along x1)
 
 template <typename T>
 struct KnpArgs {
@@ -450,20 +467,31 @@ __device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, dou
     return dtd;
 }
 
-// resident blocks per SM the register allocation must allow (FP64 needs more registers),
-// and nodes per thread stacked along x2 (amortises the block's load phases and halo)
-template <typename T> struct KnpOcc { static constexpr int value = 4; static constexpr int npt = 4; };
-template <> struct KnpOcc<double> { static constexpr int value = 2; static constexpr int npt = 2; };
-template <> struct KnpOcc<df> { static constexpr int value = 3; static constexpr int npt = 2; };
+// Stencil block shapes: block (TX, ty) threads, each updating npt nodes stacked along x2,
+// with a register budget that keeps minb blocks resident per SM.  Shape 0 is the default;
+// the autotuner times all of them.  Every shape computes the same node values.
+template <typename T> struct KnpShapes;
+template <> struct KnpShapes<float> {
+    static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {4, 2, 2, 4},
+                         minb[kKnpShapes] = {4, 4, 2, 3};
+};
+template <> struct KnpShapes<double> {
+    static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 4},
+                         minb[kKnpShapes] = {2, 2, 1, 2};
+};
+template <> struct KnpShapes<df> {
+    static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 2},
+                         minb[kKnpShapes] = {3, 3, 1, 2};
+};
 
-// grid (n1 / tx, n2 / (TY npt), instances); block (tx, TY); thread (i, j) updates the
-// nodes (bx + i, by + j + k TY), k < npt
-template <typename T>
-__global__ void __launch_bounds__(TX * TY, KnpOcc<T>::value) knp_step_kernel(const T* phi0, const T* phi1,
-                                                                             const T* __restrict__ tau0,
-                                                                             int n1, int n2, int npt,
-                                                                             KnpArgs<T> a) {
-    constexpr int NPT = KnpOcc<T>::npt;
+// grid (n1 / tx, n2 / (ty npt), instances); block (tx, ty); thread (i, j) updates the
+// nodes (bx + i, by + j + k ty), k < npt
+template <typename T, int V>
+__global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V])
+    knp_step_kernel(const T* phi0, const T* phi1, const T* __restrict__ tau0, int n1, int n2, int npt,
+                    KnpArgs<T> a) {
+    constexpr int TY = KnpShapes<T>::ty[V];
+    constexpr int NPT = KnpShapes<T>::npt[V];
     __shared__ T tile[TY * NPT + 4][TX + 4];
     __shared__ T s_dt;
     __shared__ int s_run, s_cur;
@@ -668,12 +696,39 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
 }
 
 // ------------------------------------------------------------------ launchers
-static int pick_rows(int n1, int n2, size_t elt) {
-    // rows per block: as many as fit 40 KB of shared memory (one buffer), at most 16, and at
-    // most 8192 points (1024 threads)
-    size_t per_row = (size_t)padded_len(n1 / 2) * 2 * elt;
+constexpr size_t kMaxDynSmem = 200 * 1024;  // dynamic shared memory the FFT kernels may request
+
+// R rows per row-kernel block is valid when R <= n2, R <= 16, R n1/2 <= 8192 (one radix-8
+// butterfly per thread, at most 1024 threads) and the rows fit the shared-memory limit
+template <typename T> static bool row_ok(int n1, int n2, int R) {
+    return R <= n2 && R <= 16 && R * (n1 / 2) <= 8192 &&
+           (size_t)R * padded_len(n1 / 2) * sizeof(cpx<T>) <= kMaxDynSmem;
+}
+template <typename T> static bool col_ok(int n1, int n2, int C) {
+    return C <= n1 / 2 && C <= 16 && C * n2 <= 8192 && (size_t)C * padded_len(n2) * sizeof(cpx<T>) <= kMaxDynSmem;
+}
+
+template <typename T>
+int row_candidates(int n1, int n2, int* out, int max) {
+    int k = 0;
+    for (int R = 1; R <= 16 && k < max; R *= 2)
+        if (row_ok<T>(n1, n2, R)) out[k++] = R;
+    return k;
+}
+template <typename T>
+int col_candidates(int n1, int n2, int* out, int max) {
+    int k = 0;
+    for (int C = 1; C <= 16 && k < max; C *= 2)
+        if (col_ok<T>(n1, n2, C)) out[k++] = C;
+    return k;
+}
+
+// heuristic shapes: as many rows as fit 40 KB of shared memory (at most 16 and 8192
+// points); columns until a block has 1024 points
+template <typename T> static int pick_rows(int n1, int n2) {
+    const size_t per_row = (size_t)padded_len(n1 / 2) * sizeof(cpx<T>);
     int R = 1;
-    while (R < 16 && (size_t)(2 * R) * per_row <= 40 * 1024 && 2 * R <= n2 && 2 * R * (n1 / 2) <= 8192) R *= 2;
+    while (row_ok<T>(n1, n2, 2 * R) && (size_t)(2 * R) * per_row <= 40 * 1024) R *= 2;
     return R;
 }
 static int pick_cols(int n1, int n2) {
@@ -683,18 +738,45 @@ static int pick_cols(int n1, int n2) {
 }
 
 template <typename T>
-LaunchGeom geometry(int n1, int n2) {
-    LaunchGeom g;
-    g.R = pick_rows(n1, n2, sizeof(T));
-    g.C = pick_cols(n1, n2);
-    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>) + 32 * sizeof(double);
+LaunchGeom geometry(int n1, int n2, int R, int C, int knp_shape) {
+    LaunchGeom g{};
+    g.R = R > 0 ? R : pick_rows<T>(n1, n2);
+    g.C = C > 0 ? C : pick_cols(n1, n2);
+    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>);
     g.col_smem = (size_t)g.C * padded_len(n2) * sizeof(cpx<T>);
     g.row_blocks = n2 / g.R;
     g.col_blocks = (n1 / 2) / g.C;
     // the in-place FFT needs at least one thread per radix-8 butterfly; at least a warp
     g.row_threads = g.R * (n1 / 2) / 8 < 32 ? 32 : g.R * (n1 / 2) / 8;
     g.col_threads = g.C * n2 / 8 < 32 ? 32 : g.C * n2 / 8;
+    g.knp_shape = (knp_shape >= 0 && knp_shape < kKnpShapes) ? knp_shape : 0;
+    g.tuned = 0;
     return g;
+}
+
+template <typename T>
+void knp_shape_info(int shape, int* ty, int* npt, int* minb) {
+    *ty = KnpShapes<T>::ty[shape];
+    *npt = KnpShapes<T>::npt[shape];
+    *minb = KnpShapes<T>::minb[shape];
+}
+
+// smooth periodic U13 with kinks (|sin|) on a per-instance phase: every branch of the
+// stencil is taken as on a real state
+template <typename T>
+__global__ void tune_fill_kernel(T* phi, int n1, int n2, int count) {
+    const size_t n = (size_t)n1 * n2, total = n * count;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int inst = (int)(i / n);
+        const size_t c = i - (size_t)inst * n;
+        const double x = (double)(c % n1) / n1, y = (double)(c / n1) / n2;
+        const double u = sinpi(2.0 * (3.0 * x + 0.1 * inst)) * cospi(4.0 * y) + 0.5 * fabs(sinpi(2.0 * (x + 2.0 * y)));
+        phi[i] = T(0.05 * u);
+    }
+}
+template <typename T>
+void launch_tune_fill(const Dev& d, cudaStream_t s) {
+    tune_fill_kernel<T><<<4 * 152, 256, 0, s>>>((T*)d.phi[0], d.p.n1, d.p.n2, d.count);
 }
 
 template <typename T>
@@ -704,7 +786,7 @@ cudaError_t configure_kernels() {
     const void* fns[3] = {(const void*)row_forward_kernel<T>, (const void*)row_inverse_kernel<T>,
                           (const void*)col_pass_kernel<T>};
     for (const void* f : fns) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
@@ -729,7 +811,7 @@ void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with
     a.p = d.p;
     a.mode = mode;
     a.row_partials = with_mean ? d.row_partials : nullptr;
-    a.nparts = g.row_blocks;
+    a.nparts = d.p.n2;
     a.sc = d.sc;
     a.gated = d.gated;
     a.scl = T(1.0 / ((double)d.p.n1 * (double)d.p.n2));
@@ -757,6 +839,17 @@ void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, doub
                                                                 (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1, a);
 }
 
+template <typename T, int V>
+void launch_knp_shape(const Dev& d, const KnpArgs<T>& a, cudaStream_t s) {
+    constexpr int TY = KnpShapes<T>::ty[V];
+    const int tx = d.p.n1 < TX ? d.p.n1 : TX;
+    int npt = KnpShapes<T>::npt[V];
+    while (npt > 1 && d.p.n2 < TY * npt) npt >>= 1;
+    dim3 grid(d.p.n1 / tx, d.p.n2 / (TY * npt), d.count), block(tx, TY);
+    knp_step_kernel<T, V><<<grid, block, 0, s>>>((const T*)d.phi[0], (const T*)d.phi[1], (const T*)d.tau,
+                                                 d.p.n1, d.p.n2, npt, a);
+}
+
 template <typename T>
 void launch_knp(const Dev& d, cudaStream_t s) {
     KnpArgs<T> a;
@@ -769,12 +862,12 @@ void launch_knp(const Dev& d, cudaStream_t s) {
     a.time_level = d.p.time_level;
     a.sc = d.sc;
     a.gated = d.gated;
-    const int tx = d.p.n1 < TX ? d.p.n1 : TX;
-    int npt = KnpOcc<T>::npt;
-    while (npt > 1 && d.p.n2 < TY * npt) npt >>= 1;
-    dim3 grid(d.p.n1 / tx, d.p.n2 / (TY * npt), d.count), block(tx, TY);
-    knp_step_kernel<T><<<grid, block, 0, s>>>((const T*)d.phi[0], (const T*)d.phi[1], (const T*)d.tau,
-                                              d.p.n1, d.p.n2, npt, a);
+    switch (d.geom.knp_shape) {
+        case 1: launch_knp_shape<T, 1>(d, a, s); break;
+        case 2: launch_knp_shape<T, 2>(d, a, s); break;
+        case 3: launch_knp_shape<T, 3>(d, a, s); break;
+        default: launch_knp_shape<T, 0>(d, a, s); break;
+    }
 }
 
 // one kernel of a step for every instance of the group (Sec. 3.1.1: static solve with U^n,
@@ -865,7 +958,11 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
 
 // explicit instantiations
 #define FDM_INST(T)                                                                                         \
-    template LaunchGeom geometry<T>(int, int);                                                              \
+    template LaunchGeom geometry<T>(int, int, int, int, int);                                               \
+    template int row_candidates<T>(int, int, int*, int);                                                    \
+    template int col_candidates<T>(int, int, int*, int);                                                    \
+    template void knp_shape_info<T>(int, int*, int*, int*);                                                 \
+    template void launch_tune_fill<T>(const Dev&, cudaStream_t);                                            \
     template cudaError_t configure_kernels<T>();                                                            \
     template void launch_step<T>(const Dev&, cudaStream_t);                                                 \
     template void launch_phase<T>(const Dev&, int, cudaStream_t);                                           \

@@ -3,6 +3,7 @@ point declared in include/fdm.h, and rejects bad arguments before touching the d
 import ctypes as C
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -35,14 +36,36 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_params(lib):
     p = binding.default_params(64, 32)
     assert (p.n1, p.n2, p.nz, p.nh, p.dx, p.E, p.nu) == (64, 32, 0, 4, 1.0, 1.0, 0.3)
-    assert p.theta == 1.0 and p.cfl == 0.5 and p.precision == binding.FP64
+    assert p.theta == 1.0 and p.cfl == 0.5 and p.precision == binding.FP64 and p.autotune == 1
     assert binding.device_bytes(p) > 5 * 64 * 32 * 8
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's layout."""
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fdm.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(fdm_params),'
+                   ' offsetof(fdm_params, autotune), sizeof(fdm_launch_config),'
+                   ' offsetof(fdm_launch_config, kernel_us), sizeof(fdm_step_info),'
+                   ' offsetof(fdm_step_info, status)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == [C.sizeof(binding.CParams), binding.CParams.autotune.offset,
+                   C.sizeof(binding.CLaunchConfig), binding.CLaunchConfig.kernel_us.offset,
+                   C.sizeof(binding.CStepInfo), binding.CStepInfo.status.offset]
+
+
+def test_launch_config_rejects_null(lib):
+    cfg = binding.CLaunchConfig()
+    assert lib.fdm_get_launch_config(None, C.byref(cfg)) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_batch_get_launch_config(None, 0, C.byref(cfg)) == binding.FDM_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("field,value", [
     ("n1", 48), ("n1", 8), ("n2", 8192), ("nh", 0), ("nh", 300), ("dx", 0.0), ("nu", 0.5),
     ("theta", 0.5), ("theta", 2.5), ("cfl", 0.0), ("cfl", 1.5), ("velocity_mode", 7),
-    ("loading_mode", 3), ("time_level", 2), ("precision", 3), ("E", -1.0)])
+    ("loading_mode", 3), ("time_level", 2), ("precision", 3), ("E", -1.0), ("autotune", 2)])
 def test_invalid_params_rejected_without_device(lib, field, value):
     p = binding.default_params(64, 64)
     setattr(p, field, value)
