@@ -18,8 +18,9 @@ struct fdm_dev_scalars {
     double mean_up13, eps_bar13, sigma_bar13;  // state at the start of the current step
     double phi_ref;                // mixed precision: U13 = phi_ref + stored value
     int cur;                       // state buffer holding U13 (0 or 1); flipped by each step
-    int pad_;
+    unsigned int ri_count;         // blocks of the inverse row kernel that have finished
     long long steps_left;          // gated (batched) launches: steps this instance may still take
+    double dt_next, dt_h_next;     // dt of the step being taken and dt / dx (set with max |v0|)
 };
 
 constexpr int kKernelsPerStep = 4;

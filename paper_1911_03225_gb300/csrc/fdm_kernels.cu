@@ -339,6 +339,18 @@ __device__ __forceinline__ T celerity(const VelLaw<T>& v, T tau, T up, double ph
     return v.mobility * (fr - tau);
 }
 
+// dt from the CFL rule |v0|max dt / dx = CFL (Sec. 4.3, Sec. 5.2), in FP64
+__device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, double dt_max) {
+    double dtd;
+    if (vmax > 0.0) {
+        dtd = cfl * dx / vmax;
+        if (dt_max > 0.0 && dtd > dt_max) dtd = dt_max;
+    } else {
+        dtd = dt_max > 0.0 ? dt_max : 0.0;
+    }
+    return dtd;
+}
+
 template <typename T>
 struct RowArgs {
     VelLaw<T> vel;
@@ -348,6 +360,7 @@ struct RowArgs {
     fdm_dev_scalars* sc;       // ROW_TAU: scalars of instance 0
     int gated;
     T offset;                  // ROW_PLAIN: added to every output value
+    double cfl, dx, dt_max;    // ROW_TAU: time-step rule (FP64)
 };
 
 template <typename T>
@@ -438,6 +451,20 @@ __global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T
             bits = other > bits ? other : bits;
         }
         if ((threadIdx.x & 31) == 0) atomicMax(&sci->vmax_bits, bits);
+        // the last block of the instance to finish turns max |v0| into this step's dt, once
+        // (every block's maxima are in before its fenced counter increment)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&sci->ri_count, 1u) == gridDim.x - 1) {
+                __threadfence();
+                const double vmax = __longlong_as_double((long long)atomicAdd(&sci->vmax_bits, 0ull));
+                const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
+                sci->dt_next = dtd;
+                sci->dt_h_next = dtd / a.dx;   // the stencil works in cell units
+                sci->ri_count = 0u;
+            }
+        }
     }
 }
 
@@ -447,7 +474,6 @@ constexpr int TX = 32;  // stencil block width (threads along x1)
 template <typename T>
 struct KnpArgs {
     VelLaw<T> vel;
-    double cfl, dx, dt_max;  // time-step rule (FP64)
     T theta;
     int theta_code;          // 1 or 2 when theta is exactly that (exact scaling), else 0
     int time_level;
@@ -455,17 +481,6 @@ struct KnpArgs {
     int gated;
 };
 
-// dt from the CFL rule |v0|max dt / dx = CFL (Sec. 4.3, Sec. 5.2), in FP64
-__device__ __forceinline__ double cfl_dt(double vmax, double cfl, double dx, double dt_max) {
-    double dtd;
-    if (vmax > 0.0) {
-        dtd = cfl * dx / vmax;
-        if (dt_max > 0.0 && dtd > dt_max) dtd = dt_max;
-    } else {
-        dtd = dt_max > 0.0 ? dt_max : 0.0;
-    }
-    return dtd;
-}
 
 // Stencil block shapes: block (TX, ty) threads, each updating npt nodes stacked along x2,
 // with a register budget that keeps minb blocks resident per SM.  Shape 0 is the default;
@@ -493,6 +508,7 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     constexpr int TY = KnpShapes<T>::ty[V];
     constexpr int NPT = KnpShapes<T>::npt[V];
     __shared__ T tile[TY * NPT + 4][TX + 4];
+    __shared__ T s_tau[TY * NPT][TX];
     __shared__ T s_dt;
     __shared__ int s_run, s_cur;
     const int inst = blockIdx.z;
@@ -508,17 +524,17 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
         s_run = run;
         s_cur = cur;
         if (run) {
-            // dt of this step from the max |v0| reduced by the previous kernel; the last block
+            // dt / h of this step, set by the inverse row kernel from max |v0|; the last block
             // of this instance to read it advances the clock, flips the state buffer and clears
             // the running max (every other block has read them by then: each reads before its
             // fenced counter increment)
-            const double vmax = __longlong_as_double((long long)sc->vmax_bits);
-            const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
-            s_dt = T(dtd / a.dx);   // the node update works in cell units (dt / h)
+            s_dt = T(sc->dt_h_next);
             __threadfence();
             const unsigned int total = gridDim.x * gridDim.y;
             if (atomicAdd(&sc->done_count, 1u) == total - 1) {
                 __threadfence();
+                const double vmax = __longlong_as_double((long long)sc->vmax_bits);
+                const double dtd = sc->dt_next;
                 sc->step += 1;
                 sc->t += dtd;
                 sc->dt = dtd;
@@ -537,6 +553,11 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     const T* phi = (s_cur ? phi1 : phi0) + inst * nn;
     T* out = const_cast<T*>(s_cur ? phi0 : phi1) + inst * nn;
     const T* tau = tau0 + inst * nn;
+    const int x = bx + threadIdx.x;
+    T tv[NPT];   // tau13 at this thread's nodes: loads issued ahead of the tile's
+#pragma unroll
+    for (int k = 0; k < NPT; ++k)
+        if (k < npt) tv[k] = tau[(size_t)(by + threadIdx.y + k * TY) * n1 + x];
     for (int ly = threadIdx.y; ly < rows + 4; ly += TY) {
         const int gy = (by + ly - 2) & (n2 - 1);
         for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
@@ -544,9 +565,11 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
             tile[ly][lx] = phi[(size_t)gy * n1 + gx];
         }
     }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k)
+        if (k < npt) s_tau[threadIdx.y + k * TY][threadIdx.x] = tv[k];
     __syncthreads();
     const T dt = s_dt;
-    const int x = bx + threadIdx.x;
     const int lx = threadIdx.x + 2;
     const double phi_ref = a.vel.friction ? sc->phi_ref : 0.0;
 #pragma unroll 1
@@ -554,7 +577,7 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
         const int y = by + threadIdx.y + k * TY;
         const int ly = threadIdx.y + k * TY + 2;
         const T up = tile[ly][lx];
-        const T v0 = celerity(a.vel, tau[(size_t)y * n1 + x], up, phi_ref);
+        const T v0 = celerity(a.vel, s_tau[threadIdx.y + k * TY][threadIdx.x], up, phi_ref);
         auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
         out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
     }
@@ -834,6 +857,9 @@ void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, doub
     a.sc = d.sc;
     a.gated = d.gated;
     a.offset = T(offset);
+    a.cfl = d.p.cfl;
+    a.dx = d.p.dx;
+    a.dt_max = d.p.dt_max;
     dim3 grid(g.row_blocks, count);
     row_inverse_kernel<T><<<grid, g.row_threads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
                                                                 (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1, a);
@@ -854,9 +880,6 @@ template <typename T>
 void launch_knp(const Dev& d, cudaStream_t s) {
     KnpArgs<T> a;
     a.vel = make_vel<T>(d.p);
-    a.cfl = d.p.cfl;
-    a.dx = d.p.dx;
-    a.dt_max = d.p.dt_max;
     a.theta = T(d.p.theta);
     a.theta_code = d.p.theta == 1.0 ? 1 : (d.p.theta == 2.0 ? 2 : 0);
     a.time_level = d.p.time_level;

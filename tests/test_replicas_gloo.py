@@ -30,7 +30,8 @@ seeds = replicas.instance_seeds(4, rank)
 import torch, torch.distributed as dist
 g = [None] * world
 dist.all_gather_object(g, seeds)
-print(json.dumps({"rank": rank, "world": world, "local": local, "max": t, "seeds": seeds, "all": g}))
+with open(os.path.join(%(out)r, "rank%%d.json" %% rank), "w") as f:
+    json.dump({"rank": rank, "world": world, "local": local, "max": t, "seeds": seeds, "all": g}, f)
 replicas.finalize(world)
 """
 
@@ -45,10 +46,10 @@ def launch(code_or_args, nproc=2, timeout=180):
 
 def test_two_gloo_ranks_max_barrier_and_disjoint_seeds(tmp_path):
     script = tmp_path / "worker.py"
-    script.write_text(WORKER % {"root": ROOT})
+    script.write_text(WORKER % {"root": ROOT, "out": str(tmp_path)})
     r = launch([str(script)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    lines = [json.load(open(tmp_path / ("rank%d.json" % k))) for k in range(2)]
     assert sorted(d["rank"] for d in lines) == [0, 1]
     for d in lines:
         assert d["world"] == 2 and d["max"] == 2.5
