@@ -4,6 +4,7 @@
 // Kurganov-Noelle-Petrova update (Sec. 3.2.2-3.2.3 of arXiv 1911.03225).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "fdm_df.cuh"
@@ -198,8 +199,6 @@ __device__ __forceinline__ float thalf(float x) { return 0.5f * x; }
 __device__ __forceinline__ double thalf(double x) { return 0.5 * x; }
 // x > 0 (false for zero and NaN)
 template <typename T> __device__ __forceinline__ bool tpos(T x) { return x > T(0); }
-// sqrt(x) for x >= 0
-template <typename T> __device__ __forceinline__ T tsqrt(T x) { return tpos(x) ? x * trsqrt(x) : T(0); }
 
 // ---------------------------------------------------------------------------------
 // Decisions on doubles made on their bit patterns.  GB300's FP64 pipe retires 2 lanes per
@@ -222,6 +221,15 @@ template <typename T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
     if (a < T(0) && b < T(0) && c < T(0)) return tmax(a, tmax(b, c));
     return T(0);
 }
+// x > 0 for the tests that guard a reciprocal or reciprocal square root of x.  FP32 and
+// double words (whose exponent range is FP32's) count x <= 1e-36 as zero, so that 1/x and
+// (1/sqrt(x))^2 stay finite; every term this drops is a product with a gradient or a speed
+// span of that size, far below the types' rounding.  FP64 tests x > 0 exactly.
+template <typename T> __device__ __forceinline__ bool tguard(T x) { return x > T(1e-36f); }
+__device__ __forceinline__ bool tguard(double x) { return tpos(x); }
+// sqrt(x) for x >= 0
+template <typename T> __device__ __forceinline__ T tsqrt(T x) { return tguard(x) ? x * trsqrt(x) : T(0); }
+
 // the same function on bit patterns: when a, b, c are nonzero, not NaN and of one sign, the
 // one of least magnitude; else 0
 __device__ __forceinline__ double minmod3(double a, double b, double c) {
@@ -299,19 +307,27 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
             T p = px[s], q = qy[t];
             T r2 = p * p + q * q;
             T Hp = T(0), Hq = T(0);
-            if (tpos(r2)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
+            if (tguard(r2)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
             speed_range(Hp, ap, am);
             speed_range(Hq, bp, bm);
         }
     // Step 4 weights (G1, G5): w(s,t) = nx[s] ny[t] / (dxw dyw), one reciprocal
-    T nx[2], ny[2], dxw, dyw;
-    dxw = ap - am;
-    if (tpos(dxw)) { nx[0] = -am; nx[1] = ap; }
+    // FP64: w(s,t) = nx[s] ny[t] / (dxw dyw) with one reciprocal.  FP32 and double words
+    // normalise each direction on its own (wx = nx / dxw in [0, 1]), because the product of
+    // two small spans leaves their exponent range.
+    T nx[2], ny[2], dxw = ap - am, dyw = bp - bm;
+    if (tguard(dxw)) { nx[0] = -am; nx[1] = ap; }
     else { nx[0] = T(0.5); nx[1] = T(0.5); dxw = T(1); }
-    dyw = bp - bm;
-    if (tpos(dyw)) { ny[0] = -bm; ny[1] = bp; }
+    if (tguard(dyw)) { ny[0] = -bm; ny[1] = bp; }
     else { ny[0] = T(0.5); ny[1] = T(0.5); dyw = T(1); }
-    const T inv_w = trcp(dxw * dyw);
+    T inv_w = T(1);
+    if constexpr (std::is_same<T, double>::value) {
+        inv_w = trcp(dxw * dyw);
+    } else {
+        const T ix = trcp(dxw), iy = trcp(dyw);
+        nx[0] = nx[0] * ix; nx[1] = nx[1] * ix;
+        ny[0] = ny[0] * iy; ny[1] = ny[1] * iy;
+    }
     const T vdt = v0 * dt_h;                 // v0 dt / h
     const T hvdt = thalf(vdt);               // v0 dt / (2 h)
     // Step 3: values at the four intermediate points (G2, G3).  Along each direction the
@@ -349,7 +365,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
             if (time_level == 0) {
                 // (p, q) -= dt/2 Hess grad_(p,q) H, grad H = v0 (p, q) / |(p, q)|
                 const T r2 = p * p + q * q;
-                if (tpos(r2)) {
+                if (tguard(r2)) {
                     const T w = hvdt * trsqrt(r2);
                     const T np = p - w * (Sx * p + cross * q);
                     const T nq = q - w * (cross * p + ys[t].S * q);
@@ -357,7 +373,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
                 }
             }
             const T s2 = p * p + q * q;
-            const T g = tpos(s2) ? s2 * trsqrt(s2) : T(0);   // h |grad|
+            const T g = tguard(s2) ? s2 * trsqrt(s2) : T(0);   // h |grad|
             const T psi = val - vdt * g;
             accs += ny[t] * psi;
         }
