@@ -48,13 +48,15 @@ def workload_input(n, seed):
     return inputs.random_up(n, seed=seed, ell=16.0, rms_alpha=0.1)
 
 
-def bytes_per_cell(elt):
+def bytes_per_cell(elt, pair=False):
     """Algorithmic HBM bytes per cell and launch of each kernel (one read + one write of
-    every array the kernel must touch; halo re-reads and tables excluded)."""
-    return {"row_forward": 2 * elt,   # read U13, write half spectrum (n1/2 complex per row)
-            "col_pass": 2 * elt,      # read + write the half spectrum in place
-            "row_inverse": 2 * elt,   # read half spectrum, write tau13
-            "knp_step": 3 * elt}      # read U13 and tau13, write U13^{n+1}
+    every array the kernel must touch; halo re-reads and tables excluded).  `pair`: the
+    state is a pair of FP32 words (mixed precision), read and written whole by the stencil."""
+    w = 2 if pair else 1
+    return {"row_forward": 2 * elt,           # read U13 (high word), write half spectrum
+            "col_pass": 2 * elt,              # read + write the half spectrum in place
+            "row_inverse": 2 * elt,           # read half spectrum, write tau13
+            "knp_step": (2 * w + 1) * elt}    # read U13 and tau13, write U13^{n+1}
 
 
 # FP arithmetic per node of the KNP update (counted from knp_node in fdm_device.cuh:
@@ -244,7 +246,7 @@ def run_ours(args, world, rank, local):
         elt = 4 if prec == "mixed" else 8
         phase_mean = {ph: sum(v) / len(v) for ph, v in per_phase.items()}
         dom = max(phase_mean, key=phase_mean.get)
-        bpc = bytes_per_cell(elt)
+        bpc = bytes_per_cell(elt, pair=(prec == "mixed"))
         results[prec] = {"total_ms": t_max, "phase_ms": phase_mean, "dominant": dom,
                          "clocks": clk.summary(), "info": info, "bpc": bpc, "sim": sim,
                          "launch": sim.launch_config()}

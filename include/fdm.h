@@ -75,8 +75,10 @@ typedef struct {
     double eps_bar13_rate;
     int32_t time_level;      /* FDM_T_MIDPOINT (default) or FDM_T_LITERAL (Sec. 3.2.2 Step 3) */
     int32_t precision;       /* FDM_FP64: native FP64 throughout.
-                                FDM_MIXED: FP32 fields/FFT/stencil with the mean plastic slip,
-                                loading, dt and conserved sums in FP64.
+                                FDM_MIXED: FP32 arithmetic in the FFT and stencil; U13 held
+                                as a pair of FP32 words (the stencil adds each step's
+                                increment exactly), tau13 and spectra in FP32; the mean
+                                plastic slip, loading, dt and conserved sums in FP64.
                                 FDM_DF64: fields/FFT/stencil in double-word arithmetic (two
                                 FP32 words, ~48-bit significand, on the FP32 pipes), scalars
                                 in FP64; FP64 accuracy class at FP32-pipe speed             */

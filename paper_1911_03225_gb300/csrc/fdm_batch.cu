@@ -113,8 +113,7 @@ fdm_status fdm_batch_set_plastic_distortion(fdm_batch* b, int32_t i, const doubl
     if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
     FDM_CK(cudaStreamSynchronize(b->stream));
     const double ref = G.prec != FDM_FP64 ? mean : 0.0;
-    const size_t e = elt_size(&G.d.p);
-    fdm_status st = upload_field((char*)G.d.phi[0] + (size_t)j * n * e, up13, n, G.prec, ref, b->stream);
+    fdm_status st = upload_state(G.d, G.prec, 0, j, up13, ref, b->stream);
     if (st) return st;
     fdm_dev_scalars s;
     std::memset(&s, 0, sizeof(s));
@@ -194,9 +193,7 @@ fdm_status fdm_batch_read_fields(fdm_batch* b, int32_t i, uint32_t mask, double*
     FDM_CK(cudaStreamSynchronize(b->stream));
     fdm_status st;
     if (mask & FDM_FIELD_UP13)
-        if ((st = download_field(up13, (char*)G.d.phi[s.cur] + (size_t)j * n * e, n, G.prec, G.phi_ref[j],
-                                 b->stream)))
-            return st;
+        if ((st = download_state(up13, G.d, G.prec, s.cur, j, G.phi_ref[j], b->stream))) return st;
     if (mask & FDM_FIELD_TAU13)
         if ((st = download_field(tau13, (char*)G.d.tau + (size_t)j * n * e, n, G.prec, 0.0, b->stream)))
             return st;

@@ -3,6 +3,7 @@
 // status reporting.  Shared group/graph helpers are defined here too.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -65,6 +66,12 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     const size_t cn = (size_t)count * n;
     if ((st = A.alloc(&d.phi[0], cn * sizeof(T)))) return st;
     if ((st = A.alloc(&d.phi[1], cn * sizeof(T)))) return st;
+    if (std::is_same<T, float>::value) {   // FP32 pairs: low words of the state
+        if ((st = A.alloc(&d.phi_lo[0], cn * sizeof(T)))) return st;
+        if ((st = A.alloc(&d.phi_lo[1], cn * sizeof(T)))) return st;
+        FDM_CK(cudaMemsetAsync(d.phi_lo[0], 0, cn * sizeof(T), s));
+        FDM_CK(cudaMemsetAsync(d.phi_lo[1], 0, cn * sizeof(T), s));
+    }
     if ((st = A.alloc(&d.tau, cn * sizeof(T)))) return st;
     if ((st = A.alloc(&d.spec, cn * sizeof(T)))) return st;   // n1/2 * n2 complex per instance
     if (with_spec2 && (st = A.alloc(&d.spec2, n * sizeof(T)))) return st;
@@ -109,6 +116,8 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
         FDM_CK(autotune_group<T>(d, s));
         FDM_CK(cudaMemsetAsync(d.sc, 0, (size_t)count * sizeof(fdm_dev_scalars), s));
         FDM_CK(cudaMemsetAsync(d.phi[0], 0, cn * sizeof(T), s));
+        for (void* lo : d.phi_lo)
+            if (lo) FDM_CK(cudaMemsetAsync(lo, 0, cn * sizeof(T), s));
         FDM_CK(cudaStreamSynchronize(s));
     }
     return FDM_OK;
@@ -167,6 +176,34 @@ fdm_status download_field(double* dst, const void* src, size_t n, int prec, doub
     return FDM_OK;
 }
 
+fdm_status upload_state(const Dev& d, int prec, int b, int inst, const double* src, double offset, cudaStream_t s) {
+    const size_t n = (size_t)d.p.n1 * d.p.n2;
+    if (prec != FDM_MIXED)
+        return upload_field((char*)d.phi[b] + (size_t)inst * n * elt_size(&d.p), src, n, prec, offset, s);
+    std::vector<float> hi(n), lo(n);
+    for (size_t i = 0; i < n; ++i) {
+        const double v = src[i] - offset;
+        hi[i] = (float)v;
+        lo[i] = (float)(v - (double)hi[i]);
+    }
+    FDM_CK(cudaMemcpyAsync((float*)d.phi[b] + inst * n, hi.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    FDM_CK(cudaMemcpyAsync((float*)d.phi_lo[b] + inst * n, lo.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    return FDM_OK;
+}
+
+fdm_status download_state(double* dst, const Dev& d, int prec, int b, int inst, double offset, cudaStream_t s) {
+    const size_t n = (size_t)d.p.n1 * d.p.n2;
+    if (prec != FDM_MIXED)
+        return download_field(dst, (const char*)d.phi[b] + (size_t)inst * n * elt_size(&d.p), n, prec, offset, s);
+    std::vector<float> hi(n), lo(n);
+    FDM_CK(cudaMemcpyAsync(hi.data(), (const float*)d.phi[b] + inst * n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    FDM_CK(cudaMemcpyAsync(lo.data(), (const float*)d.phi_lo[b] + inst * n, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < n; ++i) dst[i] = ((double)hi[i] + (double)lo[i]) + offset;
+    return FDM_OK;
+}
+
 static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nsteps, const std::vector<Dev*>& groups,
                                 const std::vector<int>& prec) {
     cudaGraph_t graph = nullptr;
@@ -212,7 +249,8 @@ fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, 
     const size_t n = (size_t)d.p.n1 * d.p.n2;
     const size_t e = elt_size(&d.p);
     const void* phi = (const char*)d.phi[s.cur] + (size_t)inst * n * e;
-    FDM_DISPATCH(prec, launch_alpha_sums<T>(d, (const T*)phi, d.red, d.red_blocks, stream));
+    const void* lo = d.phi_lo[s.cur] ? (const char*)d.phi_lo[s.cur] + (size_t)inst * n * e : nullptr;
+    FDM_DISPATCH(prec, launch_alpha_sums<T>(d, (const T*)phi, (const T*)lo, d.red, d.red_blocks, stream));
     FDM_CK(cudaGetLastError());
     std::vector<double> part((size_t)6 * d.red_blocks);
     FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -298,7 +336,7 @@ fdm_status read_fields_impl(fdm_handle* h, uint32_t mask, double* up13, double* 
     const T* phi = (const T*)d.phi[sc.cur];
     const int mx = h->prec;
     if (mask & FDM_FIELD_UP13)
-        if ((st = download_field(up13, phi, h->n, mx, d.phi_ref_host, h->stream))) return st;
+        if ((st = download_state(up13, d, mx, sc.cur, 0, d.phi_ref_host, h->stream))) return st;
     if (mask & FDM_FIELD_TAU13)
         if ((st = download_field(tau, d.tau, h->n, mx, 0.0, h->stream))) return st;
     if (mask & (FDM_FIELD_ALPHA11 | FDM_FIELD_ALPHA12 | FDM_FIELD_V1 | FDM_FIELD_V2)) {
@@ -352,7 +390,8 @@ size_t fdm_device_bytes(const fdm_params* p) {
     if (!params_valid(p)) return 0;
     size_t n = (size_t)p->n1 * p->n2, e = elt_size(p);
     size_t nk = (size_t)(p->n1 / 2 + 1) * (p->n2 / 2 + 1);
-    return 5 * n * e + nk * e + (size_t)(p->n1 + p->n2) * 4 * e + (size_t)p->n2 * sizeof(double) + 64 * 1024;
+    const size_t lo = p->precision == FDM_MIXED ? 2 * n * sizeof(float) : 0;   // low words of the state
+    return 5 * n * e + lo + nk * e + (size_t)(p->n1 + p->n2) * 4 * e + (size_t)p->n2 * sizeof(double) + 64 * 1024;
 }
 
 fdm_status fdm_create(const fdm_params* p, void* stream, fdm_handle** out) {
@@ -386,7 +425,7 @@ fdm_status fdm_set_plastic_distortion(fdm_handle* h, const double* up13) {
     FDM_CK(cudaStreamSynchronize(h->stream));
     // FP32 and double-word storage hold U13 minus its mean (the scheme is offset equivariant)
     h->d.phi_ref_host = h->prec != FDM_FP64 ? mean : 0.0;
-    fdm_status st = upload_field(h->d.phi[0], up13, h->n, h->prec, h->d.phi_ref_host, h->stream);
+    fdm_status st = upload_state(h->d, h->prec, 0, 0, up13, h->d.phi_ref_host, h->stream);
     if (st) return st;
     return reset_scalars(h, mean);
 }
@@ -420,6 +459,7 @@ fdm_status fdm_set_density(fdm_handle* h, const double* a11, const double* a12, 
     double res = den > 0.0 ? std::sqrt(num / den) : 0.0;
     if (div_residual) *div_residual = res;
     d.phi_ref_host = phi_ref;
+    if (d.phi_lo[0]) FDM_CK(cudaMemsetAsync(d.phi_lo[0], 0, n * sizeof(float), h->stream));
     if ((st = reset_scalars(h, mean_up13))) return st;
     return res > 1e-6 ? FDM_WARN_NOT_DIV_FREE : FDM_OK;
 }

@@ -159,6 +159,10 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
 // FDM_DF64), minus offset / downloads it, adding offset back.
 fdm_status upload_field(void* dst, const double* src, size_t n, int prec, double offset, cudaStream_t s);
 fdm_status download_field(double* dst, const void* src, size_t n, int prec, double offset, cudaStream_t s);
+// U13 of instance `inst` in state buffer b, from / to host doubles (minus / plus `offset`);
+// FDM_MIXED stores FP32 pairs: hi = fl(v), lo = fl(v - hi)
+fdm_status upload_state(const Dev& d, int prec, int b, int inst, const double* src, double offset, cudaStream_t s);
+fdm_status download_state(double* dst, const Dev& d, int prec, int b, int inst, double offset, cudaStream_t s);
 
 // A step of every group as CUDA graphs (1 and kGraphSteps steps), replayed on a stream.
 struct StepGraphs {

@@ -45,6 +45,7 @@ struct Dev {
     int count;             // instances in the group
     int gated;             // step launches honour each instance's steps_left (batches)
     void* phi[2];          // double-buffered U13 (type T); the current one is sc[i].cur
+    void* phi_lo[2];       // FDM_MIXED: low FP32 words of U13 (U13 = phi + phi_lo); else null
     void* tau;             // T
     void* spec;            // cpx<T> [n1/2][n2] per instance
     void* spec2;           // cpx<T> [n1/2][n2] (single instance only; readouts)
@@ -82,7 +83,8 @@ template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,
                          double* partials, int nblk, cudaStream_t s);
 template <typename T> void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t s);
-template <typename T> void launch_alpha_sums(const Dev& d, const T* phi, double* partials, int nblk, cudaStream_t s);
+template <typename T>
+void launch_alpha_sums(const Dev& d, const T* phi, const T* phi_lo, double* partials, int nblk, cudaStream_t s);
 template <typename T>
 void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
                      cudaStream_t s);

@@ -474,6 +474,8 @@ constexpr int TX = 32;  // stencil block width (threads along x1)
 template <typename T>
 struct KnpArgs {
     VelLaw<T> vel;
+    const T* lo0;            // FP32: low words of the two state buffers (U13 = hi + lo)
+    const T* lo1;
     T theta;
     int theta_code;          // 1 or 2 when theta is exactly that (exact scaling), else 0
     int time_level;
@@ -507,7 +509,12 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
                     KnpArgs<T> a) {
     constexpr int TY = KnpShapes<T>::ty[V];
     constexpr int NPT = KnpShapes<T>::npt[V];
+    // FP32 carries the state as a pair of words, U13 = hi + lo: the node update works on
+    // differences to the node's own value and adds its increment with an exact TwoSum, so
+    // the state keeps ~48 bits while all arithmetic stays on the FP32 pipes
+    constexpr bool kPair = std::is_same<T, float>::value;
     __shared__ T tile[TY * NPT + 4][TX + 4];
+    __shared__ T tile_lo[kPair ? TY * NPT + 4 : 1][kPair ? TX + 4 : 1];
     __shared__ T s_tau[TY * NPT][TX];
     __shared__ T s_dt;
     __shared__ int s_run, s_cur;
@@ -553,6 +560,8 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     const T* phi = (s_cur ? phi1 : phi0) + inst * nn;
     T* out = const_cast<T*>(s_cur ? phi0 : phi1) + inst * nn;
     const T* tau = tau0 + inst * nn;
+    const T* lo_in = kPair ? (s_cur ? a.lo1 : a.lo0) + inst * nn : nullptr;
+    T* lo_out = kPair ? const_cast<T*>(s_cur ? a.lo0 : a.lo1) + inst * nn : nullptr;
     const int x = bx + threadIdx.x;
     T tv[NPT];   // tau13 at this thread's nodes: loads issued ahead of the tile's
 #pragma unroll
@@ -563,6 +572,7 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
         for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
             const int gx = (bx + lx - 2) & (n1 - 1);
             tile[ly][lx] = phi[(size_t)gy * n1 + gx];
+            if constexpr (kPair) tile_lo[ly][lx] = lo_in[(size_t)gy * n1 + gx];
         }
     }
 #pragma unroll
@@ -576,10 +586,25 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     for (int k = 0; k < npt; ++k) {
         const int y = by + threadIdx.y + k * TY;
         const int ly = threadIdx.y + k * TY + 2;
-        const T up = tile[ly][lx];
-        const T v0 = celerity(a.vel, s_tau[threadIdx.y + k * TY][threadIdx.x], up, phi_ref);
-        auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
-        out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
+        const T tau_k = s_tau[threadIdx.y + k * TY][threadIdx.x];
+        if constexpr (kPair) {
+            const T h0 = tile[ly][lx], l0 = tile_lo[ly][lx];
+            const T v0 = celerity(a.vel, tau_k, h0 + l0, phi_ref);
+            // differences to the node value, exact in the high words for nearby values;
+            // the offset-equivariant update then returns the increment of U13
+            auto g = [&](int i, int j) -> T { return (tile[ly + j][lx + i] - h0) + (tile_lo[ly + j][lx + i] - l0); };
+            const T inc = knp_node<T>(g, v0, dt, a.theta, a.theta_code, a.time_level);
+            float s1, e1, hi, lo;
+            two_sum(h0, inc, s1, e1);
+            two_sum(s1, DF_ADD(l0, e1), hi, lo);
+            out[(size_t)y * n1 + x] = hi;
+            lo_out[(size_t)y * n1 + x] = lo;
+        } else {
+            const T up = tile[ly][lx];
+            const T v0 = celerity(a.vel, tau_k, up, phi_ref);
+            auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
+            out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
+        }
     }
 }
 
@@ -683,15 +708,17 @@ __global__ void curl_inverse_kernel(const cpx<T>* __restrict__ sa, const cpx<T>*
 
 // info: FP64 sums over the staggered Nye components of the current state
 template <typename T>
-__global__ void alpha_sums_kernel(const T* __restrict__ phi, int n1, int n2, double dx, double* __restrict__ partials) {
+__global__ void alpha_sums_kernel(const T* __restrict__ phi, const T* __restrict__ lo, int n1, int n2, double dx,
+                                  double* __restrict__ partials) {
     __shared__ double red[32];
     double s[6] = {0, 0, 0, 0, 0, 0};
     const size_t total = (size_t)n1 * n2;
+    auto val = [&](size_t k) -> double { return lo ? (double)phi[k] + (double)lo[k] : (double)phi[k]; };
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         int y = (int)(i / n1), x = (int)(i - (size_t)y * n1);
-        double u = (double)phi[i];
-        double a12 = ((double)phi[(size_t)y * n1 + ((x + 1) & (n1 - 1))] - u) / dx;
-        double a11 = -((double)phi[(size_t)((y + 1) & (n2 - 1)) * n1 + x] - u) / dx;
+        double u = val(i);
+        double a12 = (val((size_t)y * n1 + ((x + 1) & (n1 - 1))) - u) / dx;
+        double a11 = -(val((size_t)((y + 1) & (n2 - 1)) * n1 + x) - u) / dx;
         s[0] += a12 > 0 ? a12 : 0.0;
         s[1] += a12 < 0 ? a12 : 0.0;
         s[2] += a11 > 0 ? a11 : 0.0;
@@ -880,6 +907,8 @@ template <typename T>
 void launch_knp(const Dev& d, cudaStream_t s) {
     KnpArgs<T> a;
     a.vel = make_vel<T>(d.p);
+    a.lo0 = (const T*)d.phi_lo[0];
+    a.lo1 = (const T*)d.phi_lo[1];
     a.theta = T(d.p.theta);
     a.theta_code = d.p.theta == 1.0 ? 1 : (d.p.theta == 2.0 ? 2 : 0);
     a.time_level = d.p.time_level;
@@ -966,8 +995,8 @@ void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t
 }
 
 template <typename T>
-void launch_alpha_sums(const Dev& d, const T* phi, double* partials, int nblk, cudaStream_t s) {
-    alpha_sums_kernel<T><<<nblk, 256, 0, s>>>(phi, d.p.n1, d.p.n2, d.p.dx, partials);
+void launch_alpha_sums(const Dev& d, const T* phi, const T* phi_lo, double* partials, int nblk, cudaStream_t s) {
+    alpha_sums_kernel<T><<<nblk, 256, 0, s>>>(phi, phi_lo, d.p.n1, d.p.n2, d.p.dx, partials);
 }
 
 template <typename T>
@@ -994,7 +1023,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \
     template void launch_convert<T>(const double*, T*, size_t, double, cudaStream_t);                       \
-    template void launch_alpha_sums<T>(const Dev&, const T*, double*, int, cudaStream_t);                   \
+    template void launch_alpha_sums<T>(const Dev&, const T*, const T*, double*, int, cudaStream_t);         \
     template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
                                      cudaStream_t);
 FDM_INST(double)
