@@ -64,13 +64,16 @@ def bytes_per_cell(elt, pair=False):
 KNP_FLOPS_PER_CELL = 380
 
 
+KERNEL_SOURCES = ["fdm_kernels.cu", "fdm_device.cuh", "fdm_df.cuh", "fdm_internal.h"]
+
+
 def kernel_source_hash():
-    """sha256 (first 16 hex) of the CUDA sources; profile figures are valid only for it."""
-    import glob
+    """sha256 (first 16 hex) of the step kernels' CUDA sources; profile figures are valid
+    only for it."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1911_03225_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1911_03225_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -291,6 +291,8 @@ struct fdm_handle {
     int prec;                // FDM_FP64, FDM_MIXED or FDM_DF64
     size_t n;                // n1 * n2
     void* rd[4];             // readout buffers (type T, n each), allocated on first use
+    Dev rd64;                // mixed precision: FP64 spectra and tables for the Nye readout
+    void* rd64_buf[3];       //   U13 and the two Nye components in FP64 (n each)
 };
 
 namespace {
@@ -326,6 +328,36 @@ fdm_status ensure_readout(fdm_handle* h) {
     return FDM_OK;
 }
 
+// The mixed path reads its Nye field out in FP64: the state's word pairs convert exactly,
+// so the readout adds no FP32 transform rounding to a field whose norm may be a small
+// fraction of U13's.  Spectra and tables are allocated on first use.
+fdm_status ensure_readout64(fdm_handle* h) {
+    Dev& r = h->rd64;
+    if (r.spec) return FDM_OK;
+    fdm_status st;
+    const fdm_params& p = h->d.p;
+    r = Dev{};
+    r.p = p;
+    r.p.precision = FDM_FP64;
+    r.count = 1;
+    FDM_CK(configure_kernels<double>());
+    r.geom = geometry<double>(p.n1, p.n2);
+    const size_t n = h->n;
+    if ((st = h->arena.alloc(&r.spec, n * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&r.spec2, n * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&r.tw1, (size_t)p.n1 * 2 * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&r.tw2, (size_t)p.n2 * 2 * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&r.pt1, (size_t)(pass_table_len(p.n1 / 2) + 1) * 2 * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&r.pt2, (size_t)(pass_table_len(p.n2) + 1) * 2 * sizeof(double)))) return st;
+    if ((st = upload_twiddles<double>(r.tw1, p.n1, h->stream))) return st;
+    if ((st = upload_twiddles<double>(r.tw2, p.n2, h->stream))) return st;
+    if ((st = upload_pass_twiddles<double>(r.pt1, p.n1 / 2, h->stream))) return st;
+    if ((st = upload_pass_twiddles<double>(r.pt2, p.n2, h->stream))) return st;
+    for (int i = 0; i < 3; ++i)
+        if ((st = h->arena.alloc(&h->rd64_buf[i], n * sizeof(double)))) return st;
+    return FDM_OK;
+}
+
 template <typename T>
 fdm_status read_fields_impl(fdm_handle* h, uint32_t mask, double* up13, double* a11, double* a12, double* tau,
                             double* v1, double* v2) {
@@ -339,13 +371,25 @@ fdm_status read_fields_impl(fdm_handle* h, uint32_t mask, double* up13, double* 
         if ((st = download_state(up13, d, mx, sc.cur, 0, d.phi_ref_host, h->stream))) return st;
     if (mask & FDM_FIELD_TAU13)
         if ((st = download_field(tau, d.tau, h->n, mx, 0.0, h->stream))) return st;
-    if (mask & (FDM_FIELD_ALPHA11 | FDM_FIELD_ALPHA12 | FDM_FIELD_V1 | FDM_FIELD_V2)) {
+    const bool nye64 = mx == FDM_MIXED && (mask & (FDM_FIELD_ALPHA11 | FDM_FIELD_ALPHA12));
+    if (nye64) {
+        if ((st = ensure_readout64(h))) return st;
+        double* u64 = (double*)h->rd64_buf[0];
+        launch_pair_to_double((const float*)d.phi[sc.cur], (const float*)d.phi_lo[sc.cur], u64, h->n, h->stream);
+        launch_alpha<double>(h->rd64, u64, (double*)h->rd64_buf[1], (double*)h->rd64_buf[2], h->stream);
+        FDM_CK(cudaGetLastError());
+        if (mask & FDM_FIELD_ALPHA11)
+            if ((st = download_field(a11, h->rd64_buf[1], h->n, FDM_FP64, 0.0, h->stream))) return st;
+        if (mask & FDM_FIELD_ALPHA12)
+            if ((st = download_field(a12, h->rd64_buf[2], h->n, FDM_FP64, 0.0, h->stream))) return st;
+    }
+    if ((mask & (FDM_FIELD_V1 | FDM_FIELD_V2)) || (!nye64 && (mask & (FDM_FIELD_ALPHA11 | FDM_FIELD_ALPHA12)))) {
         if ((st = ensure_readout<T>(h))) return st;
         launch_alpha<T>(d, phi, (T*)h->rd[0], (T*)h->rd[1], h->stream);
         FDM_CK(cudaGetLastError());
-        if (mask & FDM_FIELD_ALPHA11)
+        if ((mask & FDM_FIELD_ALPHA11) && !nye64)
             if ((st = download_field(a11, h->rd[0], h->n, mx, 0.0, h->stream))) return st;
-        if (mask & FDM_FIELD_ALPHA12)
+        if ((mask & FDM_FIELD_ALPHA12) && !nye64)
             if ((st = download_field(a12, h->rd[1], h->n, mx, 0.0, h->stream))) return st;
         if (mask & (FDM_FIELD_V1 | FDM_FIELD_V2)) {
             launch_velocity<T>(d, (const T*)h->rd[0], (const T*)h->rd[1], (const T*)d.tau, phi, (T*)h->rd[2],

@@ -88,6 +88,7 @@ void launch_alpha_sums(const Dev& d, const T* phi, const T* phi_lo, double* part
 template <typename T>
 void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
                      cudaStream_t s);
+void launch_pair_to_double(const float* hi, const float* lo, double* out, size_t n, cudaStream_t s);
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
                          cudaStream_t s);
 

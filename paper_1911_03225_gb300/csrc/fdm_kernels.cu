@@ -633,6 +633,16 @@ __global__ void kernel_table_kernel(double* __restrict__ Kh, int n1, int n2, int
     }
 }
 
+// FP32 word pairs -> FP64 (exact: hi + lo has at most 48 significant bits)
+__global__ void pair_to_double_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
+                                      double* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)hi[i] + (double)lo[i];
+}
+void launch_pair_to_double(const float* hi, const float* lo, double* out, size_t n, cudaStream_t s) {
+    pair_to_double_kernel<<<4 * 152, 256, 0, s>>>(hi, lo, out, n);
+}
+
 template <typename T>
 __global__ void convert_kernel(const double* __restrict__ a, T* __restrict__ b, size_t n, double offset) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
