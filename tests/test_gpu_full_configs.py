@@ -8,7 +8,7 @@ size in test_gpu_parity.py)."""
 import numpy as np
 import pytest
 
-from paper_1911_03225_gb300 import FDM, Params, inputs
+from paper_1911_03225_gb300 import FDM, Batch, Params, inputs
 from paper_1911_03225_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -64,7 +64,7 @@ def test_ring_loop_expansion_1024_2000_steps(precision):
 # decayed to 2% of its initial norm (and is nearly flat by step 5000), so its relative
 # error there measures a vanishing quantity and is checked only through U13 and the stress.
 TOL = {
-    B.MIXED: {"tau13": 1e-5, "up13": 1e-5, "alpha": {40: 1e-5, 100: 2e-5, 1000: 3e-4}},
+    B.MIXED: {"tau13": 1e-5, "up13": 1e-5, "alpha": {40: 1e-5, 100: 2e-5, 1000: 1e-4}},
     B.DF64: {"tau13": 1e-8, "up13": 1e-8, "alpha": {40: 1e-8, 100: 1e-8, 1000: 1e-5}},
 }
 
@@ -106,3 +106,35 @@ def test_coupled_2048_5000_steps_mixed_and_df64_against_fp64():
     finally:
         for s_ in sims.values():
             s_.close()
+
+
+def test_batched_256_uneven_instances_mixed_against_fp64():
+    """Configuration 4: 256 instances, side per seed in {64, 128, 256, 512}, random fields with
+    the instance's seed, mixed precision, 1000 steps in one batch (CUDA-graph steps, every
+    instance's budget on the device).  A sample of instances, one of each side, matches its
+    plain FP64 run within the stated mixed tolerance (stress and U13: 1e-5)."""
+    sizes = [64, 128, 256, 512]
+    steps = 1000
+    side = [sizes[int(np.random.default_rng(i).integers(4))] for i in range(256)]
+    coupled = lambda n, prec: Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP,  # noqa: E731
+                                     eps_bar13_rate=1e-4, cfl=0.4, theta=1.0, precision=prec)
+    ups = [inputs.random_up(n, seed=i, ell=16.0, rms_alpha=0.1) for i, n in enumerate(side)]
+    sample = [side.index(n) for n in sizes]
+    with Batch([coupled(n, B.MIXED) for n in side]) as b:
+        for i in range(256):
+            b.set_plastic_distortion(i, ups[i])
+            b.set_budget(i, steps)
+        b.enqueue_steps(steps)
+        assert (b.sync() == 0).all()
+        got = {i: b.read_fields(i, "up13", "tau13") for i in sample}
+        infos = {i: b.info(i) for i in sample}
+    rel = lambda a, c: float(np.linalg.norm(a - c) / np.linalg.norm(c))  # noqa: E731
+    for i in sample:
+        with FDM(coupled(side[i], B.FP64)) as sim:
+            sim.set_plastic_distortion(ups[i])
+            sim.enqueue_steps(steps)
+            sim.sync()
+            ref = sim.read_fields("up13", "tau13")
+        assert infos[i].step == steps
+        assert rel(got[i]["up13"], ref["up13"]) < 1e-5, (i, side[i])
+        assert rel(got[i]["tau13"], ref["tau13"]) < 1e-5, (i, side[i])
