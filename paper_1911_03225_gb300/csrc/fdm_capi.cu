@@ -204,12 +204,30 @@ fdm_status download_state(double* dst, const Dev& d, int prec, int b, int inst, 
     return FDM_OK;
 }
 
-static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nsteps, const std::vector<Dev*>& groups,
-                                const std::vector<int>& prec) {
+static fdm_status capture_steps(cudaGraphExec_t* out, const StepGraphs& sg, int nsteps,
+                                const std::vector<Dev*>& groups, const std::vector<int>& prec) {
     cudaGraph_t graph = nullptr;
+    cudaStream_t cap = sg.capture;
     FDM_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < nsteps; ++k)
-        for (size_t g = 0; g < groups.size(); ++g) FDM_DISPATCH(prec[g], launch_step<T>(*groups[g], cap));
+    if (groups.size() == 1) {
+        for (int k = 0; k < nsteps; ++k) FDM_DISPATCH(prec[0], launch_step<T>(*groups[0], cap));
+    } else {
+        // fork: every group's steps on its own stream; join them all at the end
+        cudaEvent_t fork = sg.join.back();
+        cudaError_t r = cudaEventRecord(fork, cap);
+        for (size_t g = 0; g < groups.size() && r == cudaSuccess; ++g) {
+            r = cudaStreamWaitEvent(sg.side[g], fork, 0);
+            for (int k = 0; k < nsteps && r == cudaSuccess; ++k) FDM_DISPATCH(prec[g], launch_step<T>(*groups[g], sg.side[g]));
+            if (r == cudaSuccess) r = cudaEventRecord(sg.join[g], sg.side[g]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(cap, sg.join[g], 0);
+        }
+        if (r != cudaSuccess) {
+            cudaStreamEndCapture(cap, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return FDM_ERR_DEVICE;
+        }
+    }
     cudaError_t e = cudaStreamEndCapture(cap, &graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -227,9 +245,21 @@ static fdm_status capture_steps(cudaGraphExec_t* out, cudaStream_t cap, int nste
 fdm_status build_step_graphs(StepGraphs& g, const std::vector<Dev*>& groups, const std::vector<int>& prec) {
     if (g.one) return FDM_OK;
     if (!g.capture) FDM_CK(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
-    fdm_status st = capture_steps(&g.one, g.capture, 1, groups, prec);
+    if (groups.size() > 1 && g.side.empty()) {
+        for (size_t i = 0; i < groups.size(); ++i) {
+            cudaStream_t x = nullptr;
+            FDM_CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+            g.side.push_back(x);
+        }
+        for (size_t i = 0; i <= groups.size(); ++i) {
+            cudaEvent_t x = nullptr;
+            FDM_CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+            g.join.push_back(x);
+        }
+    }
+    fdm_status st = capture_steps(&g.one, g, 1, groups, prec);
     if (st) return st;
-    return capture_steps(&g.many, g.capture, StepGraphs::kGraphSteps, groups, prec);
+    return capture_steps(&g.many, g, StepGraphs::kGraphSteps, groups, prec);
 }
 
 fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s) {

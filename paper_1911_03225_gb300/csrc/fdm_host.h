@@ -165,16 +165,25 @@ fdm_status upload_state(const Dev& d, int prec, int b, int inst, const double* s
 fdm_status download_state(double* dst, const Dev& d, int prec, int b, int inst, double offset, cudaStream_t s);
 
 // A step of every group as CUDA graphs (1 and kGraphSteps steps), replayed on a stream.
+// Whole steps recorded as CUDA graphs.  With several groups each group's kernels form their
+// own branch of the graph (captured on a side stream forked from and joined back to the
+// capture stream), so independent groups run concurrently and fill the GPU together.
 struct StepGraphs {
     cudaGraphExec_t one = nullptr, many = nullptr;
     cudaStream_t capture = nullptr;
+    std::vector<cudaStream_t> side;   // one per group (several groups only)
+    std::vector<cudaEvent_t> join;    // one per group, plus the fork event at the end
     static constexpr int kGraphSteps = 8;
     void destroy() {
         if (one) cudaGraphExecDestroy(one);
         if (many) cudaGraphExecDestroy(many);
         if (capture) cudaStreamDestroy(capture);
+        for (cudaStream_t x : side) cudaStreamDestroy(x);
+        for (cudaEvent_t x : join) cudaEventDestroy(x);
         one = many = nullptr;
         capture = nullptr;
+        side.clear();
+        join.clear();
     }
 };
 
