@@ -92,11 +92,17 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     s = t;
 }
 
+// Thread and residency bounds of the FFT kernels.  The FP32 kernels are latency bound: a
+// block of at most 512 threads with three resident per SM caps them at 40 registers, which
+// keeps 48 warps per SM instead of 32 (no spills).
+template <typename T> struct FftBounds { static constexpr int threads = 1024, minb = 1; };
+template <> struct FftBounds<float> { static constexpr int threads = 512, minb = 3; };
+
 // ------------------------------------------------------------------ row forward (R2C)
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional FP64 sum of each row
 // (for <U13>), in an order fixed by the row alone, so that results do not depend on R.
 template <typename T>
-__global__ void __launch_bounds__(1024) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1,
                                                           const cpx<T>* __restrict__ pt1,
@@ -204,7 +210,7 @@ __device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
                                                        int n1, int n2, int C,
                                                        const cpx<T>* __restrict__ pt2, const T* __restrict__ Kh,
                                                        ColArgs<T> a) {
@@ -364,7 +370,7 @@ struct RowArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(1024) row_inverse_kernel(const cpx<T>* spec, T* dst,
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_inverse_kernel(const cpx<T>* spec, T* dst,
                                                           int n1, int n2, int R,
                                                           const cpx<T>* __restrict__ tw1,
                                                           const cpx<T>* __restrict__ pt1, RowArgs<T> a) {
@@ -758,14 +764,14 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
 // ------------------------------------------------------------------ launchers
 constexpr size_t kMaxDynSmem = 200 * 1024;  // dynamic shared memory the FFT kernels may request
 
-// R rows per row-kernel block is valid when R <= n2, R <= 16, R n1/2 <= 8192 (one radix-8
-// butterfly per thread, at most 1024 threads) and the rows fit the shared-memory limit
+// R rows per row-kernel block is valid when R <= n2, R <= 16, R n1/2 <= 8 x the thread
+// bound (one radix-8 butterfly per thread) and the rows fit the shared-memory limit
 template <typename T> static bool row_ok(int n1, int n2, int R) {
-    return R <= n2 && R <= 16 && R * (n1 / 2) <= 8192 &&
+    return R <= n2 && R <= 16 && R * (n1 / 2) <= 8 * FftBounds<T>::threads &&
            (size_t)R * padded_len(n1 / 2) * sizeof(cpx<T>) <= kMaxDynSmem;
 }
 template <typename T> static bool col_ok(int n1, int n2, int C) {
-    return C <= n1 / 2 && C <= 16 && C * n2 <= 8192 && (size_t)C * padded_len(n2) * sizeof(cpx<T>) <= kMaxDynSmem;
+    return C <= n1 / 2 && C <= 16 && C * n2 <= 8 * FftBounds<T>::threads && (size_t)C * padded_len(n2) * sizeof(cpx<T>) <= kMaxDynSmem;
 }
 
 template <typename T>
@@ -783,8 +789,8 @@ int col_candidates(int n1, int n2, int* out, int max) {
     return k;
 }
 
-// heuristic shapes: as many rows as fit 40 KB of shared memory (at most 16 and 8192
-// points); columns until a block has 1024 points
+// heuristic shapes: as many valid rows as fit 40 KB of shared memory; columns until a
+// block has 1024 points
 template <typename T> static int pick_rows(int n1, int n2) {
     const size_t per_row = (size_t)padded_len(n1 / 2) * sizeof(cpx<T>);
     int R = 1;
