@@ -328,11 +328,42 @@ def run_ours(args, world, rank, local):
             "gpu_launches": len(PHASES) * K,
             "precisions": extra,
         }
+        import torch
+        line["fft_comparison"] = {
+            "note": "static solve (rows, K multiply with the xi = 0 loading, inverse) of this library vs the same "
+                    "transform pair through cuFFT (torch.fft.rfft2 / irfft2 with one multiply), both L2-cold; "
+                    "cuFFT is a timing comparison only",
+            "ours_ms": {p_: round(sum(v["phase_ms"][k_] for k_ in PHASES[:3]), 5) for p_, v in extra.items()},
+            "cufft_ms": {"fp64": round(cufft_static_solve_ms(n, torch.float64), 5),
+                         "mixed": round(cufft_static_solve_ms(n, torch.float32), 5)}}
         if args.cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     for rr in results.values():
         rr["sim"].close()
+
+
+def cufft_static_solve_ms(n, dtype, reps=20):
+    """Timing comparison only (never on the result path): the same static solve -- real 2-D
+    FFT, multiply by a real symbol, inverse -- through torch.fft (cuFFT) on an n x n field of
+    `dtype`, with the L2 flushed before each repetition like the timed steps."""
+    import torch
+    dev = torch.device("cuda")
+    u = torch.randn(n, n, dtype=dtype, device=dev)
+    k = torch.rand(n, n // 2 + 1, dtype=dtype, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        torch.fft.irfft2(torch.fft.rfft2(u) * k, s=(n, n))
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        torch.fft.irfft2(torch.fft.rfft2(u) * k, s=(n, n))
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
 
 
 def cpu_baseline(seconds):

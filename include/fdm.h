@@ -84,8 +84,10 @@ typedef struct {
                                 in FP64; FP64 accuracy class at FP32-pipe speed             */
     int32_t autotune;        /* 1: at creation, time the candidate launch shapes of the step
                                 kernels on this GPU and keep the fastest (cached per device,
-                                precision, grid and instance count for the process); 0: fixed
-                                heuristic shapes.  Every shape computes bit-identical values. */
+                                precision, grid and instance count for the process, and across
+                                processes in the JSON-lines file named by the environment
+                                variable FDM_TUNE_CACHE, if set); 0: fixed heuristic shapes.
+                                Every shape computes bit-identical values.                    */
 } fdm_params;
 
 /* Launch shapes of the step kernels of a handle (or of a batch instance's group). */
@@ -188,6 +190,13 @@ fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
+
+/* Heterogeneous drag (Sec. 5.3, Orowan mechanism: precipitates with infinite drag):
+ * factor[n2][n1] (host, float64, finite, >= 0) multiplies the celerity of every node,
+ * v0(x) = m(x) v0_law(x), i.e. eta(x) = eta~ / m(x); m = 0 inside impenetrable particles,
+ * whose nodes then never change.  NULL restores m = 1.  The time step follows the
+ * resulting max |v0|.  Copied to the device; waits for the stream. */
+fdm_status fdm_set_mobility_field(fdm_handle *h, const double *factor);
 
 /* Launch shapes the handle's step kernels use (see fdm_params.autotune). */
 fdm_status fdm_get_launch_config(const fdm_handle *h, fdm_launch_config *cfg);

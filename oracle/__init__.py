@@ -34,7 +34,7 @@ def lib():
         _lib.oracle_sum.argtypes = [C.c_size_t, d]
         _lib.oracle_sum.restype = C.c_double
         _lib.oracle_alpha_sums.argtypes = [C.c_int, C.c_int, C.c_double, d, d]
-        _lib.oracle_run.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d]
+        _lib.oracle_run.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d]
         _lib.oracle_run.restype = C.c_int
     return _lib
 
@@ -196,8 +196,10 @@ class State:
     v0: np.ndarray = field(default=None, repr=False)
 
 
-def run(params: Params, up13, nsteps, K=None, state: State = None):
-    """Advance ``nsteps`` FDM steps (Sec. 3.1.1) from ``up13`` (or ``state``)."""
+def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None):
+    """Advance ``nsteps`` FDM steps (Sec. 3.1.1) from ``up13`` (or ``state``).
+    ``mobility_factor``: optional per-node m(x) >= 0 multiplying the celerity
+    (heterogeneous drag, m = 0 in impenetrable precipitates; Sec. 5.3)."""
     p = params._c()
     if K is None:
         K = kernel_table(p.n1, p.n2, p.nz, p.nh, params.mu, params.nu)
@@ -209,7 +211,11 @@ def run(params: Params, up13, nsteps, K=None, state: State = None):
     u = _f64(state.up13).copy()
     tau = np.zeros_like(u)
     v0 = np.zeros_like(u)
-    rc = lib().oracle_run(C.byref(p), _p(_f64(K)), _p(u), C.byref(sc), int(nsteps), _p(tau), _p(v0))
+    mf = None if mobility_factor is None else _f64(mobility_factor)
+    if mf is not None and mf.shape != u.shape:
+        raise ValueError("mobility factor must have the field's shape")
+    rc = lib().oracle_run(C.byref(p), _p(_f64(K)), _p(u), C.byref(sc), int(nsteps), _p(tau), _p(v0),
+                          None if mf is None else _p(mf))
     return State(up13=u, step=sc.step, t=sc.t, dt=sc.dt, max_abs_v0=sc.max_abs_v0,
                  mean_up13=sc.mean_up13, eps_bar13=sc.eps_bar13, sigma_bar13=sc.sigma_bar13,
                  tau13=tau, v0=v0), rc

@@ -493,11 +493,13 @@ static void loading(const oracle_params *p, int64_t step, double mean_up13, doub
 
 /*
  * Advance `nsteps` steps in place.  K is the table from oracle_kernel_table; tau13 and v0
- * (may be NULL) receive the fields of the last step's static solve.  Returns 0, or 1 if a
- * non-finite value appeared.
+ * (may be NULL) receive the fields of the last step's static solve.  mfac (may be NULL):
+ * per-node mobility factor m(x) >= 0 multiplying the celerity -- a heterogeneous drag
+ * eta(x) = eta~ / m(x), with m = 0 inside impenetrable precipitates (Sec. 5.3, Orowan
+ * mechanism).  Returns 0, or 1 if a non-finite value appeared.
  */
 int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_scalars *st,
-               int nsteps, double *tau_out, double *v0_out)
+               int nsteps, double *tau_out, double *v0_out, const double *mfac)
 {
     int n1 = p->n1, n2 = p->n2;
     size_t n = (size_t)n1 * n2;
@@ -519,6 +521,7 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
                 double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;
                 c = p->mobility * (fr - tau[i]);
             }
+            if (mfac) c *= mfac[i];
             v0[i] = c;
             if (fabs(c) > vmax) vmax = fabs(c);
         }
@@ -550,6 +553,7 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
         for (size_t i = 0; i < n; i++) {
             double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;
             v0[i] = (p->velocity_mode == 0) ? p->v0 : p->mobility * (fr - tau[i]);
+            if (mfac) v0[i] *= mfac[i];
         }
         st->mean_up13 = mean; st->eps_bar13 = eps; st->sigma_bar13 = sig;
     }

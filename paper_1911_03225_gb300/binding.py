@@ -44,7 +44,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget", "fdm_batch_enqueue_steps",
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
-           "fdm_set_launch_config", "fdm_launch_candidates"]
+           "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field"]
 
 
 class CParams(C.Structure):
@@ -185,6 +185,8 @@ def load():
     lib.fdm_batch_get_launch_config.restype = C.c_int
     lib.fdm_set_launch_config.argtypes = [H, C.POINTER(CLaunchConfig)]
     lib.fdm_set_launch_config.restype = C.c_int
+    lib.fdm_set_mobility_field.argtypes = [H, d]
+    lib.fdm_set_mobility_field.restype = C.c_int
     lib.fdm_launch_candidates.argtypes = [C.POINTER(CParams), C.POINTER(CLaunchConfig), C.c_int32]
     lib.fdm_launch_candidates.restype = C.c_int32
     for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
@@ -273,6 +275,15 @@ class FDM:
         else:
             _check(st, "fdm_set_density")
         return res.value
+
+    def set_mobility_field(self, factor=None):
+        """Per-cell mobility factor m(x) >= 0 multiplying the celerity (heterogeneous drag,
+        m = 0 in impenetrable precipitates, Sec. 5.3); None restores m = 1."""
+        if factor is None:
+            _check(self.lib.fdm_set_mobility_field(self.h, None), "fdm_set_mobility_field")
+            return
+        f = _field(factor, self.shape)
+        _check(self.lib.fdm_set_mobility_field(self.h, _dptr(f)), "fdm_set_mobility_field")
 
     def set_plastic_distortion(self, up13):
         u = _field(up13, self.shape)

@@ -321,6 +321,7 @@ struct fdm_handle {
     int prec;                // FDM_FP64, FDM_MIXED or FDM_DF64
     size_t n;                // n1 * n2
     void* rd[4];             // readout buffers (type T, n each), allocated on first use
+    void* mfac_buf;          // mobility factor (type T, n), allocated on first use
     Dev rd64;                // mixed precision: FP64 spectra and tables for the Nye readout
     void* rd64_buf[3];       //   U13 and the two Nye components in FP64 (n each)
 };
@@ -625,6 +626,28 @@ fdm_status fdm_get_info(fdm_handle* h, fdm_step_info* info) {
 int32_t fdm_kernels_per_step(const fdm_handle* h) {
     (void)h;
     return kKernelsPerStep;
+}
+
+fdm_status fdm_set_mobility_field(fdm_handle* h, const double* factor) {
+    if (!h) return FDM_ERR_INVALID_ARG;
+    if (h->next_phase != 0) return FDM_ERR_STATE;
+    if (factor)
+        for (size_t i = 0; i < h->n; ++i)
+            if (!std::isfinite(factor[i]) || factor[i] < 0.0) return FDM_ERR_INVALID_ARG;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    h->graphs.destroy();   // the step kernels were captured with the previous field
+    if (!factor) {
+        h->d.mfac = nullptr;   // the buffer stays owned by the arena for later use
+        return FDM_OK;
+    }
+    if (!h->mfac_buf) {
+        fdm_status st = h->arena.alloc(&h->mfac_buf, h->n * elt_size(&h->d.p));
+        if (st) return st;
+    }
+    fdm_status st = upload_field(h->mfac_buf, factor, h->n, h->prec, 0.0, h->stream);
+    if (st) return st;
+    h->d.mfac = h->mfac_buf;
+    return FDM_OK;
 }
 
 fdm_status fdm_get_launch_config(const fdm_handle* h, fdm_launch_config* cfg) {

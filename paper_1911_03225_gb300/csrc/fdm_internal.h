@@ -46,6 +46,7 @@ struct Dev {
     int gated;             // step launches honour each instance's steps_left (batches)
     void* phi[2];          // double-buffered U13 (type T); the current one is sc[i].cur
     void* phi_lo[2];       // FDM_MIXED: low FP32 words of U13 (U13 = phi + phi_lo); else null
+    void* mfac;            // T [count][n]: mobility factor m(x) of the celerity, or null (m = 1)
     void* tau;             // T
     void* spec;            // cpx<T> [n1/2][n2] per instance
     void* spec2;           // cpx<T> [n1/2][n2] (single instance only; readouts)

@@ -319,10 +319,12 @@ struct VelLaw {
     int friction;        // tau_y != 0 and stress driven
     T v0, mobility;
     double tau_y, beta;  // lattice friction (FP64; evaluated only when friction != 0)
+    const T* mfac;       // per-cell mobility factor m(x) (heterogeneous drag, Sec. 5.3), or null
 };
 
-template <typename T> VelLaw<T> make_vel(const fdm_params& p) {
+template <typename T> VelLaw<T> make_vel(const fdm_params& p, const void* mfac = nullptr) {
     VelLaw<T> v;
+    v.mfac = static_cast<const T*>(mfac);
     v.mode = p.velocity_mode;
     v.friction = (p.tau_y != 0.0 && p.velocity_mode == FDM_V_STRESS) ? 1 : 0;
     v.v0 = T(p.v0);
@@ -427,6 +429,10 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
             T u0 = T(0), u1 = T(0);
             if (need_up) { u0 = up[o]; u1 = up[o + 1]; }
             T c0 = celerity(a.vel, v.x, u0, phi_ref), c1 = celerity(a.vel, v.y, u1, phi_ref);
+            if (a.vel.mfac) {
+                c0 = c0 * a.vel.mfac[inst * nn + o];
+                c1 = c1 * a.vel.mfac[inst * nn + o + 1];
+            }
             if constexpr (std::is_same<T, double>::value) {
                 const unsigned long long m0 = ubits(c0) & kMagBits, m1 = ubits(c1) & kMagBits;
                 vbits = m0 > vbits ? m0 : vbits;
@@ -590,7 +596,8 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
         const T tau_k = s_tau[threadIdx.y + k * TY][threadIdx.x];
         if constexpr (kPair) {
             const T h0 = tile[ly][lx], l0 = tile_lo[ly][lx];
-            const T v0 = celerity(a.vel, tau_k, h0 + l0, phi_ref);
+            T v0 = celerity(a.vel, tau_k, h0 + l0, phi_ref);
+            if (a.vel.mfac) v0 = v0 * a.vel.mfac[inst * nn + (size_t)y * n1 + x];
             // differences to the node value, exact in the high words for nearby values;
             // the offset-equivariant update then returns the increment of U13
             auto g = [&](int i, int j) -> T { return (tile[ly + j][lx + i] - h0) + (tile_lo[ly + j][lx + i] - l0); };
@@ -602,7 +609,8 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
             lo_out[(size_t)y * n1 + x] = lo;
         } else {
             const T up = tile[ly][lx];
-            const T v0 = celerity(a.vel, tau_k, up, phi_ref);
+            T v0 = celerity(a.vel, tau_k, up, phi_ref);
+            if (a.vel.mfac) v0 = v0 * a.vel.mfac[inst * nn + (size_t)y * n1 + x];
             auto f = [&](int i, int j) -> T { return tile[ly + j][lx + i]; };
             out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
         }
@@ -750,6 +758,7 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
                                 VelLaw<T> p, double phi_ref) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T c = celerity(p, tau[i], phi[i], phi_ref);
+        if (p.mfac) c = c * p.mfac[i];
         T m = tsqrt(a11[i] * a11[i] + a12[i] * a12[i]);
         if (m > T(0)) { v1[i] = c * a12[i] / m; v2[i] = -c * a11[i] / m; }
         else { v1[i] = T(0); v2[i] = T(0); }
@@ -888,7 +897,7 @@ void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, doub
                         cudaStream_t s) {
     const LaunchGeom& g = d.geom;
     RowArgs<T> a;
-    a.vel = make_vel<T>(d.p);
+    a.vel = make_vel<T>(d.p, d.mfac);
     a.mode = mode;
     a.phi0 = d.phi[0];
     a.phi1 = d.phi[1];
@@ -917,7 +926,7 @@ void launch_knp_shape(const Dev& d, const KnpArgs<T>& a, cudaStream_t s) {
 template <typename T>
 void launch_knp(const Dev& d, cudaStream_t s) {
     KnpArgs<T> a;
-    a.vel = make_vel<T>(d.p);
+    a.vel = make_vel<T>(d.p, d.mfac);
     a.lo0 = (const T*)d.phi_lo[0];
     a.lo1 = (const T*)d.phi_lo[1];
     a.theta = T(d.p.theta);
@@ -1016,7 +1025,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     size_t n = (size_t)d.p.n1 * d.p.n2;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
-    velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, make_vel<T>(d.p), d.phi_ref_host);
+    velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, make_vel<T>(d.p, d.mfac), d.phi_ref_host);
 }
 
 // explicit instantiations

@@ -8,11 +8,17 @@
 // per launch and the GPU.  At creation a group therefore times every candidate on its own
 // buffers, filled with a synthetic field, and keeps the fastest shape for each kernel.
 // Choices are cached for the process per (device, precision, grid, instances, scheme
-// variant), so later groups of the same kind start without timing.
+// variant), so later groups of the same kind start without timing.  If the environment
+// variable FDM_TUNE_CACHE names a file, choices also persist across processes there, one
+// JSON object per line keyed by the GPU's name and SM count; lines that do not parse or
+// name shapes this build does not offer are ignored.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -30,6 +36,80 @@ template <typename T> constexpr int prec_code();
 template <> constexpr int prec_code<double>() { return FDM_FP64; }
 template <> constexpr int prec_code<float>() { return FDM_MIXED; }
 template <> constexpr int prec_code<df>() { return FDM_DF64; }
+
+// ---- persistent cache (FDM_TUNE_CACHE)
+struct FileKey {
+    std::string gpu;
+    int sms, prec, n1, n2, count, gated, tl, vm, fr;
+    bool operator<(const FileKey& o) const {
+        return std::tie(gpu, sms, prec, n1, n2, count, gated, tl, vm, fr) <
+               std::tie(o.gpu, o.sms, o.prec, o.n1, o.n2, o.count, o.gated, o.tl, o.vm, o.fr);
+    }
+};
+struct FileVal {
+    int R, C, shape;
+    double us[kKernelsPerStep];
+};
+bool g_file_loaded = false;
+std::map<FileKey, FileVal> g_file_cache;
+
+const char* cache_path() {
+    const char* p = std::getenv("FDM_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+bool device_identity(int dev, std::string* name, int* sms) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    name->assign(prop.name);
+    for (char& c : *name)
+        if (c == '"' || c == '\\') c = '_';
+    *sms = prop.multiProcessorCount;
+    return true;
+}
+
+// reads the cache file once (caller holds g_tune_mutex)
+void load_file_cache() {
+    if (g_file_loaded) return;
+    g_file_loaded = true;
+    const char* path = cache_path();
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[1024], gpu[256];
+    while (std::fgets(line, sizeof line, f)) {
+        FileKey k;
+        FileVal v;
+        int n = std::sscanf(line,
+                            "{\"gpu\": \"%255[^\"]\", \"sms\": %d, \"precision\": %d, \"n1\": %d, \"n2\": %d, "
+                            "\"instances\": %d, \"gated\": %d, \"time_level\": %d, \"velocity_mode\": %d, "
+                            "\"friction\": %d, \"rows\": %d, \"cols\": %d, \"stencil_shape\": %d, "
+                            "\"kernel_us\": [%lf, %lf, %lf, %lf]}",
+                            gpu, &k.sms, &k.prec, &k.n1, &k.n2, &k.count, &k.gated, &k.tl, &k.vm, &k.fr, &v.R, &v.C,
+                            &v.shape, &v.us[0], &v.us[1], &v.us[2], &v.us[3]);
+        if (n != 17) continue;
+        k.gpu = gpu;
+        g_file_cache[k] = v;
+    }
+    std::fclose(f);
+}
+
+void append_file_cache(const FileKey& k, const FileVal& v) {
+    const char* path = cache_path();
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"gpu\": \"%s\", \"sms\": %d, \"precision\": %d, \"n1\": %d, \"n2\": %d, \"instances\": %d, "
+                 "\"gated\": %d, \"time_level\": %d, \"velocity_mode\": %d, \"friction\": %d, \"rows\": %d, "
+                 "\"cols\": %d, \"stencil_shape\": %d, \"kernel_us\": [%.3f, %.3f, %.3f, %.3f]}\n",
+                 k.gpu.c_str(), k.sms, k.prec, k.n1, k.n2, k.count, k.gated, k.tl, k.vm, k.fr, v.R, v.C, v.shape,
+                 v.us[0], v.us[1], v.us[2], v.us[3]);
+    std::fclose(f);
+}
 
 struct Events {
     cudaEvent_t e[kKernelsPerStep + 1] = {};
@@ -78,6 +158,19 @@ cudaError_t autotune_group(Dev& d, cudaStream_t s) {
     const fdm_params& p = d.p;
     const TuneKey key{dev, prec_code<T>(), p.n1, p.n2, d.count, d.gated, p.time_level, p.velocity_mode,
                       p.tau_y != 0.0 ? 1 : 0};
+    int Rs[8], Cs[8];
+    const int nR = row_candidates<T>(p.n1, p.n2, Rs, 8), nC = col_candidates<T>(p.n1, p.n2, Cs, 8);
+    if (nR == 0 || nC == 0) return cudaSuccess;  // keep the heuristic shapes
+    FileKey fkey;
+    const bool have_id = device_identity(dev, &fkey.gpu, &fkey.sms);
+    fkey.prec = prec_code<T>();
+    fkey.n1 = p.n1;
+    fkey.n2 = p.n2;
+    fkey.count = d.count;
+    fkey.gated = d.gated;
+    fkey.tl = p.time_level;
+    fkey.vm = p.velocity_mode;
+    fkey.fr = p.tau_y != 0.0 ? 1 : 0;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
@@ -85,10 +178,21 @@ cudaError_t autotune_group(Dev& d, cudaStream_t s) {
             d.geom = it->second;
             return cudaSuccess;
         }
+        load_file_cache();
+        auto ft = have_id ? g_file_cache.find(fkey) : g_file_cache.end();
+        if (ft != g_file_cache.end()) {
+            const FileVal& v = ft->second;
+            const bool r_ok = std::find(Rs, Rs + nR, v.R) != Rs + nR, c_ok = std::find(Cs, Cs + nC, v.C) != Cs + nC;
+            if (r_ok && c_ok && v.shape >= 0 && v.shape < kKnpShapes) {
+                LaunchGeom gm = geometry<T>(p.n1, p.n2, v.R, v.C, v.shape);
+                gm.tuned = 1;
+                for (int ph = 0; ph < kKernelsPerStep; ++ph) gm.kernel_us[ph] = v.us[ph];
+                g_tune_cache.emplace(key, gm);
+                d.geom = gm;
+                return cudaSuccess;
+            }
+        }
     }
-    int Rs[8], Cs[8];
-    const int nR = row_candidates<T>(p.n1, p.n2, Rs, 8), nC = col_candidates<T>(p.n1, p.n2, Cs, 8);
-    if (nR == 0 || nC == 0) return cudaSuccess;  // keep the heuristic shapes
     Events ev;
     if (!ev.ok) return cudaErrorUnknown;
     launch_tune_fill<T>(d, s);
@@ -133,6 +237,12 @@ cudaError_t autotune_group(Dev& d, cudaStream_t s) {
     d.geom = best;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune_cache.emplace(key, best);
+    if (have_id) {
+        FileVal v{best.R, best.C, best.knp_shape, {}};
+        for (int ph = 0; ph < kKernelsPerStep; ++ph) v.us[ph] = best.kernel_us[ph];
+        g_file_cache[fkey] = v;
+        append_file_cache(fkey, v);
+    }
     return cudaSuccess;
 }
 

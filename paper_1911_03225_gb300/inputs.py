@@ -99,6 +99,27 @@ def ring_alpha(n: int, r0: float = 100.0, sigma: float = 2.0, amp: float = 1.0):
     return g * uy, -g * ux
 
 
+def square_signed_distance(x, y, half_side: float):
+    """Signed Euclidean distance to the square |x|, |y| <= half_side (negative inside)."""
+    qx, qy = np.abs(x) - half_side, np.abs(y) - half_side
+    outside = np.hypot(np.maximum(qx, 0.0), np.maximum(qy, 0.0))
+    return outside + np.minimum(np.maximum(qx, qy), 0.0)
+
+
+def loop_profile(d, sigma: float, amp: float = 1.0):
+    """U13 across a loop with a Gaussian cross-section centred on the loop line, as a
+    function of the signed distance d to that line: amp * int_d^inf exp(-s^2/(2 sigma^2)) ds."""
+    return amp * sigma * math.sqrt(math.pi / 2.0) * erfc(np.asarray(d) / (sigma * math.sqrt(2.0)))
+
+
+def square_up(n: int, half_side: float = 60.0, sigma: float = 2.0, amp: float = 1.0, centre=None):
+    """Polygonal (square) loop: U13 = loop_profile(signed distance to the square's edges)
+    (Sec. 4.4.2's loop with corners), centred at `centre` (default: the cell centre)."""
+    cx, cy = centre if centre is not None else (n / 2.0, n / 2.0)
+    x, y = _centred_coords(n, n, cx, cy)
+    return loop_profile(square_signed_distance(x, y, half_side), sigma, amp)
+
+
 def random_up(n: int, seed: int = 0, ell: float = 16.0, rms_alpha: float = 0.1, dx: float = 1.0):
     """Zero-mean smoothed Gaussian random U13 with RMS |grad U13| = rms_alpha."""
     z = normal_field(n, n, seed)

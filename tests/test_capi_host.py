@@ -82,6 +82,7 @@ def test_null_arguments(lib):
     assert lib.fdm_static_solve(None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_set_plastic_distortion(None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_read_fields(None, 1, None, None, None, None, None, None) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_set_mobility_field(None, None) == binding.FDM_ERR_INVALID_ARG
     lib.fdm_destroy(None)   # NULL-safe
 
 

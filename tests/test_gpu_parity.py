@@ -193,6 +193,99 @@ def test_ring_expansion_long_within_rounding_envelope(precision, eps):
     assert info.t == pytest.approx(40.0, rel=1e-12)
 
 
+@pytest.mark.parametrize("v0", [-1.0, 1.0])
+@pytest.mark.parametrize("precision,eps", [(B.FP64, 1e-16), (B.DF64, 100 * 2.0 ** -48), (B.MIXED, 6e-8)])
+def test_square_loop_expansion_and_shrinkage(v0, precision, eps):
+    """Polygonal loop (Sec. 4.4.2): square of half side ~40 cells, Gaussian section sigma 2,
+    MC limiter, CFL 0.4, expansion (v0 = -1) and shrinkage (v0 = +1), 20 steps.  The MC
+    limiter amplifies rounding differences, and more so at the square's corners than on the
+    smooth ring, so the GPU must stay within the oracle's own spread under a perturbation
+    of the size of the path's rounding (as for the long ring run); the full-size run is
+    checked against the exact solution in test_gpu_full_configs.py.  The square sits off
+    the grid's symmetry: on a symmetric square the limiter meets exact ties along the
+    diagonals, and rounding order alone would pick the branch."""
+    n, steps = 128, 20
+    up0 = inputs.square_up(n, half_side=40.3, sigma=2.0, centre=(64.31, 63.77))
+    p = Params(n1=n, n2=n, v0=v0, theta=2.0, cfl=0.4, precision=precision)
+    got, info, ref, _ = run_both(p, up0=up0, steps=steps)
+    pert = up0 * (1 + eps * np.random.default_rng(1).standard_normal(up0.shape))
+    ref2, _ = oracle.run(oparams(p), pert, steps)
+    envelope = rel(ref2.up13, ref.up13)
+    assert rel(got["up13"], ref.up13) < 10 * envelope + 1e-14
+    assert info.t == pytest.approx(ref.t, rel=1e-12)
+
+
+def _precipitates(n, centres, radius):
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    m = np.ones((n, n))
+    for cx, cy in centres:
+        m[np.hypot(x - cx, y - cy) <= radius] = 0.0
+    return m
+
+
+@pytest.mark.parametrize("precision,eps", [(B.FP64, 1e-16), (B.DF64, 100 * 2.0 ** -48), (B.MIXED, 6e-8)])
+def test_orowan_precipitates_match_oracle(precision, eps):
+    """Heterogeneous drag (Sec. 5.3): edge walls driven by an applied stress through a field
+    of impenetrable precipitates (m = 0) and a softer zone (m = 0.5), stress-driven velocity,
+    minmod, 40 steps.  The driven wall pair amplifies rounding differences by ~1.3 per step
+    (it does so without precipitates too: exact after one step, 1e-8 after five), so the GPU
+    must stay within the oracle's own spread under a perturbation of the size of the path's
+    rounding.  Exactly: nodes inside precipitates never change, their velocity is zero."""
+    n, steps = 128, 40
+    up0 = inputs.lines_up(n, sep=32.0, sigma=3.0)
+    m = _precipitates(n, [(64, 30), (64, 90), (40, 64)], 6.0)
+    m[:, 100:110] *= 0.5
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, mobility=1.0, loading_mode=B.LOAD_STRESS,
+               sigma_bar13=0.05, cfl=0.4, theta=1.0, precision=precision)
+    with FDM(p) as sim:
+        sim.set_mobility_field(m)
+        sim.set_plastic_distortion(up0)
+        first = sim.step(1)
+        f1 = sim.read_fields("up13")["up13"]
+        sim.set_plastic_distortion(up0)
+        info = sim.step(steps)
+        got = sim.read_fields("up13", "tau13", "v1")
+    ref1, _ = oracle.run(oparams(p), up0, 1, mobility_factor=m)
+    ref, rc = oracle.run(oparams(p), up0, steps, mobility_factor=m)
+    assert rc == 0
+    tol1 = TOL64 if precision != B.MIXED else TOL_MIXED
+    assert rel(f1, ref1.up13) < tol1 and first.dt == pytest.approx(ref1.dt, rel=tol1)
+    pert = up0 * (1 + eps * np.random.default_rng(2).standard_normal(up0.shape))
+    ref2, _ = oracle.run(oparams(p), pert, steps, mobility_factor=m)
+    envelope = rel(ref2.up13, ref.up13)
+    assert rel(got["up13"], ref.up13) < 10 * envelope + 1e-14
+    inside = m == 0.0
+    if precision == B.FP64:
+        np.testing.assert_array_equal(got["up13"][inside], up0[inside])
+    else:
+        assert np.abs(got["up13"][inside] - up0[inside]).max() < 1e-6 * np.abs(up0).max()
+    assert np.all(got["v1"][inside] == 0.0)
+
+
+def test_mobility_field_cleared_and_uniform_factor_rescales_time():
+    n = 64
+    up0 = inputs.random_up(n, seed=8, ell=6.0)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.02, cfl=0.4)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        a = sim.step(10)
+        ua = sim.read_fields("up13")["up13"]
+        sim.set_mobility_field(np.full((n, n), 4.0))
+        sim.set_plastic_distortion(up0)
+        b = sim.step(10)
+        ub = sim.read_fields("up13")["up13"]
+        sim.set_mobility_field(None)
+        sim.set_plastic_distortion(up0)
+        c = sim.step(10)
+        uc = sim.read_fields("up13")["up13"]
+        with pytest.raises(FDMError):
+            sim.set_mobility_field(np.full((n, n), -1.0))
+    assert np.abs(ub - ua).max() < 1e-12 * np.abs(ua).max()
+    assert b.t == pytest.approx(a.t / 4.0, rel=1e-13)
+    np.testing.assert_array_equal(uc, ua)
+    assert c.t == a.t
+
+
 @pytest.mark.parametrize("shape", [(128, 128), (64, 256)])
 @pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.DF64, TOL64), (B.MIXED, TOL_MIXED)])
 def test_coupled_random_field(shape, precision, tol):

@@ -97,3 +97,33 @@ def test_invalid_launch_shapes_refused():
                 sim.set_launch_config(bad)
             assert e.value.status == B.FDM_ERR_INVALID_ARG
         assert sim.launch_config() == good
+
+
+def test_tuning_persists_across_processes(tmp_path):
+    """With FDM_TUNE_CACHE set, the first process times the shapes and appends one JSON line;
+    a second process reads the choice back instead of timing again."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.jsonl"
+    code = ("import json, sys; sys.path.insert(0, %r)\n"
+            "from paper_1911_03225_gb300 import FDM, Params\n"
+            "from paper_1911_03225_gb300 import binding as B\n"
+            "p = Params(n1=256, n2=128, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, "
+            "eps_bar13_rate=1e-4, cfl=0.4, precision=B.MIXED, autotune=1)\n"
+            "with FDM(p) as s: print(json.dumps(s.launch_config()))\n" % root)
+    env = dict(os.environ, FDM_TUNE_CACHE=str(path))
+    runs = [subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+            for _ in range(2)]
+    for r in runs:
+        assert r.returncode == 0, r.stderr[-2000:]
+    first, second = (json.loads(r.stdout.strip().splitlines()[-1]) for r in runs)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == 1 and lines[0]["n1"] == 256 and lines[0]["n2"] == 128
+    assert first["tuned"] == 1 and second["tuned"] == 1
+    for k in ("rows_per_block", "cols_per_block", "stencil_block_rows", "stencil_nodes", "stencil_min_blocks"):
+        assert first[k] == second[k]
+    assert second["kernel_us"] == pytest.approx(lines[0]["kernel_us"], abs=1e-9)
+    assert first["kernel_us"] == pytest.approx(second["kernel_us"], abs=1e-3)

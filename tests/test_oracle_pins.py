@@ -358,6 +358,74 @@ def test_hopf_lax_ring_expansion_converges():
     assert math.log2(e1 / e2) > 1.5 and math.log2(e2 / e3) > 1.5
 
 
+def _square_setup(n, L=64.0, a=12.0, sig=1.5):
+    """Square loop (half side a, Gaussian section sig) on an L x L periodic cell with n nodes
+    per side: (U13, signed distance to the square, X, Y, h)."""
+    h = L / n
+    x = (np.arange(n) * h) - L / 2
+    X, Y = np.meshgrid(x, x)
+    sd = inputs.square_signed_distance(X, Y, a)
+    return inputs.loop_profile(sd, sig), sd, X, Y, h
+
+
+def _square_move(phi, v0, T, h, cfl=0.4):
+    dt = cfl * h
+    steps = int(round(T / dt))
+    for _ in range(steps):
+        phi = oracle.knp2d_step(phi, v0, dt, theta=2.0, h=h)
+    return phi, steps * dt
+
+
+def _rms(e, mask):
+    return float(np.sqrt(np.mean(e[mask] ** 2)))
+
+
+def test_square_loop_expansion_takes_the_fan_and_shrinkage_keeps_corners():
+    """Sec. 4.4.2: a loop with corners admits several weak solutions; the scheme must pick the
+    viscosity (Hopf-Lax) one.  With U13 = profile(signed distance to the square), profile
+    decreasing, the dilation (v0 = -1) is profile(sd - t): the exterior distance turns each
+    corner into an arc of radius t (expansion fan); the erosion (v0 = +1) is profile(sd + t):
+    corners stay sharp.  The expanding loop must converge to the fan and stay far from the
+    sharp-cornered alternative; the shrinking loop converges at order > 1.5, corners included."""
+    T, sig = 6.0, 1.5
+    fan, alt = {}, {}
+    for n in (64, 128):
+        phi0, sd, X, Y, h = _square_setup(n)
+        phi, t = _square_move(phi0, -1.0, T, h)
+        band = np.abs(sd - t) < 6.0
+        fan[n] = _rms(phi - inputs.loop_profile(sd - t, sig), band)
+        sharp = inputs.loop_profile(np.maximum(np.abs(X), np.abs(Y)) - 12.0 - t, sig)
+        alt[n] = _rms(phi - sharp, band)
+    assert fan[128] < fan[64]
+    assert alt[128] > 0.25 and alt[128] > 3.5 * fan[128]
+    shrink, corner = {}, {}
+    for n in (64, 128, 256):
+        phi0, sd, X, Y, h = _square_setup(n)
+        phi, t = _square_move(phi0, 1.0, T, h)
+        band = np.abs(sd + t) < 6.0
+        err = phi - inputs.loop_profile(sd + t, sig)
+        shrink[n] = _rms(err, band)
+        corner[n] = _rms(err, band & (np.abs(np.abs(X) - np.abs(Y)) < 1.0))
+    assert math.log2(shrink[64] / shrink[128]) > 1.5 and math.log2(shrink[128] / shrink[256]) > 1.5
+    assert corner[256] < 2.5 * shrink[256]
+
+
+def test_square_loop_expansion_then_shrinkage_returns_the_initial_loop():
+    """Sec. 4.4.2: reversing the expanded polygonal loop brings back its initial shape: the
+    closing (dilation then erosion by the same disc) of the convex sublevel sets returns
+    them, so the exact solution returns U0.  The numerical round trip converges to U0,
+    corners included."""
+    rel, corner = {}, {}
+    for n in (128, 256):
+        phi0, sd, X, Y, h = _square_setup(n)
+        phi, _ = _square_move(phi0, -1.0, 6.0, h)
+        phi, _ = _square_move(phi, 1.0, 6.0, h)
+        rel[n] = np.linalg.norm(phi - phi0) / np.linalg.norm(phi0)
+        corner[n] = _rms(phi - phi0, (np.abs(sd) < 6.0) & (np.abs(np.abs(X) - np.abs(Y)) < 1.0))
+    assert rel[128] < 2e-2 and rel[256] < 4e-3
+    assert corner[256] < 0.5 * corner[128]
+
+
 def _flat_top_ring(n, r_in, r_out, s):
     """U13 of a loop whose density is uniform across its width (Sec. 4.2: the density is
     spread uniformly over a surface of the dislocation's width), edges smoothed over s."""
@@ -489,3 +557,53 @@ def test_nondimensional_numbers_printed_in_paper():
     dt2 = units.cfl_time_step(g["cfl"], dx2, 1.0)
     assert dt2 == pytest.approx(g["dt_2d_approx"], rel=0.03)
     assert al.time_seconds(dt2) == pytest.approx(g["dt_2d_seconds_approx"], rel=0.03)
+
+
+# ------------------------------------------------------------------ heterogeneous drag
+def _obstacle_mask(n, centres, radius):
+    """Mobility factor with impenetrable circular precipitates (m = 0 inside, 1 outside)."""
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    m = np.ones((n, n))
+    for cx, cy in centres:
+        m[np.hypot(x - cx, y - cy) <= radius] = 0.0
+    return m
+
+
+def test_mobility_factor_one_is_the_uniform_law():
+    n = 32
+    up0 = inputs.random_up(n, seed=5, ell=4.0)
+    p = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=1, eps_bar13_rate=1e-3, cfl=0.4)
+    a, _ = oracle.run(p, up0, 8)
+    b, _ = oracle.run(p, up0, 8, mobility_factor=np.ones((n, n)))
+    np.testing.assert_array_equal(a.up13, b.up13)
+    assert a.t == b.t
+
+
+def test_precipitates_never_change_and_the_rest_moves():
+    """Sec. 5.3 (Orowan): inside a precipitate the drag is infinite, so v0 = 0 there; the
+    update at a node with v0 = 0 returns the node's value exactly (both speeds vanish, the
+    intermediate points coincide with the node, the weights are 1/2), so U13 inside the
+    precipitates never changes while the walls around them move."""
+    n = 64
+    up0 = inputs.lines_up(n, sep=24.0, sigma=2.0)
+    m = _obstacle_mask(n, [(32, 20), (32, 44)], 5.0)
+    p = oracle.Params(n1=n, n2=n, velocity_mode=0, v0=1.0, cfl=0.5)
+    st, rc = oracle.run(p, up0, 20, mobility_factor=m)
+    assert rc == 0
+    inside = m == 0.0
+    np.testing.assert_array_equal(st.up13[inside], up0[inside])
+    assert np.abs(st.up13 - up0)[~inside].max() > 0.5
+    np.testing.assert_array_equal(st.v0[inside], 0.0)
+
+
+def test_uniform_mobility_factor_rescales_time_only():
+    """The update depends on v0 only through v0 dt and through ratios of speeds, and dt
+    follows CFL / max |v0|: a uniform factor c gives the same field per step with time
+    steps divided by c."""
+    n = 32
+    up0 = inputs.random_up(n, seed=6, ell=4.0)
+    p = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=0, sigma_bar13=0.02, cfl=0.4)
+    a, _ = oracle.run(p, up0, 10)
+    b, _ = oracle.run(p, up0, 10, mobility_factor=np.full((n, n), 4.0))
+    assert np.abs(b.up13 - a.up13).max() < 1e-13 * np.abs(a.up13).max()
+    assert b.t == pytest.approx(a.t / 4.0, rel=1e-14)
