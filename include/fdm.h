@@ -50,7 +50,7 @@ typedef enum {
 } fdm_status;
 
 enum { FDM_V_PRESCRIBED = 0, FDM_V_STRESS = 1 };
-enum { FDM_LOAD_STRESS = 0, FDM_LOAD_STRAIN_RAMP = 1, FDM_LOAD_ZERO_MEAN_STRESS = 2 };
+enum { FDM_LOAD_STRESS = 0, FDM_LOAD_STRAIN_RAMP = 1, FDM_LOAD_ZERO_MEAN_STRESS = 2, FDM_LOAD_STRAIN_RATE = 3 };
 enum { FDM_FP64 = 0, FDM_MIXED = 1, FDM_DF64 = 2 };
 enum { FDM_T_MIDPOINT = 0, FDM_T_LITERAL = 1 };
 
@@ -71,7 +71,10 @@ typedef struct {
     double dt_max;           /* upper bound on dt (<= 0: none); dt when every v0 is 0         */
     int32_t loading_mode;    /* FDM_LOAD_* (Sec. 3.1.2 sigma-hat(0); Sec. 5.1)                 */
     double sigma_bar13;      /* FDM_LOAD_STRESS: macroscopic stress                          */
-    double eps_bar13_0;      /* FDM_LOAD_STRAIN_RAMP: eps_bar13 = eps_bar13_0 + rate * step   */
+    double eps_bar13_0;      /* FDM_LOAD_STRAIN_RAMP: eps_bar13 = eps_bar13_0 + rate * step;
+                                FDM_LOAD_STRAIN_RATE: eps_bar13 = eps_bar13_0 + rate * t
+                                (Sec. 5.1); FDM_LOAD_ZERO_MEAN_STRESS: eps_bar13 = <U13>/2,
+                                so that sigma_bar13 = 0 (the equilibration stage, Sec. 5.1) */
     double eps_bar13_rate;
     int32_t time_level;      /* FDM_T_MIDPOINT (default) or FDM_T_LITERAL (Sec. 3.2.2 Step 3) */
     int32_t precision;       /* FDM_FP64: native FP64 throughout.
@@ -190,6 +193,12 @@ fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
+
+/* Switches the macroscopic loading between stages of a run (Sec. 5.1: equilibration at
+ * zero mean stress, then a strain rate): the next step uses the new mode and values; step
+ * and time carry on.  Same validation as fdm_create; waits for the stream. */
+fdm_status fdm_set_loading(fdm_handle *h, int32_t mode, double sigma_bar13, double eps_bar13_0,
+                           double eps_bar13_rate);
 
 /* Heterogeneous drag (Sec. 5.3, Orowan mechanism: precipitates with infinite drag):
  * factor[n2][n1] (host, float64, finite, >= 0) multiplies the celerity of every node,

@@ -462,7 +462,8 @@ typedef struct {
     double dx, E, nu;
     int32_t velocity_mode;      /* 0 prescribed uniform v0, 1 stress driven */
     double v0, mobility, tau_y, beta, theta, cfl, dt_max;
-    int32_t loading_mode;       /* 0 stress (sigma_bar13), 1 strain ramp, 2 zero mean stress */
+    int32_t loading_mode;       /* 0 stress (sigma_bar13), 1 strain ramp per step, 2 zero mean
+                                   stress, 3 strain rate in time */
     double sigma_bar13, eps_bar13_0, eps_bar13_rate;
     int32_t time_level;         /* 0 midpoint, 1 literal */
 } oracle_params;
@@ -475,15 +476,18 @@ typedef struct {
 
 static double shear_modulus(const oracle_params *p) { return p->E / (2.0 * (1.0 + p->nu)); }
 
-/* macroscopic stress at step `step` (Sec. 3.1.2 sigma-hat(0); Sec. 5.1 loading paths; G10) */
-static void loading(const oracle_params *p, int64_t step, double mean_up13, double *eps, double *sig)
+/* macroscopic stress at step `step`, time t (Sec. 3.1.2 sigma-hat(0); Sec. 5.1 loading
+ * paths; G10).  Modes: 0 given stress; 1 strain ramp per step; 2 zero mean stress (the
+ * equilibration stage of Sec. 5.1); 3 strain rate in time, eps = eps0 + rate t (Sec. 5.1). */
+static void loading(const oracle_params *p, int64_t step, double t, double mean_up13, double *eps, double *sig)
 {
     double mu = shear_modulus(p), frac = (double)p->nh / (double)p->nz;
     if (p->loading_mode == 0) {
         *sig = p->sigma_bar13;
         *eps = (p->sigma_bar13 + mu * frac * mean_up13) / (2.0 * mu);
-    } else if (p->loading_mode == 1) {
-        *eps = p->eps_bar13_0 + p->eps_bar13_rate * (double)step;
+    } else if (p->loading_mode == 1 || p->loading_mode == 3) {
+        double x = p->loading_mode == 1 ? (double)step : t;
+        *eps = p->eps_bar13_0 + p->eps_bar13_rate * x;
         *sig = 2.0 * mu * (*eps) - mu * frac * mean_up13;
     } else {
         *eps = 0.5 * frac * mean_up13;  /* eps_bar13 = <U13>/2 over the cell (Sec. 5.1) */
@@ -509,7 +513,7 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
     for (int it = 0; it < nsteps; it++) {
         double mean = oracle_sum(n, up13) / (double)n;
         double eps, sig;
-        loading(p, st->step, mean, &eps, &sig);
+        loading(p, st->step, st->t, mean, &eps, &sig);
         /* static problem with the previous plastic distortion (Sec. 3.1.1) */
         oracle_static_tau(n1, n2, up13, K, sig, tau);
         /* celerity (Sec. 3.2.3 Hamiltonian; Sec. 4.1 prescribed) */
@@ -541,14 +545,14 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
         st->max_abs_v0 = vmax;
         st->mean_up13 = oracle_sum(n, up13) / (double)n;
         /* loading state of the new step (used by the next static solve) */
-        loading(p, st->step, st->mean_up13, &eps, &sig);
+        loading(p, st->step, st->t, st->mean_up13, &eps, &sig);
         st->eps_bar13 = eps;
         st->sigma_bar13 = sig;
         if (!isfinite(dt)) rc = 1;
     }
     if (nsteps == 0) {
         double mean = oracle_sum(n, up13) / (double)n, eps, sig;
-        loading(p, st->step, mean, &eps, &sig);
+        loading(p, st->step, st->t, mean, &eps, &sig);
         oracle_static_tau(n1, n2, up13, K, sig, tau);
         for (size_t i = 0; i < n; i++) {
             double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;

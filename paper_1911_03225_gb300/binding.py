@@ -27,7 +27,7 @@ FDM_ERR_STATE = 8
 FDM_ERR_TOO_LARGE = 9
 
 V_PRESCRIBED, V_STRESS = 0, 1
-LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS = 0, 1, 2
+LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS, LOAD_STRAIN_RATE = 0, 1, 2, 3
 FP64, MIXED, DF64 = 0, 1, 2
 T_MIDPOINT, T_LITERAL = 0, 1
 
@@ -44,7 +44,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget", "fdm_batch_enqueue_steps",
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
-           "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field"]
+           "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading"]
 
 
 class CParams(C.Structure):
@@ -187,6 +187,8 @@ def load():
     lib.fdm_set_launch_config.restype = C.c_int
     lib.fdm_set_mobility_field.argtypes = [H, d]
     lib.fdm_set_mobility_field.restype = C.c_int
+    lib.fdm_set_loading.argtypes = [H, C.c_int32, C.c_double, C.c_double, C.c_double]
+    lib.fdm_set_loading.restype = C.c_int
     lib.fdm_launch_candidates.argtypes = [C.POINTER(CParams), C.POINTER(CLaunchConfig), C.c_int32]
     lib.fdm_launch_candidates.restype = C.c_int32
     for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
@@ -295,6 +297,32 @@ class FDM:
     # -- compute
     def static_solve(self):
         _check(self.lib.fdm_static_solve(self.h), "fdm_static_solve")
+
+    def set_loading(self, mode: int, sigma_bar13: float = 0.0, eps_bar13_0: float = 0.0,
+                    eps_bar13_rate: float = 0.0):
+        """Switch the macroscopic loading for the following steps (stages of Sec. 5.1)."""
+        _check(self.lib.fdm_set_loading(self.h, int(mode), float(sigma_bar13), float(eps_bar13_0),
+                                        float(eps_bar13_rate)), "fdm_set_loading")
+
+    def equilibrate(self, tol: float = 1e-6, chunk: int = 50, max_steps: int = 100000):
+        """Equilibration stage of Sec. 5.1: zero mean stress until the microstructure stops
+        evolving, i.e. until a chunk of steps changes U13 by less than ``tol`` (relative L2)
+        or ``max_steps`` are taken.  Returns (steps taken, last relative change); the loading
+        stays at zero mean stress (switch it with ``set_loading`` for the next stage)."""
+        self.set_loading(LOAD_ZERO_MEAN_STRESS)
+        prev = self.read_fields("up13")["up13"]
+        taken, change = 0, float("inf")
+        while taken < max_steps:
+            k = min(chunk, max_steps - taken)
+            self.enqueue_steps(k)
+            self.sync()
+            taken += k
+            cur = self.read_fields("up13")["up13"]
+            change = float(np.linalg.norm(cur - prev) / max(np.linalg.norm(prev), 1e-300))
+            if change < tol:
+                break
+            prev = cur
+        return taken, change
 
     def step(self, nsteps: int = 1, info: bool = True) -> Optional[StepInfo]:
         if info:

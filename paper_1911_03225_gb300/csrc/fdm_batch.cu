@@ -121,7 +121,7 @@ fdm_status fdm_batch_set_plastic_distortion(fdm_batch* b, int32_t i, const doubl
     s.mean_up13 = mean;
     s.cur = 0;
     s.steps_left = 0;
-    host_loading(G.d.p, 0, mean, &s.eps_bar13, &s.sigma_bar13);
+    host_loading(G.d.p, 0, 0.0, mean, &s.eps_bar13, &s.sigma_bar13);
     FDM_CK(cudaMemcpyAsync(G.d.sc + j, &s, sizeof(s), cudaMemcpyHostToDevice, b->stream));
     FDM_CK(cudaStreamSynchronize(b->stream));
     G.phi_ref[j] = ref;

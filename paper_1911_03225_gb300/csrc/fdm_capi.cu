@@ -297,7 +297,7 @@ fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, 
     info->dt = s.dt;
     info->max_abs_v0 = s.max_abs_v0;
     info->mean_up13 = s.phi_ref + sums[5] / (double)n;
-    host_loading(d.p, s.step, info->mean_up13, &info->eps_bar13, &info->sigma_bar13);
+    host_loading(d.p, s.step, s.t, info->mean_up13, &info->eps_bar13, &info->sigma_bar13);
     info->sum_a12_pos = sums[0];
     info->sum_a12_neg = sums[1];
     info->sum_a11_pos = sums[2];
@@ -335,7 +335,7 @@ fdm_status reset_scalars(fdm_handle* h, double mean) {
     s.mean_up13 = mean;
     s.cur = 0;
     s.steps_left = -1;
-    host_loading(h->d.p, 0, mean, &s.eps_bar13, &s.sigma_bar13);
+    host_loading(h->d.p, 0, 0.0, mean, &s.eps_bar13, &s.sigma_bar13);
     FDM_CK(cudaMemcpyAsync(h->d.sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
     FDM_CK(cudaStreamSynchronize(h->stream));
     h->next_phase = 0;
@@ -626,6 +626,22 @@ fdm_status fdm_get_info(fdm_handle* h, fdm_step_info* info) {
 int32_t fdm_kernels_per_step(const fdm_handle* h) {
     (void)h;
     return kKernelsPerStep;
+}
+
+fdm_status fdm_set_loading(fdm_handle* h, int32_t mode, double sigma_bar13, double eps_bar13_0,
+                           double eps_bar13_rate) {
+    if (!h) return FDM_ERR_INVALID_ARG;
+    fdm_params q = h->d.p;
+    q.loading_mode = mode;
+    q.sigma_bar13 = sigma_bar13;
+    q.eps_bar13_0 = eps_bar13_0;
+    q.eps_bar13_rate = eps_bar13_rate;
+    if (!params_valid(&q)) return FDM_ERR_INVALID_ARG;
+    if (h->next_phase != 0) return FDM_ERR_STATE;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    h->graphs.destroy();   // the column kernel was captured with the previous loading
+    h->d.p = q;
+    return FDM_OK;
 }
 
 fdm_status fdm_set_mobility_field(fdm_handle* h, const double* factor) {

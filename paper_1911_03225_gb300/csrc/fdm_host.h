@@ -34,7 +34,7 @@ inline bool params_valid(const fdm_params* p) {
     if (!(p->theta >= 1.0 && p->theta <= 2.0)) return false;
     if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return false;
     if (!std::isfinite(p->dt_max)) return false;
-    if (p->loading_mode < FDM_LOAD_STRESS || p->loading_mode > FDM_LOAD_ZERO_MEAN_STRESS) return false;
+    if (p->loading_mode < FDM_LOAD_STRESS || p->loading_mode > FDM_LOAD_STRAIN_RATE) return false;
     if (!std::isfinite(p->sigma_bar13) || !std::isfinite(p->eps_bar13_0) || !std::isfinite(p->eps_bar13_rate))
         return false;
     if (p->time_level != FDM_T_MIDPOINT && p->time_level != FDM_T_LITERAL) return false;
@@ -95,14 +95,14 @@ inline int red_blocks_for(size_t n) {
 }
 
 // macroscopic loading state (Sec. 3.1.2 sigma-hat(0); Sec. 5.1), same law as the kernels
-inline void host_loading(const fdm_params& p, long long step, double mean, double* eps, double* sig) {
+inline void host_loading(const fdm_params& p, long long step, double t, double mean, double* eps, double* sig) {
     const double mu = p.E / (2.0 * (1.0 + p.nu));
     const double frac = (double)p.nh / (double)p.nz;
     if (p.loading_mode == FDM_LOAD_STRESS) {
         *sig = p.sigma_bar13;
         *eps = (p.sigma_bar13 + mu * frac * mean) / (2.0 * mu);
-    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP) {
-        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (double)step;
+    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP || p.loading_mode == FDM_LOAD_STRAIN_RATE) {
+        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (p.loading_mode == FDM_LOAD_STRAIN_RAMP ? (double)step : t);
         *sig = 2.0 * mu * (*eps) - mu * frac * mean;
     } else {
         *eps = 0.5 * frac * mean;

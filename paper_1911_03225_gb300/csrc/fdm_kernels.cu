@@ -42,15 +42,15 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(fabs(v));
 }
 
-__device__ __forceinline__ void loading_state(const fdm_params& p, long long step, double mean,
+__device__ __forceinline__ void loading_state(const fdm_params& p, long long step, double t, double mean,
                                               double* eps, double* sig) {
     const double mu = p.E / (2.0 * (1.0 + p.nu));
     const double frac = (double)p.nh / (double)p.nz;
     if (p.loading_mode == FDM_LOAD_STRESS) {
         *sig = p.sigma_bar13;
         *eps = (p.sigma_bar13 + mu * frac * mean) / (2.0 * mu);
-    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP) {
-        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (double)step;
+    } else if (p.loading_mode == FDM_LOAD_STRAIN_RAMP || p.loading_mode == FDM_LOAD_STRAIN_RATE) {
+        *eps = p.eps_bar13_0 + p.eps_bar13_rate * (p.loading_mode == FDM_LOAD_STRAIN_RAMP ? (double)step : t);
         *sig = 2.0 * mu * (*eps) - mu * frac * mean;
     } else {
         *eps = 0.5 * frac * mean;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
         if (threadIdx.x == 0) {
             double mean = parts ? sci->phi_ref + tot / ((double)n1 * (double)n2) : sci->mean_up13;
             double eps, sig;
-            loading_state(a.p, sci->step, mean, &eps, &sig);
+            loading_state(a.p, sci->step, sci->t, mean, &eps, &sig);
             sci->mean_up13 = mean;
             sci->eps_bar13 = eps;
             sci->sigma_bar13 = sig;

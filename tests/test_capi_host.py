@@ -65,7 +65,7 @@ def test_launch_config_rejects_null(lib):
 @pytest.mark.parametrize("field,value", [
     ("n1", 48), ("n1", 8), ("n2", 8192), ("nh", 0), ("nh", 300), ("dx", 0.0), ("nu", 0.5),
     ("theta", 0.5), ("theta", 2.5), ("cfl", 0.0), ("cfl", 1.5), ("velocity_mode", 7),
-    ("loading_mode", 3), ("time_level", 2), ("precision", 3), ("E", -1.0), ("autotune", 2)])
+    ("loading_mode", 4), ("time_level", 2), ("precision", 3), ("E", -1.0), ("autotune", 2)])
 def test_invalid_params_rejected_without_device(lib, field, value):
     p = binding.default_params(64, 64)
     setattr(p, field, value)
@@ -83,6 +83,7 @@ def test_null_arguments(lib):
     assert lib.fdm_set_plastic_distortion(None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_read_fields(None, 1, None, None, None, None, None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_set_mobility_field(None, None) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_set_loading(None, 0, 0.0, 0.0, 0.0) == binding.FDM_ERR_INVALID_ARG
     lib.fdm_destroy(None)   # NULL-safe
 
 

@@ -262,6 +262,47 @@ def test_orowan_precipitates_match_oracle(precision, eps):
     assert np.all(got["v1"][inside] == 0.0)
 
 
+@pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.DF64, TOL64), (B.MIXED, TOL_MIXED)])
+def test_staged_loading_equilibration_then_strain_rate(precision, tol):
+    """Sec. 5.1: lattice friction (tau_y = 0.02, beta = 0.05), a zero-mean-stress stage of 30
+    steps, then a strain rate in time for 30 more steps, switched on the live handle; the
+    oracle runs the same two stages with its state carried over."""
+    n = 64
+    up0 = inputs.random_up(n, seed=12, ell=6.0, rms_alpha=0.1)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, mobility=1.0, tau_y=0.02, beta=0.05,
+               loading_mode=B.LOAD_ZERO_MEAN_STRESS, cfl=0.4, theta=1.0, precision=precision)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        i1 = sim.step(30)
+        f1 = sim.read_fields("up13", "tau13")
+        sim.set_loading(B.LOAD_STRAIN_RATE, eps_bar13_0=1e-4, eps_bar13_rate=2e-4)
+        i2 = sim.step(30)
+        f2 = sim.read_fields("up13", "tau13")
+    r1, _ = oracle.run(oparams(p), up0, 30)
+    p2 = oparams(Params(**{**p.__dict__, "loading_mode": B.LOAD_STRAIN_RATE, "eps_bar13_0": 1e-4,
+                           "eps_bar13_rate": 2e-4}))
+    r2, _ = oracle.run(p2, None, 30, state=r1)
+    assert abs(f1["tau13"].mean()) < 1e-12 * np.abs(f1["tau13"]).max() + (0 if precision != B.MIXED else 1e-7)
+    assert i1.sigma_bar13 == 0.0
+    assert rel(f1["up13"], r1.up13) < tol and rel(f1["tau13"], r1.tau13) < tol
+    assert rel(f2["up13"], r2.up13) < tol and rel(f2["tau13"], r2.tau13) < tol
+    assert i2.step == 60 and i2.t == pytest.approx(r2.t, rel=tol)
+    assert i2.eps_bar13 == pytest.approx(1e-4 + 2e-4 * i2.t, rel=1e-14)
+
+
+def test_equilibration_driver_stops_when_the_field_settles():
+    n = 64
+    up0 = inputs.random_up(n, seed=13, ell=6.0, rms_alpha=0.1)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, tau_y=0.05, beta=0.05, loading_mode=B.LOAD_STRESS,
+               sigma_bar13=0.3, cfl=0.4, theta=1.0)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        taken, change = sim.equilibrate(tol=1e-4, chunk=20, max_steps=4000)
+        info = sim.info()
+    assert taken < 4000 and change < 1e-4
+    assert info.sigma_bar13 == 0.0 and info.step == taken
+
+
 def test_mobility_field_cleared_and_uniform_factor_rescales_time():
     n = 64
     up0 = inputs.random_up(n, seed=8, ell=6.0)

@@ -607,3 +607,37 @@ def test_uniform_mobility_factor_rescales_time_only():
     b, _ = oracle.run(p, up0, 10, mobility_factor=np.full((n, n), 4.0))
     assert np.abs(b.up13 - a.up13).max() < 1e-13 * np.abs(a.up13).max()
     assert b.t == pytest.approx(a.t / 4.0, rel=1e-14)
+
+
+# ------------------------------------------------------------------ staged loading (Sec. 5.1)
+def test_strain_rate_loading_on_a_dislocation_free_state():
+    """Without dislocations (U13 uniform) nothing moves, tau13 is the macroscopic stress, and
+    the strain-rate mode gives sigma_bar13 = 2 mu (eps0 + rate t) - mu (nh/nz) <U13> at the
+    start of every step."""
+    n = 16
+    u0 = np.full((n, n), 0.3)
+    p = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=3, eps_bar13_0=1e-3, eps_bar13_rate=2e-4,
+                      cfl=0.4, dt_max=0.5)
+    st, rc = oracle.run(p, u0, 7)
+    mu = 1.0 / 2.6
+    assert rc == 0 and st.t == pytest.approx(3.5, rel=1e-15)
+    np.testing.assert_array_equal(st.up13, u0)
+    assert st.sigma_bar13 == pytest.approx(2 * mu * (1e-3 + 2e-4 * 3.5) - mu * (4 / 16) * 0.3, rel=1e-14)
+    np.testing.assert_allclose(st.tau13, 2 * mu * (1e-3 + 2e-4 * 3.0) - mu * (4 / 16) * 0.3, rtol=1e-13)
+
+
+def test_zero_mean_stress_stage_then_strain_rate_stage():
+    """Two stages carried by the state: the zero-mean-stress stage keeps sigma_bar13 = 0 with
+    eps_bar13 = (nh/nz) <U13> / 2, and the strain-rate stage that follows starts from the
+    stage-one time (eps = eps0 + rate t, t carried on)."""
+    n = 32
+    up0 = inputs.random_up(n, seed=9, ell=4.0)
+    p1 = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=2, cfl=0.4)
+    st1, _ = oracle.run(p1, up0, 15)
+    assert st1.sigma_bar13 == 0.0
+    assert st1.eps_bar13 == pytest.approx(0.5 * (4 / 32) * st1.mean_up13, rel=1e-15)
+    assert abs(st1.tau13.mean()) < 1e-14
+    p2 = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=3, eps_bar13_rate=1e-3, cfl=0.4)
+    st2, _ = oracle.run(p2, None, 10, state=st1)
+    assert st2.step == 25 and st2.t > st1.t
+    assert st2.eps_bar13 == pytest.approx(1e-3 * st2.t, rel=1e-14)
