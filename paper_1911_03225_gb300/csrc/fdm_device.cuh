@@ -242,6 +242,11 @@ __device__ __forceinline__ double minmod3(double a, double b, double c) {
     return ok ? r : 0.0;
 }
 
+// |a| < |b| (on bit patterns for FP64)
+__device__ __forceinline__ bool tmag_less(float a, float b) { return fabsf(a) < fabsf(b); }
+__device__ __forceinline__ bool tmag_less(df a, df b) { return tabs(a) < tabs(b); }
+__device__ __forceinline__ bool tmag_less(double a, double b) { return (ubits(a) & kMagBits) < (ubits(b) & kMagBits); }
+
 // one-sided speeds: ap = max(ap, h), am = min(am, h) for ap >= 0 >= am, NaN ignored
 template <typename T> __device__ __forceinline__ void speed_range(T h, T& ap, T& am) {
     ap = tmax(ap, h);
@@ -298,19 +303,24 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
     // one-sided derivatives at the node (times h)
     T px[2] = {xs[0].D - thalf(xs[0].S), xs[1].D + thalf(xs[1].S)};
     T qy[2] = {ys[0].D - thalf(ys[0].S), ys[1].D + thalf(ys[1].S)};
-    // Step 2: one-sided speeds over the four pairs (dH/dp = v0 p / |(p,q)|, 0 at the origin)
+    // Step 2: one-sided speeds over the four pairs (G4; dH/dp = v0 p / |(p,q)|, 0 at the
+    // origin).  For a fixed p the magnitude |p| / |(p,q)| falls as |q| grows and keeps its
+    // sign, so max(0, .) and min(0, .) of dH/dp over the pairs are attained with the q of
+    // least magnitude, and those of dH/dq with the p of least magnitude: the pairs
+    // (p0, qm), (p1, qm), (pm, qm'), where qm' is the other q, cover all four.
+    const bool tq = tmag_less(qy[1], qy[0]), tp = tmag_less(px[1], px[0]);
+    const T qm = tq ? qy[1] : qy[0], qo = tq ? qy[0] : qy[1];
+    const T pm = tp ? px[1] : px[0];
+    auto inv_norm = [&](T p, T q) -> T {   // v0 / |(p, q)|, 0 at the origin
+        const T r2 = p * p + q * q;
+        return tguard(r2) ? v0 * trsqrt(r2) : T(0);
+    };
+    const T r0 = inv_norm(px[0], qm), r1 = inv_norm(px[1], qm), rc = inv_norm(pm, qo);
     T ap = T(0), am = T(0), bp = T(0), bm = T(0);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            T p = px[s], q = qy[t];
-            T r2 = p * p + q * q;
-            T Hp = T(0), Hq = T(0);
-            if (tguard(r2)) { T vr = v0 * trsqrt(r2); Hp = vr * p; Hq = vr * q; }
-            speed_range(Hp, ap, am);
-            speed_range(Hq, bp, bm);
-        }
+    speed_range(r0 * px[0], ap, am);
+    speed_range(r1 * px[1], ap, am);
+    speed_range((tp ? r1 : r0) * qm, bp, bm);   // the pair (pm, qm) is (p0, qm) or (p1, qm)
+    speed_range(rc * qo, bp, bm);
     // Step 4 weights (G1, G5): w(s,t) = nx[s] ny[t] / (dxw dyw), one reciprocal
     // FP64: w(s,t) = nx[s] ny[t] / (dxw dyw) with one reciprocal.  FP32 and double words
     // normalise each direction on its own (wx = nx / dxw in [0, 1]), because the product of
