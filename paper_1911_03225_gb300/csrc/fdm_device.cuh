@@ -19,43 +19,52 @@ template <typename T> __host__ __device__ __forceinline__ cpx<T> operator-(cpx<T
 template <typename T> __host__ __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename T> __host__ __device__ __forceinline__ cpx<T> conj(cpx<T> a) { return mk(a.x, -a.y); }
 template <typename T> __host__ __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return mk(a.x * s, a.y * s); }
-// multiply by s*i, s = +-1
-template <typename T> __host__ __device__ __forceinline__ cpx<T> mul_si(cpx<T> a, int s) { return s > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x); }
-
-// twiddle w^m with w = exp(sign 2 pi i / len); table holds exp(-2 pi i m / len)
-template <typename T> __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* __restrict__ tw, int m, int sign) {
-    cpx<T> w = tw[m];
-    return sign < 0 ? w : conj(w);
+// multiply by S i, S = +-1 (a compile-time direction: no arithmetic)
+template <int S, typename T> __host__ __device__ __forceinline__ cpx<T> mul_si(cpx<T> a) {
+    return S > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 
-// In-register DFT of R = 2, 4 or 8 points, sign -1 forward / +1 inverse, natural order.
+// twiddle w^m with w = exp(S 2 pi i / len); table holds exp(-2 pi i m / len)
+template <int S, typename T> __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* __restrict__ tw, int m) {
+    const cpx<T> w = tw[m];
+    return S < 0 ? w : conj(w);
+}
+
+// In-register DFT of R = 2, 4 or 8 points, S = -1 forward / +1 inverse, natural order.  The
+// direction is a template parameter so that the rotations by W8 are additions, sign flips
+// and one multiply by 1/sqrt(2), never multiplications by +-1.
 template <typename T, int R> struct Dft;
 template <typename T> struct Dft<T, 2> {
-    static __device__ __forceinline__ void run(cpx<T>* v, int) {
+    template <int S> static __device__ __forceinline__ void run(cpx<T>* v) {
         cpx<T> a = v[0], b = v[1];
         v[0] = a + b; v[1] = a - b;
     }
 };
 template <typename T> struct Dft<T, 4> {
-    static __device__ __forceinline__ void run(cpx<T>* v, int sign) {
-        cpx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_si(v[1] - v[3], sign);
+    template <int S> static __device__ __forceinline__ void run(cpx<T>* v) {
+        cpx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_si<S>(v[1] - v[3]);
         v[0] = t0 + t2; v[1] = t1 + t3; v[2] = t0 - t2; v[3] = t1 - t3;
     }
 };
 template <typename T> struct Dft<T, 8> {
     // radix-2 decimation in frequency, three stages, bit-reversed result reordered
-    static __device__ __forceinline__ void run(cpx<T>* a, int s) {
+    template <int S> static __device__ __forceinline__ void run(cpx<T>* a) {
         const T r = T(0.70710678118654752440084436210485);
         cpx<T> b0 = a[0] + a[4], b4 = a[0] - a[4];
         cpx<T> b1 = a[1] + a[5], b5 = a[1] - a[5];
         cpx<T> b2 = a[2] + a[6], b6 = a[2] - a[6];
         cpx<T> b3 = a[3] + a[7], b7 = a[3] - a[7];
-        // b5 *= W8, b6 *= W8^2 = s i, b7 *= W8^3   (W8 = exp(s 2 pi i / 8))
-        b5 = mk(r * (b5.x - T(s) * b5.y), r * (b5.y + T(s) * b5.x));
-        b6 = mul_si(b6, s);
-        b7 = mk(r * (-b7.x - T(s) * b7.y), r * (-b7.y + T(s) * b7.x));
-        cpx<T> c0 = b0 + b2, c2 = b0 - b2, c1 = b1 + b3, c3 = mul_si(b1 - b3, s);
-        cpx<T> c4 = b4 + b6, c6 = b4 - b6, c5 = b5 + b7, c7 = mul_si(b5 - b7, s);
+        // b5 *= W8, b6 *= W8^2 = S i, b7 *= W8^3   (W8 = exp(S 2 pi i / 8) = (1 + S i) / sqrt 2)
+        if (S < 0) {
+            b5 = mk(r * (b5.x + b5.y), r * (b5.y - b5.x));
+            b7 = mk(r * (b7.y - b7.x), -(r * (b7.y + b7.x)));
+        } else {
+            b5 = mk(r * (b5.x - b5.y), r * (b5.y + b5.x));
+            b7 = mk(-(r * (b7.x + b7.y)), r * (b7.x - b7.y));
+        }
+        b6 = mul_si<S>(b6);
+        cpx<T> c0 = b0 + b2, c2 = b0 - b2, c1 = b1 + b3, c3 = mul_si<S>(b1 - b3);
+        cpx<T> c4 = b4 + b6, c6 = b4 - b6, c5 = b5 + b7, c7 = mul_si<S>(b5 - b7);
         a[0] = c0 + c1; a[4] = c0 - c1;
         a[2] = c2 + c3; a[6] = c2 - c3;
         a[1] = c4 + c5; a[5] = c4 - c5;
@@ -93,8 +102,8 @@ __host__ __device__ __forceinline__ int pass_table_len(int L) {
 // (two radix-4 or four radix-2 butterflies in the last pass).  Element i of sequence s at
 // a[s * ld + swz(i)].  pt: the pass twiddle tables (pass_table_len(L) entries).  Must be
 // called by all threads of the block.
-template <typename T, int R, int PER>
-__device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int ld, int Ns, int sign,
+template <typename T, int R, int PER, int S>
+__device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int ld, int Ns,
                                                  const cpx<T>* __restrict__ ptw) {
     const int q = L / R;
     const int lq = 31 - __clz(q);
@@ -113,9 +122,9 @@ __device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int
         for (int r = 0; r < R; ++r) v[u][r] = a[base[u] + swz(j + r * q)];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], twiddle(ptw, (r - 1) * Ns + k, sign));
+            for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], twiddle<S>(ptw, (r - 1) * Ns + k));
         }
-        Dft<T, R>::run(v[u], sign);
+        Dft<T, R>::template run<S>(v[u]);
     }
     __syncthreads();
 #pragma unroll
@@ -127,16 +136,16 @@ __device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int
     __syncthreads();
 }
 
-template <typename T>
-__device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, int sign, const cpx<T>* __restrict__ pt) {
+template <int S, typename T>
+__device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, const cpx<T>* __restrict__ pt) {
     int Ns = 1;
     while (Ns * 8 <= L) {
-        stockham_pass_ip<T, 8, 1>(a, L, nseq, ld, Ns, sign, pt);
+        stockham_pass_ip<T, 8, 1, S>(a, L, nseq, ld, Ns, pt);
         pt += 7 * Ns;
         Ns *= 8;
     }
-    if (Ns * 4 == L) stockham_pass_ip<T, 4, 2>(a, L, nseq, ld, Ns, sign, pt);
-    else if (Ns * 2 == L) stockham_pass_ip<T, 2, 4>(a, L, nseq, ld, Ns, sign, pt);
+    if (Ns * 4 == L) stockham_pass_ip<T, 4, 2, S>(a, L, nseq, ld, Ns, pt);
+    else if (Ns * 2 == L) stockham_pass_ip<T, 2, 4, S>(a, L, nseq, ld, Ns, pt);
 }
 
 // ---------------------------------------------------------------------------------

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
             if (lane == 0) row_partials[y0 + r] = rs;
         }
     }
-    smem_fft_ip(A, L, R, ld, -1, pt1);
+    smem_fft_ip<-1>(A, L, R, ld, pt1);
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
         int r = e / half, k = e - r * half;  // half = L/2 + 1 is not a power of two
@@ -190,9 +190,9 @@ template <typename T>
 __device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* __restrict__ Kh, int kxi,
                                                  int ky, int n1, int n2) {
     // kxi in [0, n1/2]; ky in [0, n2)
-    if (a.mode == COL_K) {
+    if (a.mode == COL_K) {   // the table carries the 1/(n1 n2) normalisation
         int kyf = ky <= n2 / 2 ? ky : n2 - ky;
-        return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf] * a.scl, T(0));
+        return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf], T(0));
     }
     if (a.mode == COL_DERIV1) {
         if (2 * kxi == n1) return mk(T(0), T(0));
@@ -202,6 +202,16 @@ __device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* _
     if (2 * ky == n2) return mk(T(0), T(0));
     int kys = ky <= n2 / 2 ? ky : ky - n2;
     return mk(T(0), -(T(kys) * a.xi2_unit) * a.scl);
+}
+
+// the symbol applied to one coefficient: real (K) or imaginary (derivatives), so two
+// multiplications rather than a general complex product
+template <typename T>
+__device__ __forceinline__ cpx<T> col_apply(const ColArgs<T>& a, const T* __restrict__ Kh, int kxi, int ky,
+                                            int n1, int n2, cpx<T> z) {
+    const cpx<T> m = col_multiplier<T>(a, Kh, kxi, ky, n1, n2);
+    if (a.mode == COL_K) return mk(m.x * z.x, m.x * z.y);
+    return mk(-(m.y * z.y), m.y * z.x);
 }
 
 template <typename T>
@@ -271,7 +281,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
         }
     }
     __syncthreads();
-    if (a.mode != COL_INV) smem_fft_ip(A, n2, C, ld, -1, pt2);
+    if (a.mode != COL_INV) smem_fft_ip<-1>(A, n2, C, ld, pt2);
     if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N) {
         // in place: a thread owns the pair (ky, n2 - ky) of one column
         const int hp = n2 / 2 + 1;
@@ -283,8 +293,8 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
             const cpx<T> z = col[swz(ky)], zr = col[swz(kyr)];
             cpx<T> o, orr;
             if (kx > 0) {
-                o = cmul(col_multiplier<T>(a, Kh, kx, ky, n1, n2), z);
-                orr = cmul(col_multiplier<T>(a, Kh, kx, kyr, n1, n2), zr);
+                o = col_apply<T>(a, Kh, kx, ky, n1, n2, z);
+                orr = col_apply<T>(a, Kh, kx, kyr, n1, n2, zr);
             } else {
                 // packed column: z = C0 + i CN (C0, CN transforms of the real columns kx = 0
                 // and kx = n1/2); multiply each by its own symbol and repack:
@@ -302,7 +312,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
         }
         __syncthreads();
     }
-    if (a.mode != COL_FWD) smem_fft_ip(A, n2, C, ld, +1, pt2);
+    if (a.mode != COL_FWD) smem_fft_ip<+1>(A, n2, C, ld, pt2);
     cpx<T>* dst = out + (size_t)kx0 * n2;
     for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = A[(e >> ln2) * ld + swz(e & (n2 - 1))];
 }
@@ -412,7 +422,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
         c2r_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
     }
     __syncthreads();
-    smem_fft_ip(A, L, R, ld, +1, pt1);
+    smem_fft_ip<+1>(A, L, R, ld, pt1);
     const cpx<T>* z = A;
     T vmax = T(0);
     bool bad = false;
@@ -618,8 +628,9 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
 }
 
 // ------------------------------------------------------------------ set-up / readout helpers
-// Layer Green kernel (Sec. 3.1.2 + layer average, Sec. 3.2.1):
-// Kh[kx][ky] = (1/(nz nh)) sum_k3 m(xi) |chi-hat(k3)|^2, m = -mu (n2^2 + 2 n1^2 n3^2/(1-nu)).
+// Layer Green kernel (Sec. 3.1.2 + layer average, Sec. 3.2.1), with the inverse transform's
+// normalisation folded in: Kh[kx][ky] = (1/(nz nh n1 n2)) sum_k3 m(xi) |chi-hat(k3)|^2,
+// m = -mu (n2^2 + 2 n1^2 n3^2/(1-nu)).
 // w3[k3] = |chi-hat(k3)|^2 for k3 in [0, nz/2] (host table), even in k3.
 __global__ void kernel_table_kernel(double* __restrict__ Kh, int n1, int n2, int nz, int nh,
                                     double mu, double nu, const double* __restrict__ w3) {
@@ -638,7 +649,7 @@ __global__ void kernel_table_kernel(double* __restrict__ Kh, int n1, int n2, int
             double mult = (k3 == 0 || 2 * k3 == nz) ? 1.0 : 2.0;
             acc += mult * m * w3[k3];
         }
-        Kh[i] = acc / ((double)nz * (double)nh);
+        Kh[i] = acc / ((double)nz * (double)nh) / ((double)n1 * (double)n2);
     }
 }
 
