@@ -194,6 +194,15 @@ fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
 
+/* sigma13 of the current state on planes of the 3-D periodic cell (Sec. 3.1.2 static problem
+ * on the cell of nz voxels; the layer occupies planes 0 .. nh-1, Sec. 3.2.1): planes[k] in
+ * [0, nz), out [nplanes][n2][n1] (host, float64).  The layer average of these planes is
+ * tau13.  For each plane the 3-D transform's sum over xi3 is folded into a 2-D symbol,
+ * (1/nz) sum_k3 m(xi) D(k3) cos(2 pi k3 (x3 - (nh - 1)/2) / nz) with D(k3) the layer's
+ * transform sin(pi k3 nh / nz) / sin(pi k3 / nz), built on the GPU in O(n1 n2 nz), then
+ * applied by the static-solve kernels.  Leaves the state and its scalars unchanged. */
+fdm_status fdm_read_stress13_planes(fdm_handle *h, int32_t nplanes, const int32_t *planes, double *out);
+
 /* Switches the macroscopic loading between stages of a run (Sec. 5.1: equilibration at
  * zero mean stress, then a strain rate): the next step uses the new mode and values; step
  * and time carry on.  Same validation as fdm_create; waits for the stream. */

@@ -35,6 +35,8 @@ def lib():
         _lib.oracle_sum.restype = C.c_double
         _lib.oracle_alpha_sums.argtypes = [C.c_int, C.c_int, C.c_double, d, d]
         _lib.oracle_run.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d]
+        _lib.oracle_stress13_planes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, d,
+                                                C.c_double, C.c_int, C.POINTER(C.c_int), d]
         _lib.oracle_run.restype = C.c_int
     return _lib
 
@@ -194,6 +196,18 @@ class State:
     sigma_bar13: float = 0.0
     tau13: np.ndarray = field(default=None, repr=False)
     v0: np.ndarray = field(default=None, repr=False)
+
+
+def stress13_planes(up13, nz, nh, mu, nu, sigma_bar13, planes):
+    """sigma13 on the planes x3 in ``planes`` of the 3-D cell of nz voxels whose planes
+    0 .. nh-1 carry U13 (Sec. 3.1.2, Sec. 3.2.1).  Returns [len(planes)][n2][n1]."""
+    u = _f64(up13)
+    n2, n1 = u.shape
+    pl = np.ascontiguousarray(planes, dtype=np.int32)
+    out = np.zeros((len(pl), n2, n1))
+    lib().oracle_stress13_planes(n1, n2, int(nz), int(nh), float(mu), float(nu), _p(u), float(sigma_bar13),
+                                 len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)), _p(out))
+    return out
 
 
 def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None):

@@ -167,6 +167,64 @@ void oracle_static_tau(int n1, int n2, const double *up13, const double *K, doub
 }
 
 /*
+ * sigma13 on chosen planes of the 3-D periodic cell (Sec. 3.1.2 static problem on the cell
+ * of nz voxels, Sec. 3.2.1 layer): U^p = U13(x1, x2) chi(x3) e1 (x) e3, chi = 1 on the planes
+ * x3 = 0 .. nh-1.  The 3-D transform of the layered field is U13-hat(k1, k2) chi-hat(k3),
+ * chi-hat(k3) = sum_{j < nh} exp(-2 pi i k3 j / nz); sigma13-hat = m(xi) U^p-hat for xi != 0
+ * and the macroscopic stress at xi = 0.  The inverse 3-D transform is evaluated at each
+ * requested plane x3: the sum over k3 first, then the inverse 2-D transform.
+ * out: [nplanes][n2][n1].
+ */
+void oracle_stress13_planes(int n1, int n2, int nz, int nh, double mu, double nu, const double *up13,
+                            double sigma_bar13, int nplanes, const int *planes, double *out)
+{
+    size_t n = (size_t)n1 * n2;
+    double *ur = malloc(sizeof(double) * n), *ui = calloc(n, sizeof(double));
+    double *re = malloc(sizeof(double) * n), *im = malloc(sizeof(double) * n);
+    double *cr = malloc(sizeof(double) * nz), *ci = malloc(sizeof(double) * nz);
+    memcpy(ur, up13, sizeof(double) * n);
+    oracle_fft2d(n1, n2, ur, ui, -1);
+    for (int k3 = 0; k3 < nz; k3++) {      /* chi-hat(k3), summed term by term */
+        cr[k3] = 0.0;
+        ci[k3] = 0.0;
+        for (int j = 0; j < nh; j++) {
+            double a = -2.0 * OR_PI * (double)k3 * (double)j / (double)nz;
+            cr[k3] += cos(a);
+            ci[k3] += sin(a);
+        }
+    }
+    for (int ip = 0; ip < nplanes; ip++) {
+        int x3 = planes[ip];
+        for (int k2 = 0; k2 < n2; k2++) {
+            for (int k1 = 0; k1 < n1; k1++) {
+                double x1 = (double)signed_index(k1, n1) / (double)n1;
+                double x2 = (double)signed_index(k2, n2) / (double)n2;
+                double sr = 0.0, si = 0.0;   /* sum over k3 of m chi-hat exp(2 pi i k3 x3 / nz) */
+                for (int k3 = 0; k3 < nz; k3++) {
+                    double z3 = (double)signed_index(k3, nz) / (double)nz;
+                    double r2 = x1 * x1 + x2 * x2 + z3 * z3;
+                    if (r2 == 0.0) continue;
+                    double r = sqrt(r2);
+                    double m = oracle_layer_symbol(x1 / r, x2 / r, z3 / r, mu, nu);
+                    double a = 2.0 * OR_PI * (double)k3 * (double)x3 / (double)nz;
+                    double er = cos(a), ei = sin(a);
+                    sr += m * (cr[k3] * er - ci[k3] * ei);
+                    si += m * (cr[k3] * ei + ci[k3] * er);
+                }
+                size_t i = (size_t)k2 * n1 + k1;
+                re[i] = (sr * ur[i] - si * ui[i]) / (double)nz;
+                im[i] = (sr * ui[i] + si * ur[i]) / (double)nz;
+            }
+        }
+        re[0] = sigma_bar13 * (double)n;   /* xi = 0: the macroscopic stress */
+        im[0] = 0.0;
+        oracle_fft2d(n1, n2, re, im, +1);
+        for (size_t i = 0; i < n; i++) out[(size_t)ip * n + i] = re[i] / (double)n;
+    }
+    free(ur); free(ui); free(re); free(im); free(cr); free(ci);
+}
+
+/*
  * Curl inverse (Sec. 3.1.2, U^p-hat = i (alpha-hat x xi)/|xi|^2; Sec. 2.2 Poisson problem):
  * for the layer ansatz alpha = a11 e1(x)e1 + a12 e1(x)e2 (Sec. 3.2.1) the 13 component is
  *   U13-hat = i (a11-hat xi2 - a12-hat xi1) / |xi|^2,   U13-hat(0) = mean_up13 * N.

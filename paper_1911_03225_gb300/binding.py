@@ -44,7 +44,8 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget", "fdm_batch_enqueue_steps",
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
-           "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading"]
+           "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
+           "fdm_read_stress13_planes"]
 
 
 class CParams(C.Structure):
@@ -189,6 +190,8 @@ def load():
     lib.fdm_set_mobility_field.restype = C.c_int
     lib.fdm_set_loading.argtypes = [H, C.c_int32, C.c_double, C.c_double, C.c_double]
     lib.fdm_set_loading.restype = C.c_int
+    lib.fdm_read_stress13_planes.argtypes = [H, C.c_int32, C.POINTER(C.c_int32), d]
+    lib.fdm_read_stress13_planes.restype = C.c_int
     lib.fdm_launch_candidates.argtypes = [C.POINTER(CParams), C.POINTER(CLaunchConfig), C.c_int32]
     lib.fdm_launch_candidates.restype = C.c_int32
     for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
@@ -297,6 +300,15 @@ class FDM:
     # -- compute
     def static_solve(self):
         _check(self.lib.fdm_static_solve(self.h), "fdm_static_solve")
+
+    def read_stress13_planes(self, planes) -> np.ndarray:
+        """sigma13 of the current state on the given planes x3 of the 3-D cell (the layer is
+        planes 0 .. nh-1); returns [len(planes)][n2][n1]."""
+        pl = np.ascontiguousarray(planes, dtype=np.int32)
+        out = np.empty((len(pl),) + self.shape, dtype=np.float64)
+        _check(self.lib.fdm_read_stress13_planes(self.h, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 _dptr(out)), "fdm_read_stress13_planes")
+        return out
 
     def set_loading(self, mode: int, sigma_bar13: float = 0.0, eps_bar13_0: float = 0.0,
                     eps_bar13_rate: float = 0.0):

@@ -79,6 +79,7 @@ template <typename T> cudaError_t configure_kernels();
 template <typename T> void launch_step(const Dev& d, cudaStream_t s);
 template <typename T> void launch_phase(const Dev& d, int phase, cudaStream_t s);
 template <typename T> void launch_static(const Dev& d, cudaStream_t s);
+template <typename T> void launch_static_to(const Dev& d, T* dst, cudaStream_t s);
 template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);
 template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,

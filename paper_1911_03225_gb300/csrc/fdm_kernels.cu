@@ -972,6 +972,16 @@ void launch_step(const Dev& d, cudaStream_t s) {
     for (int ph = 0; ph < kKernelsPerStep; ++ph) launch_phase<T>(d, ph, s);
 }
 
+// static solve of the current state with the group's table d.Kh, written without the
+// celerity reduction to dst (single instance): e.g. sigma13 on a plane of the 3-D cell when
+// d.Kh holds that plane's table
+template <typename T>
+void launch_static_to(const Dev& d, T* dst, cudaStream_t s) {
+    launch_phase<T>(d, 0, s);
+    launch_phase<T>(d, 1, s);
+    launch_row_inverse<T>(d, (const cpx<T>*)d.spec, dst, ROW_PLAIN, 0.0, 1, s);
+}
+
 // static solve only: tau for the current state of every instance
 template <typename T>
 void launch_static(const Dev& d, cudaStream_t s) {
@@ -1050,6 +1060,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_step<T>(const Dev&, cudaStream_t);                                                 \
     template void launch_phase<T>(const Dev&, int, cudaStream_t);                                           \
     template void launch_static<T>(const Dev&, cudaStream_t);                                               \
+    template void launch_static_to<T>(const Dev&, T*, cudaStream_t);                                        \
     template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \

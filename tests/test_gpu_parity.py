@@ -138,6 +138,45 @@ def test_alpha_and_velocity_readout(precision, tol):
     assert rel(f["v1"], v0 * a12 / m) < 10 * tol and rel(f["v2"], -v0 * a11 / m) < 10 * tol
 
 
+@pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.DF64, TOL64), (B.MIXED, TOL_MIXED)])
+def test_stress13_planes_of_the_3d_cell_match_oracle(precision, tol):
+    """sigma13 through the 3-D cell (Sec. 3.1.2 on the nz-voxel cell; the layer is planes
+    0 .. nh-1): planes inside, at the edge of and far from the layer against the oracle's
+    term-by-term 3-D transform; the layer average of the planes is the step's tau13."""
+    n1, n2, nz, nh = 64, 32, 32, 4
+    up0 = inputs.random_up(64, seed=14, ell=4.0)[:n2, :n1].copy()
+    p = Params(n1=n1, n2=n2, nz=nz, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS,
+               sigma_bar13=0.02, precision=precision)
+    planes = [0, 1, 2, 3, 4, 9, 16, 31]
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve()
+        tau = sim.read_fields("tau13")["tau13"]
+        got = sim.read_stress13_planes(planes)
+        assert sim.info().step == 0
+    ref = oracle.stress13_planes(up0, nz, nh, 1 / 2.6, 0.3, 0.02, planes)
+    for g, r in zip(got, ref):
+        assert rel(g, r) < tol
+    assert rel(got[:nh].mean(axis=0), tau) < (1e-13 if precision != B.MIXED else 1e-6)
+
+
+def test_stress13_planes_at_scale_reproduce_the_layer_reduction():
+    """The K(xi1, xi2) reduction validated at scale: on a 1024^2 x 1024 cell the average of
+    the four layer planes equals tau13 of the reduced static solve."""
+    n, nz, nh = 1024, 1024, 4
+    up0 = inputs.random_up(n, seed=15, ell=16.0)
+    p = Params(n1=n, n2=n, nz=nz, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.01)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve()
+        tau = sim.read_fields("tau13")["tau13"]
+        planes = sim.read_stress13_planes([0, 1, 2, 3, 512])
+    assert rel(planes[:4].mean(axis=0), tau) < 1e-12
+    # far from the layer the stress is the macroscopic stress plus a decayed image field
+    assert abs(planes[4].mean() - 0.01) < 1e-12
+    assert np.abs(planes[4] - 0.01).max() < np.abs(tau - 0.01).max()
+
+
 # ------------------------------------------------------------------ time stepping
 @pytest.mark.parametrize("precision", [B.FP64, B.DF64])
 def test_config0_lines_annihilation(precision):

@@ -54,9 +54,14 @@ def _isotropic_C(lam, mu):
 
 
 def _tensor_green_layer_tau(phi, nz, nh, lam, mu, sigma_bar13):
-    """Layer-averaged sigma13 from the general Green-operator formula of Sec. 3.1.2,
-    sigma-hat = (C0:Gamma0-hat - I):C0:U^p-hat, Gamma0-hat = [xi (x) (xi.C0.xi)^-1 (x) xi]^(s),
-    evaluated with full 3x3x3x3 tensors on a 3-D periodic cell."""
+    """Layer-averaged sigma13 from the general Green-operator formula (see below)."""
+    return _tensor_green_sigma13(phi, nz, nh, lam, mu, sigma_bar13)[:nh].mean(axis=0)
+
+
+def _tensor_green_sigma13(phi, nz, nh, lam, mu, sigma_bar13):
+    """sigma13 on every plane of the 3-D cell from the general Green-operator formula of
+    Sec. 3.1.2, sigma-hat = (C0:Gamma0-hat - I):C0:U^p-hat, Gamma0-hat =
+    [xi (x) (xi.C0.xi)^-1 (x) xi]^(s), evaluated with full 3x3x3x3 tensors."""
     n2, n1 = phi.shape
     C0 = _isotropic_C(lam, mu)
     I4 = 0.5 * (np.einsum("ik,jl->ijkl", np.eye(3), np.eye(3)) + np.einsum("il,jk->ijkl", np.eye(3), np.eye(3)))
@@ -81,8 +86,7 @@ def _tensor_green_layer_tau(phi, nz, nh, lam, mu, sigma_bar13):
         s = np.einsum("ijkl,klpq,pq->ij", op, C0, Up)
         s13[a, b, c] = s[0, 2]
     s13[0, 0, 0] = sigma_bar13 * U.size
-    sig = np.real(np.fft.ifftn(s13))
-    return sig[:nh].mean(axis=0)
+    return np.real(np.fft.ifftn(s13))
 
 
 def test_static_layer_matches_tensor_green_operator():
@@ -95,6 +99,34 @@ def test_static_layer_matches_tensor_green_operator():
     tau = oracle.static_tau(phi, K, 0.123)
     ref = _tensor_green_layer_tau(phi, nz, nh, lam, mu, 0.123)
     np.testing.assert_allclose(tau, ref, atol=1e-13, rtol=0)
+
+
+def test_stress13_planes_match_tensor_green_operator():
+    """sigma13 through the whole 3-D cell (inside and outside the layer) against the general
+    tensor formula on an 8 x 8 x 8 cell, and its average over the layer planes equals the
+    layer-reduced tau13 (the reduction K(xi1, xi2) of Sec. 3.2.1)."""
+    n, nz, nh = 8, 8, 3
+    E, nu = 1.0, 0.3
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    phi = np.random.default_rng(4).standard_normal((n, n))
+    ref = _tensor_green_sigma13(phi, nz, nh, lam, mu, 0.07)
+    got = oracle.stress13_planes(phi, nz, nh, mu, nu, 0.07, list(range(nz)))
+    np.testing.assert_allclose(got, ref, atol=1e-13, rtol=0)
+    K = oracle.kernel_table(n, n, nz, nh, mu, nu)
+    np.testing.assert_allclose(got[:nh].mean(axis=0), oracle.static_tau(phi, K, 0.07), atol=1e-13, rtol=0)
+
+
+def test_stress13_planes_of_a_full_layer_are_the_plane_problem():
+    """nh = nz: the plastic distortion fills the cell, sigma13 no longer varies in x3 and every
+    plane carries the layer result."""
+    n = 16
+    mu, nu = 1 / 2.6, 0.3
+    phi = np.random.default_rng(5).standard_normal((n, n))
+    got = oracle.stress13_planes(phi, 8, 8, mu, nu, 0.0, [0, 3, 7])
+    tau = oracle.static_tau(phi, oracle.kernel_table(n, n, 8, 8, mu, nu), 0.0)
+    for g in got:
+        np.testing.assert_allclose(g, tau, atol=1e-12, rtol=0)
 
 
 def _spectral_derivative_matrix(n):
