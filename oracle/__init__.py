@@ -37,6 +37,10 @@ def lib():
         _lib.oracle_run.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d]
         _lib.oracle_stress13_planes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, d,
                                                 C.c_double, C.c_int, C.POINTER(C.c_int), d]
+        _lib.oracle_stress_planes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, d,
+                                              C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), d]
+        _lib.oracle_stress_symbol.argtypes = [C.c_int] + [C.c_double] * 5
+        _lib.oracle_stress_symbol.restype = C.c_double
         _lib.oracle_run.restype = C.c_int
     return _lib
 
@@ -207,6 +211,29 @@ def stress13_planes(up13, nz, nh, mu, nu, sigma_bar13, planes):
     out = np.zeros((len(pl), n2, n1))
     lib().oracle_stress13_planes(n1, n2, int(nz), int(nh), float(mu), float(nu), _p(u), float(sigma_bar13),
                                  len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)), _p(out))
+    return out
+
+
+# Voigt order of the stress components (11, 22, 33, 23, 13, 12)
+STRESS_COMPONENTS = ("11", "22", "33", "23", "13", "12")
+
+
+def stress_symbol(comp, n1, n2, n3, mu, nu):
+    """sigma-hat_comp / U13-hat for the direction n (Sec. 3.1.2 Green operator)."""
+    return lib().oracle_stress_symbol(STRESS_COMPONENTS.index(comp), n1, n2, n3, mu, nu)
+
+
+def stress_planes(up13, nz, nh, mu, nu, sigma_bar13, comp, planes):
+    """Stress component ``comp`` ("11", "22", "33", "23", "13" or "12") on the planes x3 in
+    ``planes`` of the 3-D cell of nz voxels whose planes 0 .. nh-1 carry U13 (Sec. 3.1.2,
+    Sec. 3.2.1).  Returns [len(planes)][n2][n1]."""
+    u = _f64(up13)
+    n2, n1 = u.shape
+    pl = np.ascontiguousarray(planes, dtype=np.int32)
+    out = np.zeros((len(pl), n2, n1))
+    lib().oracle_stress_planes(n1, n2, int(nz), int(nh), float(mu), float(nu), _p(u), float(sigma_bar13),
+                               STRESS_COMPONENTS.index(comp), len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)),
+                               _p(out))
     return out
 
 

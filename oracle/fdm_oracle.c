@@ -225,6 +225,105 @@ void oracle_stress13_planes(int n1, int n2, int nz, int nh, double mu, double nu
 }
 
 /*
+ * Every component of the stress of the layered eigen-distortion (Sec. 3.1.2), for the
+ * Voigt index comp: 0 = 11, 1 = 22, 2 = 33, 3 = 23, 4 = 13, 5 = 12.  With n = xi/|xi| the
+ * Green operator Gamma0-hat = [xi (x) (xi.C0.xi)^-1 (x) xi]^(s) applied to the polarisation
+ * C0:U^p-hat = mu U (e1 (x) e3 + e3 (x) e1) gives the strain
+ *   eps-hat = sym(h (x) n),   h = (1/mu) (I - n (x) n / (2 (1 - nu))) (C0:U^p-hat) n,
+ * because (xi.C0.xi)^-1 = (I - c n (x) n)/(mu |xi|^2) with c = (lambda + mu)/(lambda + 2 mu)
+ * = 1/(2 (1 - nu)); the stress is sigma-hat = lambda tr(eps-hat) I + 2 mu (eps-hat - eps^p),
+ * eps^p = sym(U^p) (trace free).  Returns sigma-hat_comp / U-hat for U-hat = 1.
+ */
+static const int voigt_i[6] = {0, 1, 2, 1, 0, 0}, voigt_j[6] = {0, 1, 2, 2, 2, 1};
+
+double oracle_stress_symbol(int comp, double n1, double n2, double n3, double mu, double nu)
+{
+    const double n[3] = {n1, n2, n3};
+    const double lam = 2.0 * mu * nu / (1.0 - 2.0 * nu);
+    const double c = 1.0 / (2.0 * (1.0 - nu));
+    const double sn[3] = {n3, 0.0, n1};             /* (C0:U^p-hat) n / mu */
+    const double ns = n1 * sn[0] + n2 * sn[1] + n3 * sn[2];
+    double h[3];
+    for (int a = 0; a < 3; a++) h[a] = sn[a] - c * n[a] * ns;
+    const int i = voigt_i[comp], j = voigt_j[comp];
+    const double tr = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+    double s = mu * (h[i] * n[j] + h[j] * n[i]);
+    if (i == j) s += lam * tr;
+    if (comp == 4) s -= mu;                         /* 2 mu eps^p_13 = mu U */
+    return s;
+}
+
+/*
+ * Parity of the component's symbol in (n1, n2, n3): 1 where it is odd in that direction.
+ * (h is linear in n3 and n1 through C0:U^p, so 11, 22 and 33 carry n1 n3, 12 carries n2 n3,
+ * 23 carries n1 n2, and 13 is even in all three.)  Reading G8 extended: a symbol odd in a
+ * direction has no value at that axis's Nyquist index, so the term is dropped there.
+ */
+static const int stress_odd[6][3] = {{1, 0, 1}, {1, 0, 1}, {1, 0, 1}, {1, 1, 0}, {0, 0, 0}, {0, 1, 1}};
+
+/*
+ * One stress component on chosen planes of the 3-D periodic cell (Sec. 3.1.2 on the cell of
+ * nz voxels, Sec. 3.2.1 layer on planes 0 .. nh-1): the 3-D transform of U13(x1, x2) chi(x3)
+ * multiplied by the component's symbol term by term, then the inverse transform evaluated
+ * at each plane, the sum over k3 first.  The xi = 0 term is the macroscopic stress:
+ * sigma_bar13 for comp 4, zero otherwise (the loading only prescribes the 13 component and
+ * U^p has no other mean part).  out: [nplanes][n2][n1].
+ */
+void oracle_stress_planes(int n1, int n2, int nz, int nh, double mu, double nu, const double *up13,
+                          double sigma_bar13, int comp, int nplanes, const int *planes, double *out)
+{
+    size_t n = (size_t)n1 * n2;
+    const int *odd = stress_odd[comp];
+    double *ur = malloc(sizeof(double) * n), *ui = calloc(n, sizeof(double));
+    double *re = malloc(sizeof(double) * n), *im = malloc(sizeof(double) * n);
+    double *cr = malloc(sizeof(double) * nz), *ci = malloc(sizeof(double) * nz);
+    memcpy(ur, up13, sizeof(double) * n);
+    oracle_fft2d(n1, n2, ur, ui, -1);
+    for (int k3 = 0; k3 < nz; k3++) {      /* chi-hat(k3), summed term by term */
+        cr[k3] = 0.0;
+        ci[k3] = 0.0;
+        for (int j = 0; j < nh; j++) {
+            double a = -2.0 * OR_PI * (double)k3 * (double)j / (double)nz;
+            cr[k3] += cos(a);
+            ci[k3] += sin(a);
+        }
+    }
+    for (int ip = 0; ip < nplanes; ip++) {
+        int x3 = planes[ip];
+        for (int k2 = 0; k2 < n2; k2++) {
+            for (int k1 = 0; k1 < n1; k1++) {
+                size_t i = (size_t)k2 * n1 + k1;
+                re[i] = 0.0;
+                im[i] = 0.0;
+                if ((odd[0] && 2 * k1 == n1) || (odd[1] && 2 * k2 == n2)) continue;
+                double x1 = (double)signed_index(k1, n1) / (double)n1;
+                double x2 = (double)signed_index(k2, n2) / (double)n2;
+                double sr = 0.0, si = 0.0;
+                for (int k3 = 0; k3 < nz; k3++) {
+                    if (odd[2] && 2 * k3 == nz) continue;
+                    double z3 = (double)signed_index(k3, nz) / (double)nz;
+                    double r2 = x1 * x1 + x2 * x2 + z3 * z3;
+                    if (r2 == 0.0) continue;
+                    double r = sqrt(r2);
+                    double m = oracle_stress_symbol(comp, x1 / r, x2 / r, z3 / r, mu, nu);
+                    double a = 2.0 * OR_PI * (double)k3 * (double)x3 / (double)nz;
+                    double er = cos(a), ei = sin(a);
+                    sr += m * (cr[k3] * er - ci[k3] * ei);
+                    si += m * (cr[k3] * ei + ci[k3] * er);
+                }
+                re[i] = (sr * ur[i] - si * ui[i]) / (double)nz;
+                im[i] = (sr * ui[i] + si * ur[i]) / (double)nz;
+            }
+        }
+        re[0] = comp == 4 ? sigma_bar13 * (double)n : 0.0;
+        im[0] = 0.0;
+        oracle_fft2d(n1, n2, re, im, +1);
+        for (size_t i = 0; i < n; i++) out[(size_t)ip * n + i] = re[i] / (double)n;
+    }
+    free(ur); free(ui); free(re); free(im); free(cr); free(ci);
+}
+
+/*
  * Curl inverse (Sec. 3.1.2, U^p-hat = i (alpha-hat x xi)/|xi|^2; Sec. 2.2 Poisson problem):
  * for the layer ansatz alpha = a11 e1(x)e1 + a12 e1(x)e2 (Sec. 3.2.1) the 13 component is
  *   U13-hat = i (a11-hat xi2 - a12-hat xi1) / |xi|^2,   U13-hat(0) = mean_up13 * N.

@@ -129,6 +129,142 @@ def test_stress13_planes_of_a_full_layer_are_the_plane_problem():
         np.testing.assert_allclose(g, tau, atol=1e-12, rtol=0)
 
 
+def _tensor_green_stress(phi, nz, nh, lam, mu, sigma_bar13):
+    """All six stress components on every plane of the 3-D cell from the general tensor
+    formula of Sec. 3.1.2 (as _tensor_green_sigma13), keyed by Voigt name."""
+    n2, n1 = phi.shape
+    C0 = _isotropic_C(lam, mu)
+    I4 = 0.5 * (np.einsum("ik,jl->ijkl", np.eye(3), np.eye(3)) + np.einsum("il,jk->ijkl", np.eye(3), np.eye(3)))
+    U = np.zeros((nz, n2, n1))
+    U[:nh] = phi[None]
+    Uh = np.fft.fftn(U)
+    f3, f2, f1 = (np.fft.fftfreq(m) * m for m in (nz, n2, n1))
+    S = np.zeros((3, 3) + Uh.shape, dtype=complex)
+    for a, b, c in itertools.product(range(nz), range(n2), range(n1)):
+        xi = np.array([f1[c] / n1, f2[b] / n2, f3[a] / nz])
+        if not xi.any():
+            continue
+        Ai = np.linalg.inv(np.einsum("j,ijkl,l->ik", xi, C0, xi))
+        G = np.einsum("i,jk,l->ijkl", xi, Ai, xi)
+        G = 0.25 * (G + G.transpose(1, 0, 2, 3) + G.transpose(0, 1, 3, 2) + G.transpose(1, 0, 3, 2))
+        G = 0.5 * (G + G.transpose(2, 3, 0, 1))
+        Up = np.zeros((3, 3), dtype=complex)
+        Up[0, 2] = Uh[a, b, c]
+        op = np.einsum("ijmn,mnkl->ijkl", C0, G) - I4
+        S[:, :, a, b, c] = np.einsum("ijkl,klpq,pq->ij", op, C0, Up)
+    S[0, 2, 0, 0, 0] = S[2, 0, 0, 0, 0] = sigma_bar13 * U.size
+    real = np.real(np.fft.ifftn(S, axes=(2, 3, 4)))
+    idx = {"11": (0, 0), "22": (1, 1), "33": (2, 2), "23": (1, 2), "13": (0, 2), "12": (0, 1)}
+    return {k: real[i, j] for k, (i, j) in idx.items()}
+
+
+def _band_limited(phi):
+    """Drops the Nyquist row and column of the 2-D spectrum (no mode whose odd symbols the
+    Nyquist reading zeroes)."""
+    F = np.fft.fft2(phi)
+    n2, n1 = phi.shape
+    F[n2 // 2, :] = 0.0
+    F[:, n1 // 2] = 0.0
+    return np.real(np.fft.ifft2(F))
+
+
+def test_stress_planes_all_components_match_tensor_green_operator():
+    """Every stress component through the 3-D cell against the general tensor formula on an
+    8 x 4 x 8 cell.  The input has no Nyquist content in x1, x2 and the layer is 4 planes
+    deep (chi-hat vanishes at the x3 Nyquist index), so the reading for odd symbols at
+    Nyquist indices plays no part; the 13 component is the sigma13 routine's."""
+    n1, n2, nz, nh = 8, 4, 8, 4
+    E, nu = 1.0, 0.3
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    phi = _band_limited(np.random.default_rng(6).standard_normal((n2, n1)))
+    ref = _tensor_green_stress(phi, nz, nh, lam, mu, 0.05)
+    for comp in oracle.STRESS_COMPONENTS:
+        got = oracle.stress_planes(phi, nz, nh, mu, nu, 0.05, comp, list(range(nz)))
+        assert np.abs(ref[comp]).max() > 1e-2
+        np.testing.assert_allclose(got, ref[comp], atol=1e-13, rtol=0, err_msg=comp)
+    np.testing.assert_allclose(oracle.stress_planes(phi, nz, 3, mu, nu, 0.05, "13", [0, 2, 5]),
+                               oracle.stress13_planes(phi, nz, 3, mu, nu, 0.05, [0, 2, 5]), atol=1e-15, rtol=0)
+
+
+def test_stress_planes_are_in_equilibrium():
+    """div sigma = 0 (Sec. 3.1.2 equilibrium) for the assembled 3-D field: sum_j xi_j
+    sigma-hat_ij vanishes at every mode off the Nyquist indices."""
+    n1, n2, nz, nh = 8, 8, 8, 2
+    mu, nu = 0.4, 0.25
+    phi = _band_limited(np.random.default_rng(7).standard_normal((n2, n1)))
+    sig = {c: oracle.stress_planes(phi, nz, nh, mu, nu, 0.0, c, list(range(nz))) for c in oracle.STRESS_COMPONENTS}
+    T = np.empty((3, 3, nz, n2, n1))
+    for c, (i, j) in zip(oracle.STRESS_COMPONENTS, [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]):
+        T[i, j] = T[j, i] = sig[c]
+    Th = np.fft.fftn(T, axes=(2, 3, 4))
+    f3, f2, f1 = np.meshgrid(np.fft.fftfreq(nz), np.fft.fftfreq(n2), np.fft.fftfreq(n1), indexing="ij")
+    div = np.einsum("jabc,ijabc->iabc", np.stack([f1, f2, f3]), Th)
+    inner = (np.abs(f1) < 0.5) & (np.abs(f2) < 0.5) & (np.abs(f3) < 0.5)
+    assert np.abs(div[:, inner]).max() < 1e-12 * np.abs(Th).max()
+    assert np.abs(Th).max() > 1.0
+
+
+def test_stress_planes_reflection_symmetry_about_the_layer():
+    """Reflecting x3 about the layer's mid-plane maps the eigen-distortion U13 e1 (x) e3 to
+    minus itself, so the stress obeys R sigma(x) R = -sigma(R x): 13 and 23 are even about
+    the mid-plane, 11, 22, 33 and 12 odd.  Odd layer (mid-plane on a voxel plane), input
+    with Nyquist content."""
+    n, nz, nh = 8, 16, 3
+    mu, nu = 1 / 2.6, 0.3
+    phi = np.random.default_rng(8).standard_normal((n, n))
+    c = (nh - 1) // 2
+    for comp in oracle.STRESS_COMPONENTS:
+        sign = 1.0 if comp in ("13", "23") else -1.0
+        for d in (1, 2, 5):
+            up, dn = oracle.stress_planes(phi, nz, nh, mu, nu, 0.0, comp, [(c + d) % nz, (c - d) % nz])
+            np.testing.assert_allclose(up, sign * dn, atol=1e-13, rtol=0, err_msg=comp)
+        if sign < 0:
+            mid = oracle.stress_planes(phi, nz, nh, mu, nu, 0.0, comp, [c])[0]
+            np.testing.assert_allclose(mid, 0.0, atol=1e-13)
+
+
+def test_stress_planes_of_a_full_layer_are_antiplane_shear():
+    """nh = nz: U13 no longer varies along x3 and the problem is antiplane shear (displacement
+    u3 only): mu lap u3 = mu d1 U13, sigma13 = mu (d1 u3 - U13), sigma23 = mu d2 u3, the other
+    components vanish.  u3 from a spectral Poisson solve."""
+    n1, n2, nz = 16, 8, 4
+    mu, nu = 0.35, 0.2
+    phi = _band_limited(np.random.default_rng(9).standard_normal((n2, n1)))
+    k1 = 2 * np.pi * np.fft.fftfreq(n1)[None, :]
+    k2 = 2 * np.pi * np.fft.fftfreq(n2)[:, None]
+    lap = -(k1 ** 2 + k2 ** 2)
+    lap[0, 0] = 1.0
+    rhs = 1j * k1 * np.fft.fft2(phi)
+    u3h = rhs / lap
+    u3h[0, 0] = 0.0
+    d1 = np.real(np.fft.ifft2(1j * k1 * u3h))
+    d2 = np.real(np.fft.ifft2(1j * k2 * u3h))
+    # the mean of sigma13 is the macroscopic stress (the xi = 0 term)
+    want = {"13": mu * (d1 - (phi - phi.mean())) + 0.01, "23": mu * d2}
+    for comp in oracle.STRESS_COMPONENTS:
+        got = oracle.stress_planes(phi, nz, nz, mu, nu, 0.01, comp, [0, 1, 3])
+        for g in got:
+            np.testing.assert_allclose(g, want.get(comp, 0.0), atol=1e-13, rtol=0, err_msg=comp)
+
+
+def test_stress_planes_nyquist_reading():
+    """Reading G8 for the cell: a field made of the x1 Nyquist mode gives no stress in the
+    components whose symbol is odd in n1 (11, 22, 33, 23); 13 and 12 see it."""
+    n1, n2, nz, nh = 8, 8, 8, 3
+    x1 = np.arange(n1)[None, :]
+    x2 = np.arange(n2)[:, None]
+    phi = np.cos(np.pi * x1) * np.cos(2 * np.pi * x2 / n2)
+    for comp in oracle.STRESS_COMPONENTS:
+        got = oracle.stress_planes(phi, nz, nh, 0.4, 0.3, 0.0, comp, [0, 1, 4])
+        if comp in ("11", "22", "33", "23"):
+            assert np.abs(got).max() == 0.0, comp
+        elif comp == "13":
+            assert np.abs(got).max() > 0.05
+    # 12 (odd in n2 and n3) sees the x1 Nyquist mode through its x2 and x3 variation
+    assert np.abs(oracle.stress_planes(phi, nz, nh, 0.4, 0.3, 0.0, "12", [0, 1, 4])).max() > 1e-3
+
+
 def _spectral_derivative_matrix(n):
     """Dense first-derivative matrix of the trigonometric interpolant on n periodic
     nodes (unit spacing), Nyquist mode dropped, built by direct trig sums."""
