@@ -203,6 +203,26 @@ int32_t fdm_kernels_per_step(const fdm_handle *h);
  * applied by the static-solve kernels.  Leaves the state and its scalars unchanged. */
 fdm_status fdm_read_stress13_planes(fdm_handle *h, int32_t nplanes, const int32_t *planes, double *out);
 
+/* Stress components, Voigt order. */
+enum { FDM_S11 = 0, FDM_S22 = 1, FDM_S33 = 2, FDM_S23 = 3, FDM_S13 = 4, FDM_S12 = 5 };
+
+/* Any component of the stress of the current state on planes of the 3-D periodic cell (Sec.
+ * 3.1.2 static problem for U^p = U13(x1, x2) chi(x3) e1 (x) e3, chi = 1 on planes 0 .. nh-1).
+ * comp: FDM_S11 .. FDM_S12; FDM_S13 is fdm_read_stress13_planes.  planes[k] in [0, nz),
+ * out [nplanes][n2][n1] (host, float64, caller-owned).  Per unit U13-hat and n = xi/|xi|
+ * the isotropic Green-operator symbols are
+ *   11: 2 mu n1 n3 (1 - n1^2)/(1 - nu)      22: 2 mu n1 n3 (nu - n2^2)/(1 - nu)
+ *   33: 2 mu n1 n3 (1 - n3^2)/(1 - nu)      23: mu n1 n2 (1 - 2 n3^2/(1 - nu))
+ *   13: -mu (n2^2 + 2 n1^2 n3^2/(1 - nu))   12: mu n2 n3 (1 - 2 n1^2/(1 - nu));
+ * the sum over xi3 at plane x3 folds into a 2-D symbol (cos weights for symbols even in n3,
+ * i times sin weights for odd ones), applied by the static-solve kernels.  A symbol odd in
+ * one direction is zero at that axis's Nyquist index.  The plane means are sigma_bar13 for
+ * 13 and zero for the others.  Leaves the state unchanged.  Errors: FDM_ERR_INVALID_ARG
+ * (null handle, comp or plane out of range, null arrays with nplanes > 0), FDM_ERR_STATE
+ * (no state, or a step in progress). */
+fdm_status fdm_read_stress_planes(fdm_handle *h, int32_t comp, int32_t nplanes, const int32_t *planes,
+                                  double *out);
+
 /* Switches the macroscopic loading between stages of a run (Sec. 5.1: equilibration at
  * zero mean stress, then a strain rate): the next step uses the new mode and values; step
  * and time carry on.  Same validation as fdm_create; waits for the stream. */

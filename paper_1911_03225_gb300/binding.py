@@ -29,6 +29,8 @@ FDM_ERR_TOO_LARGE = 9
 V_PRESCRIBED, V_STRESS = 0, 1
 LOAD_STRESS, LOAD_STRAIN_RAMP, LOAD_ZERO_MEAN_STRESS, LOAD_STRAIN_RATE = 0, 1, 2, 3
 FP64, MIXED, DF64 = 0, 1, 2
+# stress components in Voigt order (FDM_S11 .. FDM_S12)
+STRESS_COMPONENTS = ("11", "22", "33", "23", "13", "12")
 T_MIDPOINT, T_LITERAL = 0, 1
 
 FIELD_UP13, FIELD_ALPHA11, FIELD_ALPHA12, FIELD_TAU13, FIELD_V1, FIELD_V2 = 1, 2, 4, 8, 16, 32
@@ -45,7 +47,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
-           "fdm_read_stress13_planes"]
+           "fdm_read_stress13_planes", "fdm_read_stress_planes"]
 
 
 class CParams(C.Structure):
@@ -192,6 +194,8 @@ def load():
     lib.fdm_set_loading.restype = C.c_int
     lib.fdm_read_stress13_planes.argtypes = [H, C.c_int32, C.POINTER(C.c_int32), d]
     lib.fdm_read_stress13_planes.restype = C.c_int
+    lib.fdm_read_stress_planes.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int32), d]
+    lib.fdm_read_stress_planes.restype = C.c_int
     lib.fdm_launch_candidates.argtypes = [C.POINTER(CParams), C.POINTER(CLaunchConfig), C.c_int32]
     lib.fdm_launch_candidates.restype = C.c_int32
     for name in ("fdm_batch_create", "fdm_batch_set_plastic_distortion", "fdm_batch_set_budget",
@@ -308,6 +312,17 @@ class FDM:
         out = np.empty((len(pl),) + self.shape, dtype=np.float64)
         _check(self.lib.fdm_read_stress13_planes(self.h, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int32)),
                                                  _dptr(out)), "fdm_read_stress13_planes")
+        return out
+
+    def read_stress_planes(self, comp, planes) -> np.ndarray:
+        """Stress component ``comp`` ("11", "22", "33", "23", "13", "12" or its Voigt index) of
+        the current state on the given planes x3 of the 3-D cell; returns
+        [len(planes)][n2][n1]."""
+        c = STRESS_COMPONENTS.index(comp) if isinstance(comp, str) else int(comp)
+        pl = np.ascontiguousarray(planes, dtype=np.int32)
+        out = np.empty((len(pl),) + self.shape, dtype=np.float64)
+        _check(self.lib.fdm_read_stress_planes(self.h, c, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int32)),
+                                               _dptr(out)), "fdm_read_stress_planes")
         return out
 
     def set_loading(self, mode: int, sigma_bar13: float = 0.0, eps_bar13_0: float = 0.0,

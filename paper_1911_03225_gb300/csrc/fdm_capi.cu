@@ -322,7 +322,7 @@ struct fdm_handle {
     size_t n;                // n1 * n2
     void* rd[4];             // readout buffers (type T, n each), allocated on first use
     void* mfac_buf;          // mobility factor (type T, n), allocated on first use
-    void* plane_buf[5];      // sigma13 planes: FP64 table, table in T, k3 weights, output in T, scalars
+    void* plane_buf[5];      // stress planes: FP64 table, table in T, k3 weights, output in T, scalars
     Dev rd64;                // mixed precision: FP64 spectra and tables for the Nye readout
     void* rd64_buf[3];       //   U13 and the two Nye components in FP64 (n each)
 };
@@ -629,8 +629,13 @@ int32_t fdm_kernels_per_step(const fdm_handle* h) {
     return kKernelsPerStep;
 }
 
-fdm_status fdm_read_stress13_planes(fdm_handle* h, int32_t nplanes, const int32_t* planes, double* out) {
-    if (!h || nplanes < 0 || (nplanes > 0 && (!planes || !out))) return FDM_ERR_INVALID_ARG;
+// Stress component comp on planes of the 3-D cell.  13 keeps the layer kernel's table (cos
+// weights, macroscopic stress at DC); the others take the component's table with cos or sin
+// weights and the symmetric or odd, real or imaginary column multiplier.
+static fdm_status read_stress_planes(fdm_handle* h, int32_t comp, int32_t nplanes, const int32_t* planes,
+                                     double* out) {
+    if (!h || comp < FDM_S11 || comp > FDM_S12 || nplanes < 0 || (nplanes > 0 && (!planes || !out)))
+        return FDM_ERR_INVALID_ARG;
     const fdm_params& p = h->d.p;
     for (int32_t k = 0; k < nplanes; ++k)
         if (planes[k] < 0 || planes[k] >= p.nz) return FDM_ERR_INVALID_ARG;
@@ -643,33 +648,55 @@ fdm_status fdm_read_stress13_planes(fdm_handle* h, int32_t nplanes, const int32_
     for (int i = 0; i < 5; ++i)
         if (!h->plane_buf[i] && (st = h->arena.alloc(&h->plane_buf[i], sizes[i]))) return st;
     const double mu = p.E / (2.0 * (1.0 + p.nu));
+    // the symbols of 11, 22, 33 and 12 are odd in n3: their sum over k3 pairs +k3 with -k3
+    // into i sin; the unpaired x3 Nyquist term is dropped
+    const bool odd3 = comp != FDM_S13 && comp != FDM_S23;
     std::vector<double> w((size_t)p.nz / 2 + 1);
     std::vector<double> host((size_t)h->n);
     for (int32_t k = 0; k < nplanes; ++k) {
-        // weights D(k3) cos(2 pi k3 (x3 - (nh - 1)/2) / nz), k3 in [0, nz/2]
+        // weights D(k3) cos (or sin) of 2 pi k3 (x3 - (nh - 1)/2) / nz, k3 in [0, nz/2]
         const double shift = (double)planes[k] - 0.5 * (double)(p.nh - 1);
         for (int k3 = 0; k3 <= p.nz / 2; ++k3) {
             const double D = k3 == 0 ? (double)p.nh
                                      : std::sin(kPi * (double)k3 * p.nh / p.nz) / std::sin(kPi * (double)k3 / p.nz);
-            w[k3] = D * std::cos(2.0 * kPi * (double)k3 * shift / (double)p.nz);
+            const double a = 2.0 * kPi * (double)k3 * shift / (double)p.nz;
+            w[k3] = odd3 ? (2 * k3 == p.nz ? 0.0 : D * std::sin(a)) : D * std::cos(a);
         }
         FDM_CK(cudaMemcpyAsync(h->plane_buf[2], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice,
                                h->stream));
         // the layer-average table divides by nz nh; a single plane divides by nz only
-        launch_kernel_table((double*)h->plane_buf[0], p.n1, p.n2, p.nz, 1, mu, p.nu, (const double*)h->plane_buf[2],
-                            h->stream);
+        if (comp == FDM_S13)
+            launch_kernel_table((double*)h->plane_buf[0], p.n1, p.n2, p.nz, 1, mu, p.nu,
+                                (const double*)h->plane_buf[2], h->stream);
+        else
+            launch_stress_table((double*)h->plane_buf[0], p.n1, p.n2, p.nz, comp, mu, p.nu,
+                                (const double*)h->plane_buf[2], h->stream);
         FDM_CK(cudaGetLastError());
         Dev r = h->d;            // the handle's buffers with the plane's table and a copy of the scalars
         r.Kh = h->plane_buf[1];
         r.sc = (fdm_dev_scalars*)h->plane_buf[4];
         FDM_CK(cudaMemcpyAsync(r.sc, h->d.sc, sizeof(fdm_dev_scalars), cudaMemcpyDeviceToDevice, h->stream));
-        FDM_DISPATCH(h->prec, launch_convert<T>((const double*)h->plane_buf[0], (T*)r.Kh, nk, 0.0, h->stream);
-                     launch_static_to<T>(r, (T*)h->plane_buf[3], h->stream));
+        if (comp == FDM_S13) {
+            FDM_DISPATCH(h->prec, launch_convert<T>((const double*)h->plane_buf[0], (T*)r.Kh, nk, 0.0, h->stream);
+                         launch_static_to<T>(r, (T*)h->plane_buf[3], h->stream));
+        } else {
+            FDM_DISPATCH(h->prec, launch_convert<T>((const double*)h->plane_buf[0], (T*)r.Kh, nk, 0.0, h->stream);
+                         launch_stress_to<T>(r, comp, (T*)h->plane_buf[3], h->stream));
+        }
         FDM_CK(cudaGetLastError());
         if ((st = download_field(host.data(), h->plane_buf[3], h->n, h->prec, 0.0, h->stream))) return st;
         std::memcpy(out + (size_t)k * h->n, host.data(), h->n * sizeof(double));
     }
     return FDM_OK;
+}
+
+fdm_status fdm_read_stress13_planes(fdm_handle* h, int32_t nplanes, const int32_t* planes, double* out) {
+    return read_stress_planes(h, FDM_S13, nplanes, planes, out);
+}
+
+fdm_status fdm_read_stress_planes(fdm_handle* h, int32_t comp, int32_t nplanes, const int32_t* planes,
+                                  double* out) {
+    return read_stress_planes(h, comp, nplanes, planes, out);
 }
 
 fdm_status fdm_set_loading(fdm_handle* h, int32_t mode, double sigma_bar13, double eps_bar13_0,

@@ -80,6 +80,9 @@ template <typename T> void launch_step(const Dev& d, cudaStream_t s);
 template <typename T> void launch_phase(const Dev& d, int phase, cudaStream_t s);
 template <typename T> void launch_static(const Dev& d, cudaStream_t s);
 template <typename T> void launch_static_to(const Dev& d, T* dst, cudaStream_t s);
+// stress component comp (Voigt order 11, 22, 33, 23, 13, 12; not 13, which takes
+// launch_static_to with its macroscopic stress) with the plane table in d.Kh
+template <typename T> void launch_stress_to(const Dev& d, int comp, T* dst, cudaStream_t s);
 template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);
 template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,
@@ -92,6 +95,8 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
                      cudaStream_t s);
 void launch_pair_to_double(const float* hi, const float* lo, double* out, size_t n, cudaStream_t s);
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
+                         cudaStream_t s);
+void launch_stress_table(double* Kh, int n1, int n2, int nz, int comp, double mu, double nu, const double* w3,
                          cudaStream_t s);
 
 struct df;  // double-word type (fdm_df.cuh)

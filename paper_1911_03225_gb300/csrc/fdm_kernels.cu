@@ -171,8 +171,12 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
 //   COL_DERIV2N   alpha11-hat = -i xi2 U-hat (odd symbol, 0 at the x2 Nyquist index)
 //   COL_FWD       forward transform only (no normalisation)
 //   COL_INV       inverse transform only
+//   COL_SYM       stress component on a plane of the 3-D cell: the quarter table Kh holds
+//                 |symbol| for kx, ky >= 0 (normalisation folded in); the symbol is i times
+//                 it when sym_imag, and changes sign with ky when sym_odd2 (the sign in kx
+//                 never enters: kx >= 0 in the half spectrum); DC is zero
 constexpr int kRedLanes = 256;  // lanes of the <U13> reduction in the column kernel
-enum ColMode { COL_K = 0, COL_DERIV1 = 1, COL_DERIV2N = 2, COL_FWD = 3, COL_INV = 4 };
+enum ColMode { COL_K = 0, COL_DERIV1 = 1, COL_DERIV2N = 2, COL_FWD = 3, COL_INV = 4, COL_SYM = 5 };
 
 template <typename T>
 struct ColArgs {
@@ -184,6 +188,7 @@ struct ColArgs {
     int gated;                   // COL_K: honour the instances' step budgets
     T scl;                       // 1 / (n1 n2)
     T xi1_unit, xi2_unit;        // 2 pi / (n dx): xi = k~ * unit
+    int sym_odd2, sym_imag;      // COL_SYM: symbol odd in xi2; symbol imaginary
 };
 
 template <typename T>
@@ -193,6 +198,12 @@ __device__ __forceinline__ cpx<T> col_multiplier(const ColArgs<T>& a, const T* _
     if (a.mode == COL_K) {   // the table carries the 1/(n1 n2) normalisation
         int kyf = ky <= n2 / 2 ? ky : n2 - ky;
         return mk(Kh[(size_t)kxi * (n2 / 2 + 1) + kyf], T(0));
+    }
+    if (a.mode == COL_SYM) {
+        int kyf = ky <= n2 / 2 ? ky : n2 - ky;
+        T v = Kh[(size_t)kxi * (n2 / 2 + 1) + kyf];
+        if (a.sym_odd2 && ky > n2 / 2) v = -v;
+        return a.sym_imag ? mk(T(0), v) : mk(v, T(0));
     }
     if (a.mode == COL_DERIV1) {
         if (2 * kxi == n1) return mk(T(0), T(0));
@@ -210,7 +221,7 @@ template <typename T>
 __device__ __forceinline__ cpx<T> col_apply(const ColArgs<T>& a, const T* __restrict__ Kh, int kxi, int ky,
                                             int n1, int n2, cpx<T> z) {
     const cpx<T> m = col_multiplier<T>(a, Kh, kxi, ky, n1, n2);
-    if (a.mode == COL_K) return mk(m.x * z.x, m.x * z.y);
+    if (a.mode == COL_K || (a.mode == COL_SYM && !a.sym_imag)) return mk(m.x * z.x, m.x * z.y);
     return mk(-(m.y * z.y), m.y * z.x);
 }
 
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     }
     __syncthreads();
     if (a.mode != COL_INV) smem_fft_ip<-1>(A, n2, C, ld, pt2);
-    if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N) {
+    if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N || a.mode == COL_SYM) {
         // in place: a thread owns the pair (ky, n2 - ky) of one column
         const int hp = n2 / 2 + 1;
         for (int e = threadIdx.x; e < C * hp; e += blockDim.x) {
@@ -653,6 +664,51 @@ __global__ void kernel_table_kernel(double* __restrict__ Kh, int n1, int n2, int
     }
 }
 
+// One stress component of the layered eigen-distortion on a plane of the 3-D cell (Sec.
+// 3.1.2), Voigt index comp (11, 22, 33, 23, 13, 12).  Closed forms of the isotropic
+// Green-operator stress per unit U13-hat, n = xi/|xi|:
+//   11: 2 mu n1 n3 (1 - n1^2)/(1 - nu)     22: 2 mu n1 n3 (nu - n2^2)/(1 - nu)
+//   33: 2 mu n1 n3 (1 - n3^2)/(1 - nu)     23: mu n1 n2 (1 - 2 n3^2/(1 - nu))
+//   13: -mu (n2^2 + 2 n1^2 n3^2/(1 - nu))  12: mu n2 n3 (1 - 2 n1^2/(1 - nu))
+// Kh[kx][ky] = (1/(nz n1 n2)) sum_{k3 = 0}^{nz/2} mult m(xi1, xi2, xi3) w3[k3] at kx, ky, k3
+// >= 0; w3 holds D(k3) cos or, for symbols odd in n3, D(k3) sin of 2 pi k3 (x3 - (nh - 1)/2)
+// / nz (host table, zero at the x3 Nyquist index for odd symbols).  A symbol odd in n1 (n2)
+// is zero at the x1 (x2) Nyquist index.
+__device__ __forceinline__ double stress_symbol(int comp, double x1, double x2, double x3, double mu,
+                                                double nu) {
+    const double ir2 = 1.0 / (x1 * x1 + x2 * x2 + x3 * x3);
+    const double q1 = x1 * x1 * ir2, q2 = x2 * x2 * ir2, q3 = x3 * x3 * ir2, inu = 1.0 / (1.0 - nu);
+    switch (comp) {
+        case 0: return 2.0 * mu * (x1 * x3 * ir2) * (1.0 - q1) * inu;
+        case 1: return 2.0 * mu * (x1 * x3 * ir2) * (nu - q2) * inu;
+        case 2: return 2.0 * mu * (x1 * x3 * ir2) * (1.0 - q3) * inu;
+        case 3: return mu * (x1 * x2 * ir2) * (1.0 - 2.0 * q3 * inu);
+        case 4: return -mu * (q2 + 2.0 * q1 * q3 * inu);
+        default: return mu * (x2 * x3 * ir2) * (1.0 - 2.0 * q1 * inu);
+    }
+}
+
+__global__ void stress_table_kernel(double* __restrict__ Kh, int n1, int n2, int nz, int comp, double mu,
+                                    double nu, const double* __restrict__ w3) {
+    const int w = n2 / 2 + 1;
+    const int total = (n1 / 2 + 1) * w;
+    const bool odd1 = comp <= 3, odd2 = comp == 3 || comp == 5;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int kx = i / w, ky = i - kx * w;
+        double acc = 0.0;
+        if (!(odd1 && 2 * kx == n1) && !(odd2 && 2 * ky == n2)) {
+            double x1 = (double)kx / (double)n1, x2 = (double)ky / (double)n2;
+            for (int k3 = 0; k3 <= nz / 2; ++k3) {
+                double x3 = (double)k3 / (double)nz;
+                if (x1 == 0.0 && x2 == 0.0 && k3 == 0) continue;
+                double mult = (k3 == 0 || 2 * k3 == nz) ? 1.0 : 2.0;
+                acc += mult * stress_symbol(comp, x1, x2, x3, mu, nu) * w3[k3];
+            }
+        }
+        Kh[i] = acc / (double)nz / ((double)n1 * (double)n2);
+    }
+}
+
 // FP32 word pairs -> FP64 (exact: hi + lo has at most 48 significant bits)
 __global__ void pair_to_double_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
                                       double* __restrict__ out, size_t n) {
@@ -886,7 +942,8 @@ void launch_row_forward(const Dev& d, const T* src0, const T* src1, cpx<T>* spec
 }
 
 template <typename T>
-void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, int count, cudaStream_t s) {
+void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, int count, cudaStream_t s,
+                int sym_odd2 = 0, int sym_imag = 0) {
     const LaunchGeom& g = d.geom;
     ColArgs<T> a;
     a.p = d.p;
@@ -898,6 +955,8 @@ void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with
     a.scl = T(1.0 / ((double)d.p.n1 * (double)d.p.n2));
     a.xi1_unit = T(6.283185307179586476925286766559 / ((double)d.p.n1 * d.p.dx));
     a.xi2_unit = T(6.283185307179586476925286766559 / ((double)d.p.n2 * d.p.dx));
+    a.sym_odd2 = sym_odd2;
+    a.sym_imag = sym_imag;
     dim3 grid(g.col_blocks, count);
     col_pass_kernel<T><<<grid, g.col_threads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
                                                              (const cpx<T>*)d.pt2, (const T*)d.Kh, a);
@@ -982,6 +1041,17 @@ void launch_static_to(const Dev& d, T* dst, cudaStream_t s) {
     launch_row_inverse<T>(d, (const cpx<T>*)d.spec, dst, ROW_PLAIN, 0.0, 1, s);
 }
 
+// one stress component of the current state (single instance) with the plane table d.Kh of
+// a COL_SYM symbol (parity and type as stress_table_kernel's comp): rows, column transform with
+// the symbol, inverse rows, written to dst
+template <typename T>
+void launch_stress_to(const Dev& d, int comp, T* dst, cudaStream_t s) {
+    launch_phase<T>(d, 0, s);
+    cpx<T>* spec = (cpx<T>*)d.spec;
+    launch_col<T>(d, spec, spec, COL_SYM, false, 1, s, comp == 3 || comp == 5, comp != 3);
+    launch_row_inverse<T>(d, (const cpx<T>*)d.spec, dst, ROW_PLAIN, 0.0, 1, s);
+}
+
 // static solve only: tau for the current state of every instance
 template <typename T>
 void launch_static(const Dev& d, cudaStream_t s) {
@@ -1028,6 +1098,14 @@ void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, 
     kernel_table_kernel<<<blocks, 256, 0, s>>>(Kh, n1, n2, nz, nh, mu, nu, w3);
 }
 
+void launch_stress_table(double* Kh, int n1, int n2, int nz, int comp, double mu, double nu, const double* w3,
+                         cudaStream_t s) {
+    int total = (n1 / 2 + 1) * (n2 / 2 + 1);
+    int blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    stress_table_kernel<<<blocks, 256, 0, s>>>(Kh, n1, n2, nz, comp, mu, nu, w3);
+}
+
 template <typename T>
 void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
@@ -1061,6 +1139,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_phase<T>(const Dev&, int, cudaStream_t);                                           \
     template void launch_static<T>(const Dev&, cudaStream_t);                                               \
     template void launch_static_to<T>(const Dev&, T*, cudaStream_t);                                        \
+    template void launch_stress_to<T>(const Dev&, int, T*, cudaStream_t);                                   \
     template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \

@@ -84,6 +84,9 @@ def test_null_arguments(lib):
     assert lib.fdm_read_fields(None, 1, None, None, None, None, None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_set_mobility_field(None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_set_loading(None, 0, 0.0, 0.0, 0.0) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_read_stress_planes(None, binding.STRESS_COMPONENTS.index("11"), 0, None, None) == \
+        binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_read_stress13_planes(None, 0, None, None) == binding.FDM_ERR_INVALID_ARG
     lib.fdm_destroy(None)   # NULL-safe
 
 

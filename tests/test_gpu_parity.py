@@ -177,6 +177,50 @@ def test_stress13_planes_at_scale_reproduce_the_layer_reduction():
     assert np.abs(planes[4] - 0.01).max() < np.abs(tau - 0.01).max()
 
 
+@pytest.mark.parametrize("precision,tol", [(B.FP64, TOL64), (B.DF64, TOL64), (B.MIXED, TOL_MIXED)])
+@pytest.mark.parametrize("nh", [3, 4])
+def test_stress_planes_all_components_match_oracle(precision, tol, nh):
+    """Every stress component through the 3-D cell (Sec. 3.1.2 on the nz-voxel cell) against
+    the oracle's term-by-term transform of the Green-operator vector form: planes in, at the
+    edge of and far from the layer, a non-square grid, input with Nyquist content; the GPU
+    folds the sum over xi3 into cos or i sin weights and the closed-form symbols."""
+    n1, n2, nz = 64, 32, 32
+    up0 = inputs.random_up(64, seed=16, ell=4.0)[:n2, :n1].copy()
+    p = Params(n1=n1, n2=n2, nz=nz, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS,
+               sigma_bar13=0.02, precision=precision)
+    planes = [0, 1, 2, 3, 4, 9, 16, 31]
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve()
+        got = {c: sim.read_stress_planes(c, planes) for c in B.STRESS_COMPONENTS}
+        s13 = sim.read_stress13_planes(planes)
+        assert sim.info().step == 0
+    for c in B.STRESS_COMPONENTS:
+        ref = oracle.stress_planes(up0, nz, nh, 1 / 2.6, 0.3, 0.02, c, planes)
+        assert rel(got[c], ref) < tol, c
+        for g in got[c]:
+            assert abs(g.mean() - (0.02 if c == "13" else 0.0)) < 1e-6
+    np.testing.assert_array_equal(got["13"], s13)
+
+
+def test_stress_planes_at_scale_reflection_symmetry():
+    """At 1024^2 x 1024 (three-plane layer, mid-plane x3 = 1): reflecting x3 about the
+    layer's mid-plane maps U13 e1 (x) e3 to minus itself, so 13 and 23 are even and 11, 22,
+    33 and 12 odd about it, at every distance."""
+    n, nz, nh = 1024, 1024, 3
+    up0 = inputs.random_up(n, seed=17, ell=16.0)
+    p = Params(n1=n, n2=n, nz=nz, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.0)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        for c in B.STRESS_COMPONENTS:
+            sign = 1.0 if c in ("13", "23") else -1.0
+            s = sim.read_stress_planes(c, [2, 0, 5, nz - 3, 300, nz - 298])
+            scale = np.abs(s[:2]).max()
+            assert scale > 1e-4, c
+            for a, b in ((0, 1), (2, 3), (4, 5)):
+                assert np.abs(s[a] - sign * s[b]).max() < 1e-12 * scale, (c, a)
+
+
 # ------------------------------------------------------------------ time stepping
 @pytest.mark.parametrize("precision", [B.FP64, B.DF64])
 def test_config0_lines_annihilation(precision):
