@@ -32,7 +32,8 @@
  *   G6  dH/dp at grad phi = 0 is 0.
  *   G7  v0 is the node's value from the previous static solve; grad v0 is ignored.
  *   G8  continuous frequencies xi = 2 pi k~/(N dx); even symbols kept at Nyquist, odd
- *       symbols (curl-inverse, spectral derivative) zeroed there.
+ *       symbols (curl-inverse, spectral derivative) zeroed there; a stress symbol of the
+ *       3-D cell odd in one direction is zeroed at that axis's Nyquist index.
  *   G9  layer of nh voxels in a cubic periodic cell of nz voxels.
  *   G10 strain control: sigma_bar13 = 2 mu eps_bar13 - mu (nh/nz) <U13>.
  *

@@ -178,3 +178,27 @@ def test_batched_256_uneven_instances_mixed_against_fp64():
         assert infos[i].step == steps
         assert rel(got[i]["up13"], ref["up13"]) < 1e-5, (i, side[i])
         assert rel(got[i]["tau13"], ref["tau13"]) < 1e-5, (i, side[i])
+
+
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+def test_coupled_2048_energy_never_increases(precision):
+    """The 2048^2 random field of the coupled configuration at zero macroscopic stress, in the
+    bench's launch shapes: the elastic energy -1/2 sum tau13 (U13 - <U13>) falls between every
+    pair of checkpoints (Sec. 3.2: the dissipation tau13 dU13/dt = M tau13^2 |grad U13| is
+    non-negative), with tau13 from a static solve of the state reached."""
+    n = 2048
+    up0 = inputs.random_up(n, seed=0, ell=16.0, rms_alpha=0.1)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, mobility=1.0, loading_mode=B.LOAD_STRESS, sigma_bar13=0.0,
+               cfl=0.4, theta=1.0, precision=precision)
+    w = []
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        for _ in range(6):
+            sim.static_solve()
+            f = sim.read_fields("up13", "tau13")
+            u = f["up13"]
+            w.append(-0.5 * float(np.sum(f["tau13"] * (u - u.mean()))))
+            sim.step(40)
+    w = np.array(w)
+    assert (np.diff(w) < 0).all(), w
+    assert w[-1] < 0.9 * w[0]

@@ -707,6 +707,34 @@ def test_stress_driven_velocity_and_cfl_step():
     assert st1.tau13.mean() == pytest.approx(0.01, abs=1e-15)
 
 
+@pytest.mark.parametrize("theta,tau_y", [(1.0, 0.0), (2.0, 0.0), (1.0, 0.02)])
+def test_energy_never_increases_under_stress_driven_motion(theta, tau_y):
+    """Sec. 3.2 (dissipation): with the linear mobility law the plastic rate is M (tau13 -
+    tau_y cos(U13/beta)) |grad U13| and the dissipation (tau13 - tau_y cos) dU13/dt >= 0, so
+    the stored energy -- elastic, -1/2 sum tau13 (U13 - <U13>) at zero macroscopic stress,
+    plus the wiggly potential beta tau_y sin(U13/beta) -- never increases along the scheme's
+    steps (a dropped term or a sign error in the static solve or the celerity law breaks it)."""
+    n, beta = 32, 0.05
+    up = inputs.random_up(n, seed=3, ell=4.0, rms_alpha=0.1)
+    K = oracle.kernel_table(n, n, n, 4, 1 / 2.6, 0.3)
+    p = oracle.Params(n1=n, n2=n, velocity_mode=1, loading_mode=0, sigma_bar13=0.0, cfl=0.4, theta=theta,
+                      tau_y=tau_y, beta=beta)
+
+    def energy(u):
+        tau = oracle.static_tau(u, K, 0.0)
+        return -0.5 * np.sum(tau * (u - u.mean())) + np.sum(beta * tau_y * np.sin(u / beta))
+
+    st, _ = oracle.run(p, up, 0, K=K)
+    w = [energy(up)]
+    for _ in range(30):
+        st, rc = oracle.run(p, up, 1, K=K, state=st)
+        assert rc == 0
+        w.append(energy(st.up13))
+    w = np.array(w)
+    assert (np.diff(w) < 0).all()
+    assert w[-1] < 0.5 * w[0]
+
+
 # --------------------------------------------------------------------------- paper's numbers
 def test_nondimensional_numbers_printed_in_paper():
     g = json.load(open(os.path.join(GOLDEN, "paper_nondimensional.json")))
