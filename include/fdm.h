@@ -191,6 +191,12 @@ fdm_status fdm_read_fields(fdm_handle *h, uint32_t mask, double *up13, double *a
 /* Scalars of the current state (same content as fdm_step's info). */
 fdm_status fdm_get_info(fdm_handle *h, fdm_step_info *info);
 
+/* Host-side fault injection for tests of the error paths: the n-th device or pinned-host
+ * allocation from now on (0 = the next one) fails as if the device were out of memory, once;
+ * n < 0 switches it off.  Process-wide; not thread-safe.  The call that hits the failure
+ * returns FDM_ERR_OOM and releases everything it had allocated. */
+void fdm_debug_fail_allocation(int32_t n);
+
 /* Number of kernel launches one step issues (for launch accounting). */
 int32_t fdm_kernels_per_step(const fdm_handle *h);
 
@@ -303,6 +309,12 @@ fdm_status fdm_batch_enqueue_steps(fdm_batch *b, int32_t nsteps);
 /* Waits for the stream; copies every instance's remaining budget to steps_left[count]
  * (may be NULL) and returns the first device-side error of any instance. */
 fdm_status fdm_batch_sync(fdm_batch *b, int64_t *steps_left);
+
+/* As fdm_batch_sync, but instance errors do not fail the call: status[count] (may be NULL)
+ * receives each instance's device-side status (FDM_OK, or FDM_ERR_NONFINITE once a time
+ * step or max |v0| stopped being finite), so that a server can retire a failed instance and
+ * keep the others running.  Returns only errors of the call itself. */
+fdm_status fdm_batch_sync_status(fdm_batch *b, int64_t *steps_left, int32_t *status);
 
 /* Scalars of instance i (as fdm_get_info). */
 fdm_status fdm_batch_get_info(fdm_batch *b, int32_t i, fdm_step_info *info);

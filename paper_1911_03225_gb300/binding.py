@@ -47,7 +47,8 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_sync", "fdm_batch_get_info", "fdm_batch_read_fields", "fdm_batch_launches_per_step",
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
-           "fdm_read_stress13_planes", "fdm_read_stress_planes"]
+           "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
+           "fdm_debug_fail_allocation"]
 
 
 class CParams(C.Structure):
@@ -176,6 +177,10 @@ def load():
     lib.fdm_batch_set_budget.argtypes = [H, C.c_int32, C.c_int64]
     lib.fdm_batch_enqueue_steps.argtypes = [H, C.c_int32]
     lib.fdm_batch_sync.argtypes = [H, C.POINTER(C.c_int64)]
+    lib.fdm_batch_sync_status.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.fdm_batch_sync_status.restype = C.c_int
+    lib.fdm_debug_fail_allocation.argtypes = [C.c_int32]
+    lib.fdm_debug_fail_allocation.restype = None
     lib.fdm_batch_get_info.argtypes = [H, C.c_int32, C.POINTER(CStepInfo)]
     lib.fdm_batch_read_fields.argtypes = [H, C.c_int32, C.c_uint32, d, d]
     lib.fdm_batch_launches_per_step.argtypes = [H]
@@ -214,6 +219,11 @@ def load():
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+def debug_fail_allocation(n: int):
+    """Test hook: the n-th device or pinned allocation from now on fails once (n < 0: off)."""
+    load().fdm_debug_fail_allocation(int(n))
 
 
 def status_str(s: int) -> str:
@@ -485,6 +495,15 @@ class Batch:
         left = np.zeros(self.count, dtype=np.int64)
         _check(self.lib.fdm_batch_sync(self.h, left.ctypes.data_as(C.POINTER(C.c_int64))), "fdm_batch_sync")
         return left
+
+    def sync_status(self):
+        """Wait; return (remaining step budgets, device-side status of every instance) without
+        raising on instance errors."""
+        left = np.zeros(self.count, dtype=np.int64)
+        status = np.zeros(self.count, dtype=np.int32)
+        _check(self.lib.fdm_batch_sync_status(self.h, left.ctypes.data_as(C.POINTER(C.c_int64)),
+                                              status.ctypes.data_as(C.POINTER(C.c_int32))), "fdm_batch_sync_status")
+        return left, status
 
     def info(self, i: int) -> StepInfo:
         ci = CStepInfo()

@@ -172,6 +172,21 @@ fdm_status fdm_batch_sync(fdm_batch* b, int64_t* steps_left) {
     return first;
 }
 
+fdm_status fdm_batch_sync_status(fdm_batch* b, int64_t* steps_left, int32_t* status) {
+    if (!b) return FDM_ERR_INVALID_ARG;
+    for (auto& G : b->groups) {
+        std::vector<fdm_dev_scalars> s(G.members.size());
+        FDM_CK(cudaMemcpyAsync(s.data(), G.d.sc, s.size() * sizeof(fdm_dev_scalars), cudaMemcpyDeviceToHost,
+                               b->stream));
+        FDM_CK(cudaStreamSynchronize(b->stream));
+        for (size_t j = 0; j < s.size(); ++j) {
+            if (steps_left) steps_left[G.members[j]] = (int64_t)s[j].steps_left;
+            if (status) status[G.members[j]] = (int32_t)s[j].status;
+        }
+    }
+    return FDM_OK;
+}
+
 fdm_status fdm_batch_get_info(fdm_batch* b, int32_t i, fdm_step_info* info) {
     if (!index_ok(b, i) || !info) return FDM_ERR_INVALID_ARG;
     if (!b->has_state[i]) return FDM_ERR_STATE;

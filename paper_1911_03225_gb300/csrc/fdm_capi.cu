@@ -84,6 +84,8 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     if ((st = A.alloc((void**)&d.row_partials, (size_t)count * p.n2 * sizeof(double)))) return st;
     d.red_blocks = red_blocks_for(n);
     if ((st = A.alloc((void**)&d.red, (size_t)6 * d.red_blocks * sizeof(double)))) return st;
+    if ((st = A.alloc_host((void**)&d.red_host, kInfoScalarBytes + (size_t)6 * d.red_blocks * sizeof(double))))
+        return st;
     if ((st = A.alloc((void**)&d.sc, (size_t)count * sizeof(fdm_dev_scalars)))) return st;
     FDM_CK(cudaMemsetAsync(d.sc, 0, (size_t)count * sizeof(fdm_dev_scalars), s));
     FDM_CK(cudaMemsetAsync(d.phi[0], 0, cn * sizeof(T), s));
@@ -272,25 +274,27 @@ fdm_status replay_steps(StepGraphs& g, int nsteps, cudaStream_t s) {
 }
 
 // FP64 sums over the staggered Nye components of one instance's current state (info)
+int g_fail_alloc_countdown = -1;
+
 fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, fdm_step_info* info) {
-    fdm_dev_scalars s;
-    FDM_CK(cudaMemcpyAsync(&s, d.sc + inst, sizeof(s), cudaMemcpyDeviceToHost, stream));
-    FDM_CK(cudaStreamSynchronize(stream));
-    const size_t n = (size_t)d.p.n1 * d.p.n2;
-    const size_t e = elt_size(&d.p);
-    const void* phi = (const char*)d.phi[s.cur] + (size_t)inst * n * e;
-    const void* lo = d.phi_lo[s.cur] ? (const char*)d.phi_lo[s.cur] + (size_t)inst * n * e : nullptr;
-    FDM_DISPATCH(prec, launch_alpha_sums<T>(d, (const T*)phi, (const T*)lo, d.red, d.red_blocks, stream));
+    // the sums read the current buffer on the device: one round trip for scalars and sums
+    FDM_DISPATCH(prec, launch_alpha_sums<T>(d, inst, d.red, d.red_blocks, stream));
     FDM_CK(cudaGetLastError());
-    std::vector<double> part((size_t)6 * d.red_blocks);
-    FDM_CK(cudaMemcpyAsync(part.data(), d.red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    fdm_dev_scalars* hs = (fdm_dev_scalars*)d.red_host;
+    double* part = (double*)((char*)d.red_host + kInfoScalarBytes);
+    FDM_CK(cudaMemcpyAsync(hs, d.sc + inst, sizeof(*hs), cudaMemcpyDeviceToHost, stream));
+    FDM_CK(cudaMemcpyAsync(part, d.red, (size_t)6 * d.red_blocks * sizeof(double), cudaMemcpyDeviceToHost, stream));
     FDM_CK(cudaStreamSynchronize(stream));
+    const fdm_dev_scalars s = *hs;
+    const size_t n = (size_t)d.p.n1 * d.p.n2;
     double sums[6];
     std::vector<double> col(d.red_blocks);
     for (int q = 0; q < 6; ++q) {
         for (int b = 0; b < d.red_blocks; ++b) col[b] = part[6 * b + q];
         sums[q] = ksum(col.data(), col.size());
     }
+    // sums of the differences d12 = dx alpha12 and d11 = -dx alpha11 (Sec. 3.2.1)
+    const double idx = 1.0 / d.p.dx;
     std::memset(info, 0, sizeof(*info));
     info->step = s.step;
     info->t = s.t;
@@ -298,11 +302,11 @@ fdm_status instance_info(const Dev& d, int inst, int prec, cudaStream_t stream, 
     info->max_abs_v0 = s.max_abs_v0;
     info->mean_up13 = s.phi_ref + sums[5] / (double)n;
     host_loading(d.p, s.step, s.t, info->mean_up13, &info->eps_bar13, &info->sigma_bar13);
-    info->sum_a12_pos = sums[0];
-    info->sum_a12_neg = sums[1];
-    info->sum_a11_pos = sums[2];
-    info->sum_a11_neg = sums[3];
-    info->sum_abs_alpha = sums[4];
+    info->sum_a12_pos = 0.5 * (sums[0] + sums[1]) * idx;
+    info->sum_a12_neg = 0.5 * (sums[1] - sums[0]) * idx;
+    info->sum_a11_pos = 0.5 * (sums[2] - sums[3]) * idx;
+    info->sum_a11_neg = -0.5 * (sums[2] + sums[3]) * idx;
+    info->sum_abs_alpha = sums[4] * idx;
     info->status = s.status;
     return FDM_OK;
 }
@@ -494,8 +498,37 @@ fdm_status fdm_create(const fdm_params* p, void* stream, fdm_handle** out) {
     return FDM_OK;
 }
 
+// FP64 state: the field goes to the device as it is (staged in the stress buffer, which the
+// next static solve overwrites) and its mean comes from a device reduction, so that a large
+// restart costs one copy rather than a host pass; the state is replaced only if the sum is
+// finite.
+static fdm_status set_state_fp64(fdm_handle* h, const double* up13) {
+    Dev& d = h->d;
+    const size_t n = h->n;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    FDM_CK(cudaMemcpyAsync(d.tau, up13, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    Dev r = d;
+    r.phi[0] = r.phi[1] = d.tau;
+    r.phi_lo[0] = r.phi_lo[1] = nullptr;
+    r.sc = nullptr;
+    launch_alpha_sums<double>(r, 0, d.red, d.red_blocks, h->stream);
+    FDM_CK(cudaGetLastError());
+    double* part = (double*)((char*)d.red_host + kInfoScalarBytes);
+    FDM_CK(cudaMemcpyAsync(part, d.red, (size_t)6 * d.red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    std::vector<double> col(d.red_blocks);
+    for (int b = 0; b < d.red_blocks; ++b) col[b] = part[6 * b + 5];
+    const double mean = ksum(col.data(), col.size()) / (double)n;
+    if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
+    FDM_CK(cudaMemcpyAsync(d.phi[0], d.tau, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    d.phi_ref_host = 0.0;
+    return reset_scalars(h, mean);
+}
+
 fdm_status fdm_set_plastic_distortion(fdm_handle* h, const double* up13) {
     if (!h || !up13) return FDM_ERR_INVALID_ARG;
+    if (h->prec == FDM_FP64) return set_state_fp64(h, up13);
     double mean = ksum(up13, h->n) / (double)h->n;
     if (!std::isfinite(mean)) return FDM_ERR_INVALID_ARG;
     FDM_CK(cudaStreamSynchronize(h->stream));
@@ -762,6 +795,8 @@ fdm_status fdm_set_launch_config(fdm_handle* h, const fdm_launch_config* cfg) {
     h->d.geom = g;
     return FDM_OK;
 }
+
+void fdm_debug_fail_allocation(int32_t n) { g_fail_alloc_countdown = n < 0 ? -1 : n; }
 
 void fdm_destroy(fdm_handle* h) {
     if (!h) return;

@@ -121,11 +121,36 @@ inline double ksum(const double* x, size_t n) {
     return s + c;
 }
 
-// Device memory owned by one handle or batch; freed together.
+// Bytes of the scalars' slot at the head of a group's pinned readout buffer (16-aligned).
+constexpr size_t kInfoScalarBytes = (sizeof(fdm_dev_scalars) + 15) / 16 * 16;
+
+// Test hook (fdm_debug_fail_allocation): allocations left before one fails, or -1.
+extern int g_fail_alloc_countdown;
+inline bool injected_alloc_failure() {
+    if (g_fail_alloc_countdown < 0) return false;
+    if (g_fail_alloc_countdown-- == 0) return true;
+    return false;
+}
+
+// Device memory (and small pinned host buffers) owned by one handle or batch; freed together.
 struct Arena {
     std::vector<void*> owned;
+    std::vector<void*> owned_host;
+    fdm_status alloc_host(void** ptr, size_t bytes) {
+        *ptr = nullptr;
+        if (injected_alloc_failure()) return FDM_ERR_OOM;
+        cudaError_t e = cudaMallocHost(ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return e == cudaErrorMemoryAllocation ? FDM_ERR_OOM : FDM_ERR_DEVICE;
+        }
+        owned_host.push_back(*ptr);
+        return FDM_OK;
+    }
     fdm_status alloc(void** ptr, size_t bytes) {
         *ptr = nullptr;
+        if (injected_alloc_failure()) return FDM_ERR_OOM;
         cudaError_t e = cudaMalloc(ptr, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -146,6 +171,8 @@ struct Arena {
     void free_all() {
         for (void* q : owned) cudaFree(q);
         owned.clear();
+        for (void* q : owned_host) cudaFreeHost(q);
+        owned_host.clear();
     }
 };
 

@@ -57,6 +57,7 @@ struct Dev {
     void* pt2;             // cpx<T> pass twiddle tables of the n2-point column transform
     double* row_partials;  // [count][n2]: FP64 sum of each row of U13
     double* red;           // reduction partials [6 * red_blocks]
+    double* red_host;      // pinned host copy: the instance's scalars, then the partials
     int red_blocks;
     fdm_dev_scalars* sc;   // [count]
     double phi_ref_host;   // single instance: host copy of sc[0].phi_ref
@@ -88,8 +89,8 @@ template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,
                          double* partials, int nblk, cudaStream_t s);
 template <typename T> void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t s);
-template <typename T>
-void launch_alpha_sums(const Dev& d, const T* phi, const T* phi_lo, double* partials, int nblk, cudaStream_t s);
+// sums of the Nye components of the current state of instance inst (buffer sc[inst].cur)
+template <typename T> void launch_alpha_sums(const Dev& d, int inst, double* partials, int nblk, cudaStream_t s);
 template <typename T>
 void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
                      cudaStream_t s);

@@ -792,24 +792,34 @@ __global__ void curl_inverse_kernel(const cpx<T>* __restrict__ sa, const cpx<T>*
     if (threadIdx.x == 0) { partials[2 * blockIdx.x] = s1; partials[2 * blockIdx.x + 1] = s2; }
 }
 
-// info: FP64 sums over the staggered Nye components of the current state
+// info: FP64 sums over the staggered Nye components of the current state, unscaled by the
+// cell size (the host divides the totals by dx once): per block, sum |d12|, sum d12,
+// sum |d11|, sum d11, sum |(d11, d12)| and sum U13, with d12 = U(x+1, y) - U(x, y) = dx
+// alpha12 and d11 = U(x, y+1) - U(x, y) = -dx alpha11.  The positive and negative parts of
+// each component follow from (sum |d| +- sum d) / 2.  The buffer of the current state is
+// chosen on the device (sc->cur; buffer 0 without scalars).
 template <typename T>
-__global__ void alpha_sums_kernel(const T* __restrict__ phi, const T* __restrict__ lo, int n1, int n2, double dx,
+__global__ void alpha_sums_kernel(const T* __restrict__ phi0, const T* __restrict__ phi1,
+                                  const T* __restrict__ lo0, const T* __restrict__ lo1,
+                                  const fdm_dev_scalars* __restrict__ sc, int n1, int n2,
                                   double* __restrict__ partials) {
     __shared__ double red[32];
+    const int cur = sc ? sc->cur : 0;
+    const T* phi = cur ? phi1 : phi0;
+    const T* lo = cur ? lo1 : lo0;
     double s[6] = {0, 0, 0, 0, 0, 0};
     const size_t total = (size_t)n1 * n2;
     auto val = [&](size_t k) -> double { return lo ? (double)phi[k] + (double)lo[k] : (double)phi[k]; };
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         int y = (int)(i / n1), x = (int)(i - (size_t)y * n1);
         double u = val(i);
-        double a12 = (val((size_t)y * n1 + ((x + 1) & (n1 - 1))) - u) / dx;
-        double a11 = -(val((size_t)((y + 1) & (n2 - 1)) * n1 + x) - u) / dx;
-        s[0] += a12 > 0 ? a12 : 0.0;
-        s[1] += a12 < 0 ? a12 : 0.0;
-        s[2] += a11 > 0 ? a11 : 0.0;
-        s[3] += a11 < 0 ? a11 : 0.0;
-        s[4] += sqrt(a11 * a11 + a12 * a12);
+        double d12 = val((size_t)y * n1 + ((x + 1) & (n1 - 1))) - u;
+        double d11 = val((size_t)((y + 1) & (n2 - 1)) * n1 + x) - u;
+        s[0] += fabs(d12);
+        s[1] += d12;
+        s[2] += fabs(d11);
+        s[3] += d11;
+        s[4] += tsqrt(d11 * d11 + d12 * d12);
         s[5] += u;
     }
     for (int q = 0; q < 6; ++q) {
@@ -1114,8 +1124,11 @@ void launch_convert(const double* a, T* b, size_t n, double offset, cudaStream_t
 }
 
 template <typename T>
-void launch_alpha_sums(const Dev& d, const T* phi, const T* phi_lo, double* partials, int nblk, cudaStream_t s) {
-    alpha_sums_kernel<T><<<nblk, 256, 0, s>>>(phi, phi_lo, d.p.n1, d.p.n2, d.p.dx, partials);
+void launch_alpha_sums(const Dev& d, int inst, double* partials, int nblk, cudaStream_t s) {
+    const size_t off = (size_t)inst * d.p.n1 * d.p.n2;
+    auto at = [&](void* b) -> const T* { return b ? (const T*)b + off : nullptr; };
+    alpha_sums_kernel<T><<<nblk, 256, 0, s>>>(at(d.phi[0]), at(d.phi[1]), at(d.phi_lo[0]), at(d.phi_lo[1]),
+                                             d.sc ? d.sc + inst : nullptr, d.p.n1, d.p.n2, partials);
 }
 
 template <typename T>
@@ -1144,7 +1157,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \
     template void launch_convert<T>(const double*, T*, size_t, double, cudaStream_t);                       \
-    template void launch_alpha_sums<T>(const Dev&, const T*, const T*, double*, int, cudaStream_t);         \
+    template void launch_alpha_sums<T>(const Dev&, int, double*, int, cudaStream_t);                        \
     template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
                                      cudaStream_t);
 FDM_INST(double)

@@ -5,7 +5,9 @@ one ``Batch`` whose slots are grouped by (grid, precision); all resident simulat
 on the device and advance together, ``tick_steps`` batched steps per tick.  Between ticks
 it retires the simulations whose step budget is spent (reading their result back) and
 admits waiting requests into free slots while the device memory of the resident set stays
-within the HBM budget.  Requests that arrive while others run are admitted as soon as a
+within the HBM budget.  A request whose input is refused, or whose simulation stops being
+finite, is retired as failed (``Server.failed``, with the library status) and its slot freed;
+the others carry on.  Requests that arrive while others run are admitted as soon as a
 slot and memory are free; their work then shares every launch with the running ones.
 """
 import math
@@ -40,6 +42,7 @@ class Result:
     finished: float
     up13: Optional[np.ndarray] = field(repr=False, default=None)
     t: float = 0.0
+    status: int = 0          # 0, or the library status that failed the request
 
     @property
     def latency(self) -> float:
@@ -76,6 +79,7 @@ class Server:
             self.free.setdefault(c, deque()).append(s)
         self.bytes_in_use = 0
         self.resident: Dict[int, Tuple[Request, float]] = {}   # slot -> (request, admitted time)
+        self.failed: List[Result] = []
         self.launched_steps = 0
 
     def _admit(self, queue: deque, now: float) -> None:
@@ -93,8 +97,13 @@ class Server:
             if self.bytes_in_use + self.slot_bytes[s] > self.hbm_budget:
                 keep.append(r)
                 continue
+            try:
+                self.batch.set_plastic_distortion(s, r.up13)
+            except FDMError as e:   # refused input (e.g. non-finite): fails alone, slot stays free
+                self.failed.append(Result(r.rid, r.n, r.steps, r.precision, r.arrival, now, now, None, 0.0,
+                                          e.status))
+                continue
             slots.popleft()
-            self.batch.set_plastic_distortion(s, r.up13)
             self.batch.set_budget(s, r.steps)
             self.bytes_in_use += self.slot_bytes[s]
             self.resident[s] = (r, now)
@@ -124,9 +133,17 @@ class Server:
                 continue
             self.batch.enqueue_steps(self.tick_steps)
             self.launched_steps += self.tick_steps
-            left = self.batch.sync()
+            left, status = self.batch.sync_status()
             ticks += 1
             done_at = clock()
+            for s in [s for s in self.resident if status[s] != 0]:
+                # the simulation left the finite range: retire it as failed, free its slot
+                r, adm = self.resident.pop(s)
+                self.batch.set_budget(s, 0)
+                self.failed.append(Result(r.rid, r.n, r.steps, r.precision, r.arrival, adm, done_at, None, 0.0,
+                                          int(status[s])))
+                self.free[(r.n, r.precision)].append(s)
+                self.bytes_in_use -= self.slot_bytes[s]
             for s in [s for s in self.resident if left[s] == 0]:
                 r, adm = self.resident.pop(s)
                 f = self.batch.read_fields(s, "up13") if self.keep_fields else {}
@@ -140,7 +157,8 @@ class Server:
         elapsed = clock()
         lat = np.array([r.latency for r in results]) if results else np.zeros(1)
         work = sum(r.n * r.n * r.steps for r in results)
-        stats = {"completed": len(results), "submitted": len(requests), "elapsed_s": elapsed,
+        stats = {"completed": len(results), "failed": len(self.failed), "submitted": len(requests),
+                 "elapsed_s": elapsed,
                  "cell_steps": work, "cell_steps_per_s": work / elapsed if elapsed > 0 else 0.0,
                  "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                  "max_queue": max_queue, "ticks": ticks, "tick_steps": self.tick_steps,

@@ -87,6 +87,7 @@ def test_null_arguments(lib):
     assert lib.fdm_read_stress_planes(None, binding.STRESS_COMPONENTS.index("11"), 0, None, None) == \
         binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_read_stress13_planes(None, 0, None, None) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_batch_sync_status(None, None, None) == binding.FDM_ERR_INVALID_ARG
     lib.fdm_destroy(None)   # NULL-safe
 
 

@@ -105,3 +105,63 @@ def test_served_results_equal_alone_runs():
         ref, info = alone(Params(**{**base.__dict__, "n1": r.n, "n2": r.n, "precision": r.precision}), r.up13, r.steps)
         np.testing.assert_array_equal(by_id[k].up13, ref["up13"])
         assert by_id[k].t == info.t
+
+
+def test_server_retires_failed_requests_and_keeps_the_others():
+    """A request with a non-finite input is refused at admission; one whose simulation
+    leaves the finite range (U13 of 1e308 drives an infinite stress) is retired with
+    FDM_ERR_NONFINITE and its slot freed; every other request completes and equals its solo
+    run, including one admitted into the freed slot afterwards."""
+    n = 32
+    base = coupled(n)
+    good = [inputs.random_up(n, seed=200 + k, ell=6.0) for k in range(3)]
+    nan_in = good[0].copy()
+    nan_in[4, 5] = np.nan
+    blow = np.zeros((n, n))
+    blow[3, 4] = 1e308
+    reqs = [Request(rid=0, n=n, steps=20, precision=B.FP64, arrival=0.0, up13=good[0]),
+            Request(rid=1, n=n, steps=20, precision=B.FP64, arrival=0.0, up13=nan_in),
+            Request(rid=2, n=n, steps=40, precision=B.FP64, arrival=0.0, up13=blow),
+            Request(rid=3, n=n, steps=30, precision=B.FP64, arrival=0.0, up13=good[1]),
+            Request(rid=4, n=n, steps=12, precision=B.FP64, arrival=0.0, up13=good[2])]
+    srv = Server(base, {(n, B.FP64): 2}, hbm_budget=1e9, tick_steps=4)
+    try:
+        results, stats = srv.run(reqs)
+        failed = {r.rid: r.status for r in srv.failed}
+    finally:
+        srv.close()
+    assert failed == {1: B.FDM_ERR_INVALID_ARG, 2: B.FDM_ERR_NONFINITE}
+    assert stats["completed"] == 3 and stats["failed"] == 2
+    by_id = {r.rid: r for r in results}
+    for k, up in ((0, good[0]), (3, good[1]), (4, good[2])):
+        ref, info = alone(base, up, reqs[k].steps)
+        np.testing.assert_array_equal(by_id[k].up13, ref["up13"])
+        assert by_id[k].t == info.t
+
+
+def test_allocation_failures_release_everything():
+    """Host-side fault injection: each allocation of a handle or a batch in turn fails; the
+    call returns FDM_ERR_OOM with no handle and no device memory left behind."""
+    import torch
+    p = coupled(64)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    try:
+        for make in (lambda: FDM(p), lambda: Batch([p, coupled(32, B.MIXED), p])):
+            k, done = 0, False
+            while not done:
+                B.debug_fail_allocation(k)
+                try:
+                    obj = make()
+                except B.FDMError as e:
+                    assert e.status == B.FDM_ERR_OOM
+                    k += 1
+                    continue
+                B.debug_fail_allocation(-1)
+                obj.close()
+                done = True
+            assert k >= 10
+    finally:
+        B.debug_fail_allocation(-1)
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)

@@ -503,6 +503,30 @@ def test_nonfinite_state_reported():
         assert e.value.status == B.FDM_ERR_NONFINITE
 
 
+@pytest.mark.parametrize("precision", [B.FP64, B.DF64, B.MIXED])
+def test_nonfinite_input_rejected_and_state_kept(precision):
+    """A field with a NaN or an infinity is refused (invalid argument) and the state, step
+    and time of the handle stay as they were."""
+    n = 32
+    up0 = inputs.random_up(n, seed=18, ell=4.0)
+    p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_rate=1e-3,
+               cfl=0.4, precision=precision)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        i0 = sim.step(3)
+        before = sim.read_fields("up13")["up13"]
+        for bad in (np.nan, np.inf, -np.inf):
+            u = up0.copy()
+            u[5, 7] = bad
+            with pytest.raises(FDMError) as e:
+                sim.set_plastic_distortion(u)
+            assert e.value.status == B.FDM_ERR_INVALID_ARG
+            np.testing.assert_array_equal(sim.read_fields("up13")["up13"], before)
+            i = sim.info()
+            assert i.step == i0.step == 3 and i.t == i0.t
+        assert sim.step(1).step == 4
+
+
 def test_largest_grid_runs_and_conserves():
     """Maximum size 4096^2 FP64: one coupled step; the total Burgers vector stays 0 and the
     mean stress equals the macroscopic stress."""
