@@ -41,6 +41,9 @@ def lib():
                                               C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), d]
         _lib.oracle_stress_symbol.argtypes = [C.c_int] + [C.c_double] * 5
         _lib.oracle_stress_symbol.restype = C.c_double
+        _lib.oracle_hetero_antiplane.argtypes = [C.c_int, C.c_int, d, d, C.c_int, C.c_double, C.c_double, C.c_int,
+                                                 d, d, d]
+        _lib.oracle_hetero_antiplane.restype = C.c_int
         _lib.oracle_run.restype = C.c_int
     return _lib
 
@@ -235,6 +238,18 @@ def stress_planes(up13, nz, nh, mu, nu, sigma_bar13, comp, planes):
                                STRESS_COMPONENTS.index(comp), len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)),
                                _p(out))
     return out
+
+
+def hetero_antiplane(mu, up13, stress_control, load, tol=0.0, max_iter=50):
+    """Antiplane static problem with a shear modulus field mu(x) (Sec. 3.1.2, heterogeneous
+    medium; plastic layer filling the cell): returns (sigma13, sigma23, iterations, residual).
+    ``load``: sigma_bar13 under stress control, else eps_bar13 (strain control)."""
+    m, u = _f64(mu), _f64(up13)
+    n2, n1 = u.shape
+    s13, s23, r = np.zeros((n2, n1)), np.zeros((n2, n1)), C.c_double(0.0)
+    it = lib().oracle_hetero_antiplane(n1, n2, _p(m), _p(u), int(bool(stress_control)), float(load), float(tol),
+                                       int(max_iter), _p(s13), _p(s23), C.byref(r))
+    return s13, s23, it, r.value
 
 
 def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None):

@@ -726,5 +726,99 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
     return rc;
 }
 
+/*
+ * Heterogeneous elasticity (Sec. 3.1.2, heterogeneous medium): static problem for a shear
+ * modulus mu(x1, x2) that varies in the plane, with the plastic layer filling the cell
+ * (nh = nz).  U^p = U13(x1, x2) e1 (x) e3 then does not vary along x3 and the problem is
+ * antiplane shear: u = u3(x1, x2) e3, unknown g = grad u3, stresses
+ *   sigma13 = mu (g1 - U13),   sigma23 = mu g2,   equilibrium d1 sigma13 + d2 sigma23 = 0.
+ * With a reference medium mu0 the paper's polarisation is tau = (mu - mu0) g - mu (U13, 0) and
+ * sigma = mu0 g + tau, and its series expansion of the solution is summed by the fixed-point
+ * iteration (each iterate adds the next term of the series)
+ *   g <- G - Gamma0 * tau(g),  Gamma0-hat(xi) = xi (x) xi / (mu0 |xi|^2) for xi != 0,
+ * with the odd products xi1 xi2 zeroed at the Nyquist indices (G8), g-hat(0) = G.
+ * Loading: strain control G = (2 eps_bar13, 0); stress control G = ((sigma_bar13 - <tau1>) /
+ * mu0, -<tau2> / mu0), recomputed from each iterate's tau so that <sigma13> = sigma_bar13.
+ * mu0 = (min mu + max mu) / 2; g starts at zero.  Stops when
+ *   rms(g_new - g) <= tol * max(rms(g_new), rms(U13 - <U13>))
+ * or after max_iter iterations (tol = 0: exactly max_iter).  Returns the iterations done;
+ * *res receives the last ratio rms(g_new - g) / max(...).  Outputs [n2][n1].
+ */
+int oracle_hetero_antiplane(int n1, int n2, const double *mu, const double *up13, int stress_control,
+                            double load, double tol, int max_iter, double *sig13, double *sig23, double *res)
+{
+    size_t n = (size_t)n1 * n2;
+    double mmin = mu[0], mmax = mu[0];
+    for (size_t i = 1; i < n; i++) { if (mu[i] < mmin) mmin = mu[i]; if (mu[i] > mmax) mmax = mu[i]; }
+    const double mu0 = 0.5 * (mmin + mmax);
+    double *g1 = calloc(n, sizeof(double)), *g2 = calloc(n, sizeof(double));
+    double *t1r = malloc(sizeof(double) * n), *t1i = malloc(sizeof(double) * n);
+    double *t2r = malloc(sizeof(double) * n), *t2i = malloc(sizeof(double) * n);
+    double umean = oracle_sum(n, up13) / (double)n, urms = 0.0;
+    for (size_t i = 0; i < n; i++) urms += (up13[i] - umean) * (up13[i] - umean);
+    urms = sqrt(urms / (double)n);
+    int it = 0;
+    double r = 0.0;
+    while (it < max_iter) {
+        it++;
+        for (size_t i = 0; i < n; i++) {
+            t1r[i] = (mu[i] - mu0) * g1[i] - mu[i] * up13[i];
+            t2r[i] = (mu[i] - mu0) * g2[i];
+            t1i[i] = 0.0;
+            t2i[i] = 0.0;
+        }
+        oracle_fft2d(n1, n2, t1r, t1i, -1);
+        oracle_fft2d(n1, n2, t2r, t2i, -1);
+        double G1, G2;
+        if (stress_control) {
+            G1 = (load - t1r[0] / (double)n) / mu0;
+            G2 = -(t2r[0] / (double)n) / mu0;
+        } else {
+            G1 = 2.0 * load;
+            G2 = 0.0;
+        }
+        for (int k2 = 0; k2 < n2; k2++) {
+            for (int k1 = 0; k1 < n1; k1++) {
+                size_t i = (size_t)k2 * n1 + k1;
+                if (k1 == 0 && k2 == 0) {
+                    t1r[i] = G1 * (double)n; t1i[i] = 0.0;
+                    t2r[i] = G2 * (double)n; t2i[i] = 0.0;
+                    continue;
+                }
+                double x1 = 2.0 * OR_PI * (double)signed_index(k1, n1) / (double)n1;
+                double x2 = 2.0 * OR_PI * (double)signed_index(k2, n2) / (double)n2;
+                double o1 = (2 * k1 == n1) ? 0.0 : x1, o2 = (2 * k2 == n2) ? 0.0 : x2;
+                double q = mu0 * (x1 * x1 + x2 * x2);
+                double a11 = x1 * x1 / q, a12 = o1 * o2 / q, a22 = x2 * x2 / q;
+                double ar = t1r[i], ai = t1i[i], br = t2r[i], bi = t2i[i];
+                t1r[i] = -(a11 * ar + a12 * br);
+                t1i[i] = -(a11 * ai + a12 * bi);
+                t2r[i] = -(a12 * ar + a22 * br);
+                t2i[i] = -(a12 * ai + a22 * bi);
+            }
+        }
+        oracle_fft2d(n1, n2, t1r, t1i, +1);
+        oracle_fft2d(n1, n2, t2r, t2i, +1);
+        double dd = 0.0, gg = 0.0;
+        for (size_t i = 0; i < n; i++) {
+            double a = t1r[i] / (double)n, b = t2r[i] / (double)n;
+            dd += (a - g1[i]) * (a - g1[i]) + (b - g2[i]) * (b - g2[i]);
+            gg += a * a + b * b;
+            g1[i] = a;
+            g2[i] = b;
+        }
+        double scale = fmax(sqrt(gg / (double)n), urms);
+        r = scale > 0.0 ? sqrt(dd / (double)n) / scale : 0.0;
+        if (tol > 0.0 && r <= tol) break;
+    }
+    for (size_t i = 0; i < n; i++) {
+        if (sig13) sig13[i] = mu[i] * (g1[i] - up13[i]);
+        if (sig23) sig23[i] = mu[i] * g2[i];
+    }
+    if (res) *res = r;
+    free(g1); free(g2); free(t1r); free(t1i); free(t2r); free(t2i);
+    return it;
+}
+
 /* size check used by the wrapper */
 int oracle_valid_size(int n) { return is_pow2(n) && n >= 4; }

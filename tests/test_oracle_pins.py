@@ -735,6 +735,97 @@ def test_energy_never_increases_under_stress_driven_motion(theta, tau_y):
     assert w[-1] < 0.5 * w[0]
 
 
+# ------------------------------------------------------------------ heterogeneous elasticity
+def _smooth_field(n2, n1, seed, lo, hi, ell=3.0):
+    """Seeded smooth field with values spread over [lo, hi] (a test input)."""
+    rng = np.random.default_rng(seed)
+    F = np.fft.fft2(rng.standard_normal((n2, n1)))
+    k2 = np.fft.fftfreq(n2)[:, None] * 2 * np.pi
+    k1 = np.fft.fftfreq(n1)[None, :] * 2 * np.pi
+    f = np.real(np.fft.ifft2(F * np.exp(-(k1 ** 2 + k2 ** 2) * ell ** 2 / 4)))
+    f = (f - f.min()) / (f.max() - f.min())
+    return lo + (hi - lo) * f
+
+
+@pytest.mark.parametrize("stress_control", [True, False])
+def test_hetero_homogeneous_modulus_is_the_layer_solve(stress_control):
+    """mu(x) = mu: the polarisation is -mu U13 alone, one iteration is exact, and the stress
+    is the layer solve of a layer filling the cell (K with nh = nz) and, for 23, the 3-D
+    cell's sigma23 on any plane."""
+    n1, n2, nz = 16, 8, 4
+    mu, nu = 0.37, 0.3
+    up = np.random.default_rng(11).standard_normal((n2, n1))
+    load = 0.02 if stress_control else 3e-3
+    s13, s23, it, r = oracle.hetero_antiplane(np.full((n2, n1), mu), up, stress_control, load, tol=0.0, max_iter=2)
+    sbar = load if stress_control else mu * (2 * load - up.mean())
+    K = oracle.kernel_table(n1, n2, nz, nz, mu, nu)
+    np.testing.assert_allclose(s13, oracle.static_tau(up, K, sbar), atol=1e-13, rtol=0)
+    np.testing.assert_allclose(s23, oracle.stress_planes(up, nz, nz, mu, nu, sbar, "23", [1])[0], atol=1e-13, rtol=0)
+    assert r < 1e-14
+
+
+def test_hetero_laminates_have_closed_forms():
+    """Fields depending on one coordinate only.  Along x1: equilibrium makes sigma13 uniform,
+    g1 = U13 + Sigma / mu, and <g1> = 2 eps_bar13 gives Sigma = (2 eps_bar13 - <U13>) /
+    <1/mu> (harmonic mean); sigma23 = 0.  Along x2: compatibility makes g1 uniform (= 2
+    eps_bar13), so sigma13 = mu (2 eps_bar13 - U13) pointwise, and sigma23 = 0; under stress
+    control g1 = (sigma_bar13 + <mu U13>) / <mu>."""
+    n = 32
+    x = np.arange(n)
+    mu_line = 0.5 + 0.4 * np.sin(2 * np.pi * x / n) ** 2 + 0.1 * (x % 3)
+    u_line = np.cos(2 * np.pi * 3 * x / n) + 0.3 * np.sin(2 * np.pi * x / n)
+    eps = 2e-3
+    mu1, u1 = np.tile(mu_line, (n, 1)), np.tile(u_line, (n, 1))
+    s13, s23, it, r = oracle.hetero_antiplane(mu1, u1, False, eps, tol=1e-15, max_iter=400)
+    sig = (2 * eps - u_line.mean()) / np.mean(1.0 / mu_line)
+    np.testing.assert_allclose(s13, sig, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(s23, 0.0, atol=1e-12)
+    s13, _, _, _ = oracle.hetero_antiplane(mu1, u1, True, 0.05, tol=1e-15, max_iter=400)
+    np.testing.assert_allclose(s13, 0.05, atol=1e-12, rtol=0)
+    mu2, u2 = mu1.T.copy(), u1.T.copy()
+    s13, s23, it, r = oracle.hetero_antiplane(mu2, u2, False, eps, tol=1e-15, max_iter=400)
+    np.testing.assert_allclose(s13, mu2 * (2 * eps - u2), atol=1e-12, rtol=0)
+    np.testing.assert_allclose(s23, 0.0, atol=1e-12)
+    s13, _, _, _ = oracle.hetero_antiplane(mu2, u2, True, 0.05, tol=1e-15, max_iter=400)
+    g1 = (0.05 + np.mean(mu_line * u_line)) / np.mean(mu_line)
+    np.testing.assert_allclose(s13, mu2 * (g1 - u2), atol=1e-12, rtol=0)
+
+
+def test_hetero_solution_is_in_equilibrium_and_compatible():
+    """Random modulus (contrast 4) and plastic field, iterated to convergence: the stress is
+    divergence free and g = (sigma13 / mu + U13, sigma23 / mu) is a gradient (curl g = 0),
+    at every mode off the Nyquist indices; <sigma13> is the prescribed stress."""
+    n1, n2 = 32, 16
+    mu = _smooth_field(n2, n1, 12, 0.25, 1.0)
+    up = _smooth_field(n2, n1, 13, -1.0, 1.0, ell=2.0)
+    s13, s23, it, r = oracle.hetero_antiplane(mu, up, True, 0.03, tol=1e-14, max_iter=500)
+    assert r <= 1e-14 and it < 500
+    assert s13.mean() == pytest.approx(0.03, abs=1e-14)
+    k1 = 2 * np.pi * np.fft.fftfreq(n1)[None, :]
+    k2 = 2 * np.pi * np.fft.fftfreq(n2)[:, None]
+    inner = (np.abs(k1) < np.pi - 1e-9) & (np.abs(k2) < np.pi - 1e-9)
+    div = k1 * np.fft.fft2(s13) + k2 * np.fft.fft2(s23)
+    assert np.abs(div[inner]).max() < 1e-11 * np.abs(np.fft.fft2(s13)).max()
+    g1, g2 = s13 / mu + up, s23 / mu
+    curl = k1 * np.fft.fft2(g2) - k2 * np.fft.fft2(g1)
+    assert np.abs(curl[inner]).max() < 1e-11 * np.abs(np.fft.fft2(g1)).max()
+    assert np.abs(s23).max() > 1e-2
+
+
+def test_hetero_iteration_contracts_at_the_basic_scheme_rate():
+    """Successive increments of the fixed-point iteration shrink at least by the factor
+    (kappa - 1) / (kappa + 1) of the reference medium mu0 = (min + max) / 2, kappa = max / min
+    (a dropped or mis-signed polarisation term stalls or diverges)."""
+    n = 32
+    mu = _smooth_field(n, n, 14, 0.2, 1.0)
+    up = _smooth_field(n, n, 15, -1.0, 1.0, ell=2.0)
+    rho = (1.0 - 0.2) / (1.0 + 0.2)
+    res = [oracle.hetero_antiplane(mu, up, False, 1e-3, tol=0.0, max_iter=k)[3] for k in range(2, 12)]
+    for a, b in zip(res, res[1:]):
+        assert b <= rho * a * (1 + 1e-9)
+    assert res[-1] < 0.05 * res[0]
+
+
 # --------------------------------------------------------------------------- paper's numbers
 def test_nondimensional_numbers_printed_in_paper():
     g = json.load(open(os.path.join(GOLDEN, "paper_nondimensional.json")))
