@@ -336,11 +336,41 @@ def run_ours(args, world, rank, local):
             "ours_ms": {p_: round(sum(v["phase_ms"][k_] for k_ in PHASES[:3]), 5) for p_, v in extra.items()},
             "cufft_ms": {"fp64": round(cufft_static_solve_ms(n, torch.float64), 5),
                          "mixed": round(cufft_static_solve_ms(n, torch.float32), 5)}}
+        # the mixed path's iterates stop improving at FP32 rounding (~1e-7)
+        line["hetero_static"] = {"fp64": hetero_static(n, "fp64", tol=1e-12),
+                                 "mixed": hetero_static(n, "mixed", tol=1e-6)}
         if args.cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     for rr in results.values():
         rr["sim"].close()
+
+
+def hetero_static(n, precision, tol=1e-12, contrast=4.0):
+    """Heterogeneous static problem (shear-modulus field of the given contrast, plastic layer
+    filling the cell, stress control) on the n x n random field: iterations to the tolerance
+    and wall time of one converged solve through the public call (after one untimed solve).
+    One iteration moves 32 field words per cell, 33 with the mixed path's low words
+    (polarisation 6, four transforms 16, Green operator 4, update 6): 256 B in FP64."""
+    import torch
+    from paper_1911_03225_gb300 import FDM, inputs
+    from paper_1911_03225_gb300 import binding as B
+    p = B.Params(n1=n, n2=n, nz=8, nh=8, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.01,
+                 precision={"fp64": B.FP64, "mixed": B.MIXED}[precision])
+    up0 = inputs.random_up(n, seed=0, ell=16.0, rms_alpha=0.1)
+    f = inputs.modulus_factor(n, n, seed=1, lo=1.0 / contrast, hi=1.0, ell=24.0)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve_heterogeneous(f, tol=tol, max_iter=400)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, it, res = sim.static_solve_heterogeneous(f, tol=tol, max_iter=400)
+        ms = (time.perf_counter() - t0) * 1e3
+    bpc = 8 * 32 if precision == "fp64" else 4 * 33
+    return {"n": n, "contrast": contrast, "tol": tol, "iterations": it,
+            "residual": res, "ms": round(ms, 3), "ms_per_iteration": round(ms / it, 4),
+            "bytes_per_cell_iteration": bpc,
+            "achieved_GBs": round(float(bpc) * n * n * it / (ms / 1e3) / 1e9, 1)}
 
 
 def cufft_static_solve_ms(n, dtype, reps=20):

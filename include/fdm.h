@@ -209,6 +209,27 @@ int32_t fdm_kernels_per_step(const fdm_handle *h);
  * applied by the static-solve kernels.  Leaves the state and its scalars unchanged. */
 fdm_status fdm_read_stress13_planes(fdm_handle *h, int32_t nplanes, const int32_t *planes, double *out);
 
+/* Heterogeneous elasticity (Sec. 3.1.2, heterogeneous medium) for a plastic layer filling
+ * the cell (p.nh == p.nz, else FDM_ERR_INVALID_ARG): U^p = U13(x1, x2) e1 (x) e3 is then
+ * uniform along x3 and the static problem is antiplane shear in a medium of shear modulus
+ * mu(x) = mu * mu_factor[x] (mu = E / (2 (1 + nu)); mu_factor host [n2][n1], every entry
+ * finite and > 0).  Unknown g = grad u3; sigma13 = mu(x) (g1 - U13), sigma23 = mu(x) g2.
+ * With the reference medium mu0 = (min mu + max mu) / 2 the polarisation is
+ * tau = (mu - mu0) g - mu (U13, 0), and the paper's series expansion is summed by the
+ * fixed-point iteration g <- G - Gamma0 * tau(g), Gamma0-hat(xi) = xi (x) xi / (mu0 |xi|^2)
+ * (odd products xi1 xi2 zeroed at Nyquist indices), g-hat(0) = G, starting from g = 0.
+ * Loading of the current step: FDM_LOAD_STRESS and FDM_LOAD_ZERO_MEAN_STRESS prescribe
+ * <sigma13> (G follows from each iterate's <tau>); the strain modes prescribe
+ * <g1> = 2 eps_bar13, <g2> = 0.  Stops when rms(g_new - g) <= tol max(rms(g_new),
+ * rms(U13 - <U13>)) or after max_iter (>= 1) iterations; tol = 0 runs exactly max_iter.
+ * Writes sigma13 to the handle's tau13 (fdm_read_fields) and, when not NULL, to the host
+ * arrays sigma13 and sigma23 ([n2][n1] float64); iterations and residual (nullable) receive
+ * the count and the last ratio.  The state is unchanged; FDM_ERR_STATE without a state or
+ * during a step, FDM_ERR_NONFINITE if the iteration diverges. */
+fdm_status fdm_static_solve_heterogeneous(fdm_handle *h, const double *mu_factor, double tol, int32_t max_iter,
+                                          double *sigma13, double *sigma23, int32_t *iterations,
+                                          double *residual);
+
 /* Stress components, Voigt order. */
 enum { FDM_S11 = 0, FDM_S22 = 1, FDM_S33 = 2, FDM_S23 = 3, FDM_S13 = 4, FDM_S12 = 5 };
 

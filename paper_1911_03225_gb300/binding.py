@@ -48,7 +48,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
-           "fdm_debug_fail_allocation"]
+           "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous"]
 
 
 class CParams(C.Structure):
@@ -179,6 +179,9 @@ def load():
     lib.fdm_batch_sync.argtypes = [H, C.POINTER(C.c_int64)]
     lib.fdm_batch_sync_status.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     lib.fdm_batch_sync_status.restype = C.c_int
+    lib.fdm_static_solve_heterogeneous.argtypes = [H, d, C.c_double, C.c_int32, d, d, C.POINTER(C.c_int32),
+                                                   C.POINTER(C.c_double)]
+    lib.fdm_static_solve_heterogeneous.restype = C.c_int
     lib.fdm_debug_fail_allocation.argtypes = [C.c_int32]
     lib.fdm_debug_fail_allocation.restype = None
     lib.fdm_batch_get_info.argtypes = [H, C.c_int32, C.POINTER(CStepInfo)]
@@ -323,6 +326,18 @@ class FDM:
         _check(self.lib.fdm_read_stress13_planes(self.h, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int32)),
                                                  _dptr(out)), "fdm_read_stress13_planes")
         return out
+
+    def static_solve_heterogeneous(self, mu_factor, tol: float = 1e-12, max_iter: int = 200):
+        """Antiplane static problem with the shear modulus mu * mu_factor(x) (heterogeneous
+        medium, Sec. 3.1.2; needs nh == nz).  Returns (sigma13, sigma23, iterations, residual);
+        sigma13 also becomes the handle's tau13."""
+        f = _field(mu_factor, self.shape)
+        s13, s23 = np.empty(self.shape), np.empty(self.shape)
+        it, r = C.c_int32(0), C.c_double(0.0)
+        _check(self.lib.fdm_static_solve_heterogeneous(self.h, _dptr(f), float(tol), int(max_iter), _dptr(s13),
+                                                       _dptr(s23), C.byref(it), C.byref(r)),
+               "fdm_static_solve_heterogeneous")
+        return s13, s23, it.value, r.value
 
     def read_stress_planes(self, comp, planes) -> np.ndarray:
         """Stress component ``comp`` ("11", "22", "33", "23", "13", "12" or its Voigt index) of

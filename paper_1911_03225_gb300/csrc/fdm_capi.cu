@@ -327,6 +327,7 @@ struct fdm_handle {
     void* rd[4];             // readout buffers (type T, n each), allocated on first use
     void* mfac_buf;          // mobility factor (type T, n), allocated on first use
     void* plane_buf[5];      // stress planes: FP64 table, table in T, k3 weights, output in T, scalars
+    HeteroBuffers hetero;    // heterogeneous static problem, allocated on first use
     Dev rd64;                // mixed precision: FP64 spectra and tables for the Nye readout
     void* rd64_buf[3];       //   U13 and the two Nye components in FP64 (n each)
 };
@@ -720,6 +721,47 @@ static fdm_status read_stress_planes(fdm_handle* h, int32_t comp, int32_t nplane
         if ((st = download_field(host.data(), h->plane_buf[3], h->n, h->prec, 0.0, h->stream))) return st;
         std::memcpy(out + (size_t)k * h->n, host.data(), h->n * sizeof(double));
     }
+    return FDM_OK;
+}
+
+fdm_status fdm_static_solve_heterogeneous(fdm_handle* h, const double* mu_factor, double tol, int32_t max_iter,
+                                          double* sigma13, double* sigma23, int32_t* iterations, double* residual) {
+    if (!h || !mu_factor || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1) return FDM_ERR_INVALID_ARG;
+    const fdm_params& p = h->d.p;
+    if (p.nh != p.nz) return FDM_ERR_INVALID_ARG;
+    const size_t n = h->n;
+    const double mu = p.E / (2.0 * (1.0 + p.nu));
+    std::vector<double> m(n);
+    double mmin = HUGE_VAL, mmax = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!(mu_factor[i] > 0.0) || !std::isfinite(mu_factor[i])) return FDM_ERR_INVALID_ARG;
+        m[i] = mu * mu_factor[i];
+        mmin = std::fmin(mmin, m[i]);
+        mmax = std::fmax(mmax, m[i]);
+    }
+    if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
+    fdm_status st;
+    const size_t bytes = n * elt_size(&p);
+    void** bufs[5] = {&h->hetero.mu, &h->hetero.g1, &h->hetero.g2, &h->hetero.t1, &h->hetero.t2};
+    for (void** b : bufs)
+        if (!*b && (st = h->arena.alloc(b, bytes))) return st;
+    if ((st = upload_field(h->hetero.mu, m.data(), n, h->prec, 0.0, h->stream))) return st;
+    // the loading of the current step: sigma_bar13 (stress, zero mean stress) or eps_bar13
+    fdm_dev_scalars s;
+    if ((st = read_scalars(h, &s))) return st;
+    double eps = 0.0, sig = 0.0;
+    host_loading(p, s.step, s.t, s.mean_up13, &eps, &sig);
+    const bool stress = p.loading_mode == FDM_LOAD_STRESS || p.loading_mode == FDM_LOAD_ZERO_MEAN_STRESS;
+    int it = 0;
+    double r = 0.0;
+    FDM_DISPATCH(h->prec, st = hetero_solve<T>(h->d, h->hetero, 0.5 * (mmin + mmax), stress, stress ? sig : eps, tol,
+                                               max_iter, h->stream, &it, &r));
+    if (st) return st;
+    if (sigma13 && (st = download_field(sigma13, h->d.tau, n, h->prec, 0.0, h->stream))) return st;
+    if (sigma23 && (st = download_field(sigma23, h->hetero.t2, n, h->prec, 0.0, h->stream))) return st;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    if (iterations) *iterations = it;
+    if (residual) *residual = r;
     return FDM_OK;
 }
 

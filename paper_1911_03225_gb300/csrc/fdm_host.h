@@ -185,6 +185,18 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
 // Uploads a host FP64 field into a device buffer of precision `prec` (FDM_FP64, FDM_MIXED,
 // FDM_DF64), minus offset / downloads it, adding offset back.
 fdm_status upload_field(void* dst, const double* src, size_t n, int prec, double offset, cudaStream_t s);
+
+// Heterogeneous antiplane static problem (fdm_hetero.cu): device fields of type T, n each:
+// the shear modulus, the iterate g (two components) and two work fields.
+struct HeteroBuffers {
+    void *mu, *g1, *g2, *t1, *t2;
+};
+// Runs the fixed-point iteration for the current state of the single-instance group d and
+// writes sigma13 to d.tau and sigma23 to hb.t2.  stress_control: load = sigma_bar13, else
+// load = eps_bar13.  tol = 0 runs exactly max_iter iterations.
+template <typename T>
+fdm_status hetero_solve(const Dev& d, const HeteroBuffers& hb, double mu0, bool stress_control, double load,
+                        double tol, int max_iter, cudaStream_t s, int* iterations, double* residual);
 fdm_status download_field(double* dst, const void* src, size_t n, int prec, double offset, cudaStream_t s);
 // U13 of instance `inst` in state buffer b, from / to host doubles (minus / plus `offset`);
 // FDM_MIXED stores FP32 pairs: hi = fl(v), lo = fl(v - hi)

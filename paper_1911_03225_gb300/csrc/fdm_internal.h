@@ -84,6 +84,9 @@ template <typename T> void launch_static_to(const Dev& d, T* dst, cudaStream_t s
 // stress component comp (Voigt order 11, 22, 33, 23, 13, 12; not 13, which takes
 // launch_static_to with its macroscopic stress) with the plane table in d.Kh
 template <typename T> void launch_stress_to(const Dev& d, int comp, T* dst, cudaStream_t s);
+// unnormalised 2-D transforms of one real field (packed transposed spectrum of n/2 complex)
+template <typename T> void launch_fft_forward(const Dev& d, const T* src, void* spec, cudaStream_t s);
+template <typename T> void launch_fft_inverse(const Dev& d, void* spec, T* dst, cudaStream_t s);
 template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);
 template <typename T>
 void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, double mean_up13, double phi_ref,

@@ -1062,6 +1062,21 @@ void launch_stress_to(const Dev& d, int comp, T* dst, cudaStream_t s) {
     launch_row_inverse<T>(d, (const cpx<T>*)d.spec, dst, ROW_PLAIN, 0.0, 1, s);
 }
 
+// 2-D transform of one real field (single instance) for solvers outside the step: rows then
+// columns, unnormalised, into the packed transposed spectrum; and back (spec is overwritten;
+// dst must not alias it)
+template <typename T>
+void launch_fft_forward(const Dev& d, const T* src, void* spec, cudaStream_t s) {
+    InstCtl none{nullptr, 0};
+    launch_row_forward<T>(d, src, src, (cpx<T>*)spec, nullptr, none, 1, s);
+    launch_col<T>(d, (const cpx<T>*)spec, (cpx<T>*)spec, COL_FWD, false, 1, s);
+}
+template <typename T>
+void launch_fft_inverse(const Dev& d, void* spec, T* dst, cudaStream_t s) {
+    launch_col<T>(d, (const cpx<T>*)spec, (cpx<T>*)spec, COL_INV, false, 1, s);
+    launch_row_inverse<T>(d, (const cpx<T>*)spec, dst, ROW_PLAIN, 0.0, 1, s);
+}
+
 // static solve only: tau for the current state of every instance
 template <typename T>
 void launch_static(const Dev& d, cudaStream_t s) {
@@ -1153,6 +1168,8 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_static<T>(const Dev&, cudaStream_t);                                               \
     template void launch_static_to<T>(const Dev&, T*, cudaStream_t);                                        \
     template void launch_stress_to<T>(const Dev&, int, T*, cudaStream_t);                                   \
+    template void launch_fft_forward<T>(const Dev&, const T*, void*, cudaStream_t);                         \
+    template void launch_fft_inverse<T>(const Dev&, void*, T*, cudaStream_t);                               \
     template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \
                                          cudaStream_t);                                                     \

@@ -9,6 +9,8 @@ only closed-form or filtered initial data:
   Gaussian cross-sections in place of the half-square waves;
 * ``ring_alpha`` / ``ring_up``: a smooth circular loop (Sec. 4.4.1), tangent-oriented
   Nye vector with a Gaussian cross-section, U13 = integral of the profile;
+* ``modulus_factor``: a smooth random shear-modulus factor for the heterogeneous static
+  problem;
 * ``random_up``: a zero-mean Gaussian random U13 field (Sec. 5.4 microstructure B) from a
   counter-based generator (SplitMix64, Steele-Lea-Flood 2014, and the Box-Muller
   transform), smoothed by a Gaussian filter exp(-|xi|^2 l^2 / 4) and scaled to a target
@@ -133,3 +135,16 @@ def random_up(n: int, seed: int = 0, ell: float = 16.0, rms_alpha: float = 0.1, 
     g2 = np.sum(q * np.abs(zh) ** 2) / float(n * n) ** 2
     u *= rms_alpha / math.sqrt(g2)
     return u - u.mean()
+
+
+def modulus_factor(n1: int, n2: int, seed: int = 0, lo: float = 0.25, hi: float = 1.0, ell: float = 16.0):
+    """Smooth random factor of the shear modulus with values spread over [lo, hi] (contrast
+    hi / lo), for the heterogeneous static problem: the counter-based normals of
+    ``normal_field`` smoothed by exp(-|xi|^2 l^2 / 4) and mapped affinely onto [lo, hi]."""
+    z = normal_field(n1, n2, seed)
+    k1 = np.fft.fftfreq(n1) * 2.0 * math.pi
+    k2 = np.fft.fftfreq(n2) * 2.0 * math.pi
+    q = k1[None, :] ** 2 + k2[:, None] ** 2
+    f = np.real(np.fft.ifft2(np.fft.fft2(z) * np.exp(-q * ell ** 2 / 4.0)))
+    f = (f - f.min()) / (f.max() - f.min())
+    return lo + (hi - lo) * f

@@ -1,0 +1,117 @@
+"""Heterogeneous elasticity (Sec. 3.1.2, heterogeneous medium) for a plastic layer filling the
+cell: the GPU fixed-point iteration against the oracle's, iterate for iterate, in every
+precision and loading mode; the homogeneous limit against the layer solve; convergence and
+equilibrium at 1024^2."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_03225_gb300 import FDM, FDMError, Params, inputs
+from paper_1911_03225_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+MU = 1 / 2.6   # E = 1, nu = 0.3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def modulus_factor(n2, n1, seed, lo=0.25, hi=1.0, ell=3.0):
+    rng = np.random.default_rng(seed)
+    F = np.fft.fft2(rng.standard_normal((n2, n1)))
+    k2 = np.fft.fftfreq(n2)[:, None] * 2 * np.pi
+    k1 = np.fft.fftfreq(n1)[None, :] * 2 * np.pi
+    f = np.real(np.fft.ifft2(F * np.exp(-(k1 ** 2 + k2 ** 2) * ell ** 2 / 4)))
+    f = (f - f.min()) / (f.max() - f.min())
+    return lo + (hi - lo) * f
+
+
+def params(n1, n2, precision, stress):
+    if stress:
+        return Params(n1=n1, n2=n2, nz=8, nh=8, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS,
+                      sigma_bar13=0.02, precision=precision)
+    return Params(n1=n1, n2=n2, nz=8, nh=8, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRAIN_RAMP,
+                  eps_bar13_0=1e-3, eps_bar13_rate=1e-4, precision=precision)
+
+
+@pytest.mark.parametrize("precision,tol", [(B.FP64, 1e-11), (B.DF64, 1e-11), (B.MIXED, 1e-5)])
+@pytest.mark.parametrize("stress", [True, False])
+def test_hetero_iterates_match_oracle(precision, tol, stress):
+    """25 iterations exactly (tolerance 0) on a 64 x 32 grid, modulus contrast 4, random
+    plastic field with Nyquist content."""
+    n1, n2 = 64, 32
+    up0 = inputs.random_up(64, seed=19, ell=4.0)[:n2, :n1].copy()
+    f = modulus_factor(n2, n1, 20)
+    with FDM(params(n1, n2, precision, stress)) as sim:
+        sim.set_plastic_distortion(up0)
+        s13, s23, it, r = sim.static_solve_heterogeneous(f, tol=0.0, max_iter=25)
+        tau = sim.read_fields("tau13")["tau13"]
+        assert sim.info().step == 0
+    load = 0.02 if stress else 1e-3
+    o13, o23, oit, orr = oracle.hetero_antiplane(MU * f, up0, stress, load, tol=0.0, max_iter=25)
+    assert it == oit == 25
+    assert rel(s13, o13) < tol and rel(s23, o23) < tol
+    if precision == B.MIXED:
+        assert r < 1e-5   # the last increment is below FP32 rounding of the field
+    else:
+        assert r == pytest.approx(orr, rel=1e-8)
+    np.testing.assert_array_equal(tau, s13)
+
+
+def test_hetero_homogeneous_modulus_is_the_layer_solve():
+    n = 64
+    up0 = inputs.random_up(n, seed=21, ell=4.0)
+    with FDM(params(n, n, B.FP64, True)) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve()
+        tau = sim.read_fields("tau13")["tau13"]
+        s13, s23, it, r = sim.static_solve_heterogeneous(np.ones((n, n)), tol=1e-14, max_iter=5)
+    assert it <= 2 and r <= 1e-14
+    assert rel(s13, tau) < 1e-13
+
+
+def test_hetero_converges_at_scale_and_is_in_equilibrium():
+    """1024^2, contrast 4, stress control: converged to 1e-12 within the basic scheme's rate
+    ((kappa - 1)/(kappa + 1) = 0.6 per iteration); the returned stress is divergence free off
+    the Nyquist indices and its mean is the prescribed stress."""
+    n = 1024
+    up0 = inputs.random_up(n, seed=22, ell=16.0)
+    f = modulus_factor(n, n, 23, ell=24.0)
+    with FDM(params(n, n, B.FP64, True)) as sim:
+        sim.set_plastic_distortion(up0)
+        s13, s23, it, r = sim.static_solve_heterogeneous(f, tol=1e-12, max_iter=200)
+    assert r <= 1e-12 and it <= 80
+    assert s13.mean() == pytest.approx(0.02, abs=1e-12)
+    k1 = 2 * np.pi * np.fft.fftfreq(n)[None, :]
+    k2 = 2 * np.pi * np.fft.fftfreq(n)[:, None]
+    inner = (np.abs(k1) < np.pi - 1e-9) & (np.abs(k2) < np.pi - 1e-9)
+    S13 = np.fft.fft2(s13)
+    div = k1 * S13 + k2 * np.fft.fft2(s23)
+    assert np.abs(div[inner]).max() < 1e-9 * np.abs(S13).max()
+
+
+def test_hetero_invalid_arguments():
+    n = 32
+    with FDM(Params(n1=n, n2=n, nz=32, nh=4)) as sim:   # layer thinner than the cell
+        sim.set_plastic_distortion(np.zeros((n, n)))
+        with pytest.raises(FDMError) as e:
+            sim.static_solve_heterogeneous(np.ones((n, n)))
+        assert e.value.status == B.FDM_ERR_INVALID_ARG
+    with FDM(params(n, n, B.FP64, True)) as sim:
+        sim.set_plastic_distortion(np.zeros((n, n)))
+        bad = np.ones((n, n))
+        bad[3, 3] = 0.0
+        with pytest.raises(FDMError) as e:
+            sim.static_solve_heterogeneous(bad)
+        assert e.value.status == B.FDM_ERR_INVALID_ARG
