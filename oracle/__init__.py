@@ -45,6 +45,8 @@ def lib():
                                                  d, d, d]
         _lib.oracle_hetero_antiplane.restype = C.c_int
         _lib.oracle_run.restype = C.c_int
+        _lib.oracle_run_hetero.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d, d, C.c_double, C.c_int]
+        _lib.oracle_run_hetero.restype = C.c_int
     return _lib
 
 
@@ -252,10 +254,14 @@ def hetero_antiplane(mu, up13, stress_control, load, tol=0.0, max_iter=50):
     return s13, s23, it, r.value
 
 
-def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None):
+def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None, shear_modulus=None,
+        hetero_tol=0.0, hetero_max_iter=50):
     """Advance ``nsteps`` FDM steps (Sec. 3.1.1) from ``up13`` (or ``state``).
     ``mobility_factor``: optional per-node m(x) >= 0 multiplying the celerity
-    (heterogeneous drag, m = 0 in impenetrable precipitates; Sec. 5.3)."""
+    (heterogeneous drag, m = 0 in impenetrable precipitates; Sec. 5.3).
+    ``shear_modulus``: optional field mu(x) (heterogeneous elasticity, layer filling the
+    cell): each step's static problem is then ``hetero_antiplane`` with ``hetero_tol`` and
+    ``hetero_max_iter``."""
     p = params._c()
     if K is None:
         K = kernel_table(p.n1, p.n2, p.nz, p.nh, params.mu, params.nu)
@@ -270,8 +276,12 @@ def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_fact
     mf = None if mobility_factor is None else _f64(mobility_factor)
     if mf is not None and mf.shape != u.shape:
         raise ValueError("mobility factor must have the field's shape")
-    rc = lib().oracle_run(C.byref(p), _p(_f64(K)), _p(u), C.byref(sc), int(nsteps), _p(tau), _p(v0),
-                          None if mf is None else _p(mf))
+    mu = None if shear_modulus is None else _f64(shear_modulus)
+    if mu is not None and mu.shape != u.shape:
+        raise ValueError("shear modulus must have the field's shape")
+    rc = lib().oracle_run_hetero(C.byref(p), _p(_f64(K)), _p(u), C.byref(sc), int(nsteps), _p(tau), _p(v0),
+                                 None if mf is None else _p(mf), None if mu is None else _p(mu), float(hetero_tol),
+                                 int(hetero_max_iter))
     return State(up13=u, step=sc.step, t=sc.t, dt=sc.dt, max_abs_v0=sc.max_abs_v0,
                  mean_up13=sc.mean_up13, eps_bar13=sc.eps_bar13, sigma_bar13=sc.sigma_bar13,
                  tau13=tau, v0=v0), rc

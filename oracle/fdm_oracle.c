@@ -660,8 +660,29 @@ static void loading(const oracle_params *p, int64_t step, double t, double mean_
  * eta(x) = eta~ / m(x), with m = 0 inside impenetrable precipitates (Sec. 5.3, Orowan
  * mechanism).  Returns 0, or 1 if a non-finite value appeared.
  */
-int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_scalars *st,
-               int nsteps, double *tau_out, double *v0_out, const double *mfac)
+int oracle_hetero_antiplane(int n1, int n2, const double *mu, const double *up13, int stress_control,
+                            double load, double tol, int max_iter, double *sig13, double *sig23, double *res);
+
+/* Static problem of one step: the layer solve with K, or, with a shear-modulus field mu, the
+ * heterogeneous antiplane problem (stress control in loading modes 0 and 2, strain control
+ * in modes 1 and 3). */
+static void static_problem(const oracle_params *p, const double *K, const double *mu, double tol, int max_iter,
+                           const double *up13, double eps, double sig, double *tau)
+{
+    if (!mu) {
+        oracle_static_tau(p->n1, p->n2, up13, K, sig, tau);
+        return;
+    }
+    int stress = p->loading_mode == 0 || p->loading_mode == 2;
+    oracle_hetero_antiplane(p->n1, p->n2, mu, up13, stress, stress ? sig : eps, tol, max_iter, tau, NULL, NULL);
+}
+
+/* oracle_run with, when mu != NULL, the heterogeneous static problem of a shear-modulus
+ * field mu (layer filling the cell) in every step, iterated as oracle_hetero_antiplane
+ * with tol and max_iter. */
+int oracle_run_hetero(const oracle_params *p, const double *K, double *up13, oracle_scalars *st,
+                      int nsteps, double *tau_out, double *v0_out, const double *mfac,
+                      const double *mu, double tol, int max_iter)
 {
     int n1 = p->n1, n2 = p->n2;
     size_t n = (size_t)n1 * n2;
@@ -673,7 +694,7 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
         double eps, sig;
         loading(p, st->step, st->t, mean, &eps, &sig);
         /* static problem with the previous plastic distortion (Sec. 3.1.1) */
-        oracle_static_tau(n1, n2, up13, K, sig, tau);
+        static_problem(p, K, mu, tol, max_iter, up13, eps, sig, tau);
         /* celerity (Sec. 3.2.3 Hamiltonian; Sec. 4.1 prescribed) */
         double vmax = 0.0;
         for (size_t i = 0; i < n; i++) {
@@ -711,7 +732,7 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
     if (nsteps == 0) {
         double mean = oracle_sum(n, up13) / (double)n, eps, sig;
         loading(p, st->step, st->t, mean, &eps, &sig);
-        oracle_static_tau(n1, n2, up13, K, sig, tau);
+        static_problem(p, K, mu, tol, max_iter, up13, eps, sig, tau);
         for (size_t i = 0; i < n; i++) {
             double fr = (p->tau_y != 0.0) ? p->tau_y * cos(up13[i] / p->beta) : 0.0;
             v0[i] = (p->velocity_mode == 0) ? p->v0 : p->mobility * (fr - tau[i]);
@@ -724,6 +745,12 @@ int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_sca
     if (v0_out) memcpy(v0_out, v0, sizeof(double) * n);
     free(tau); free(v0); free(nxt);
     return rc;
+}
+
+int oracle_run(const oracle_params *p, const double *K, double *up13, oracle_scalars *st,
+               int nsteps, double *tau_out, double *v0_out, const double *mfac)
+{
+    return oracle_run_hetero(p, K, up13, st, nsteps, tau_out, v0_out, mfac, NULL, 0.0, 0);
 }
 
 /*

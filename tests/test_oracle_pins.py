@@ -826,6 +826,41 @@ def test_hetero_iteration_contracts_at_the_basic_scheme_rate():
     assert res[-1] < 0.05 * res[0]
 
 
+def test_hetero_steps_with_uniform_modulus_are_the_layer_steps():
+    """A uniform modulus field in the time loop reproduces the layer solve with nh = nz."""
+    n = 32
+    up0 = inputs.random_up(n, seed=16, ell=4.0)
+    p = oracle.Params(n1=n, n2=n, nz=8, nh=8, velocity_mode=1, loading_mode=1, eps_bar13_rate=1e-3, cfl=0.4)
+    a, _ = oracle.run(p, up0, 6)
+    b, _ = oracle.run(p, up0, 6, shear_modulus=np.full((n, n), p.mu), hetero_tol=1e-15, hetero_max_iter=5)
+    assert np.abs(b.up13 - a.up13).max() < 1e-12 * np.abs(a.up13).max()
+    assert b.t == pytest.approx(a.t, rel=1e-12)
+
+
+def test_hetero_steps_never_increase_the_stored_energy():
+    """Heterogeneous modulus, zero macroscopic stress, stress-driven motion: the stored energy
+    1/2 sum (sigma13^2 + sigma23^2) / mu (the minimum over compatible g of the elastic energy,
+    whose derivative in U13 is -sigma13) never increases along the steps."""
+    n = 32
+    up0 = inputs.random_up(n, seed=17, ell=4.0)
+    mu = _smooth_field(n, n, 18, 0.1, 0.4)
+    p = oracle.Params(n1=n, n2=n, nz=8, nh=8, velocity_mode=1, loading_mode=0, sigma_bar13=0.0, cfl=0.4)
+    K = oracle.kernel_table(n, n, 8, 8, p.mu, p.nu)
+
+    def energy(u):
+        s13, s23, _, _ = oracle.hetero_antiplane(mu, u, True, 0.0, tol=1e-14, max_iter=500)
+        return 0.5 * np.sum((s13 ** 2 + s23 ** 2) / mu)
+
+    st, _ = oracle.run(p, up0, 0, K=K, shear_modulus=mu, hetero_tol=1e-14, hetero_max_iter=500)
+    w = [energy(up0)]
+    for _ in range(15):
+        st, rc = oracle.run(p, up0, 1, K=K, state=st, shear_modulus=mu, hetero_tol=1e-14, hetero_max_iter=500)
+        assert rc == 0
+        w.append(energy(st.up13))
+    assert (np.diff(w) < 0).all()
+    assert w[-1] < 0.8 * w[0]
+
+
 # --------------------------------------------------------------------------- paper's numbers
 def test_nondimensional_numbers_printed_in_paper():
     g = json.load(open(os.path.join(GOLDEN, "paper_nondimensional.json")))
