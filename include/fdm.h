@@ -230,6 +230,17 @@ fdm_status fdm_static_solve_heterogeneous(fdm_handle *h, const double *mu_factor
                                           double *sigma13, double *sigma23, int32_t *iterations,
                                           double *residual);
 
+/* Time steps with heterogeneous elasticity: mu_factor (host [n2][n1], as for
+ * fdm_static_solve_heterogeneous; requires nh == nz) becomes the shear-modulus field of every
+ * later fdm_static_solve and step of the handle, whose static problem is then the
+ * fixed-point iteration above with tol and max_iter; the step's dt follows the resulting
+ * max |v0| (Sec. 5.2) and the transport is unchanged.  The iteration's stopping test runs on
+ * the host, so fdm_step and fdm_enqueue_steps return when their steps are done and
+ * fdm_enqueue_phase is refused (FDM_ERR_STATE).  mu_factor NULL returns to the layer solve.
+ * A later fdm_static_solve_heterogeneous replaces the field.  Errors as
+ * fdm_static_solve_heterogeneous; FDM_ERR_STATE during a step. */
+fdm_status fdm_set_shear_modulus_field(fdm_handle *h, const double *mu_factor, double tol, int32_t max_iter);
+
 /* Stress components, Voigt order. */
 enum { FDM_S11 = 0, FDM_S22 = 1, FDM_S33 = 2, FDM_S23 = 3, FDM_S13 = 4, FDM_S12 = 5 };
 

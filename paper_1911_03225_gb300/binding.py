@@ -48,7 +48,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
-           "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous"]
+           "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field"]
 
 
 class CParams(C.Structure):
@@ -182,6 +182,8 @@ def load():
     lib.fdm_static_solve_heterogeneous.argtypes = [H, d, C.c_double, C.c_int32, d, d, C.POINTER(C.c_int32),
                                                    C.POINTER(C.c_double)]
     lib.fdm_static_solve_heterogeneous.restype = C.c_int
+    lib.fdm_set_shear_modulus_field.argtypes = [H, d, C.c_double, C.c_int32]
+    lib.fdm_set_shear_modulus_field.restype = C.c_int
     lib.fdm_debug_fail_allocation.argtypes = [C.c_int32]
     lib.fdm_debug_fail_allocation.restype = None
     lib.fdm_batch_get_info.argtypes = [H, C.c_int32, C.POINTER(CStepInfo)]
@@ -338,6 +340,16 @@ class FDM:
                                                        _dptr(s23), C.byref(it), C.byref(r)),
                "fdm_static_solve_heterogeneous")
         return s13, s23, it.value, r.value
+
+    def set_shear_modulus_field(self, mu_factor=None, tol: float = 1e-12, max_iter: int = 200):
+        """Heterogeneous elasticity in every later static solve and step: shear modulus
+        mu * mu_factor(x) (needs nh == nz); None returns to the layer solve."""
+        if mu_factor is None:
+            _check(self.lib.fdm_set_shear_modulus_field(self.h, None, 0.0, 1), "fdm_set_shear_modulus_field")
+            return
+        f = _field(mu_factor, self.shape)
+        _check(self.lib.fdm_set_shear_modulus_field(self.h, _dptr(f), float(tol), int(max_iter)),
+               "fdm_set_shear_modulus_field")
 
     def read_stress_planes(self, comp, planes) -> np.ndarray:
         """Stress component ``comp`` ("11", "22", "33", "23", "13", "12" or its Voigt index) of

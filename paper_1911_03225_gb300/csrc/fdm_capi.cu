@@ -328,6 +328,9 @@ struct fdm_handle {
     void* mfac_buf;          // mobility factor (type T, n), allocated on first use
     void* plane_buf[5];      // stress planes: FP64 table, table in T, k3 weights, output in T, scalars
     HeteroBuffers hetero;    // heterogeneous static problem, allocated on first use
+    bool hetero_on;          // steps and static solves use the shear-modulus field in hetero.mu
+    double hetero_mu0, hetero_tol;
+    int hetero_max_iter;
     Dev rd64;                // mixed precision: FP64 spectra and tables for the Nye readout
     void* rd64_buf[3];       //   U13 and the two Nye components in FP64 (n each)
 };
@@ -587,9 +590,76 @@ fdm_status fdm_set_clock(fdm_handle* h, int64_t step, double t) {
     return FDM_OK;
 }
 
+// the static problem of the current step with the handle's shear-modulus field (tau13 in d.tau)
+static fdm_status hetero_static(fdm_handle* h, int* iterations, double* residual) {
+    const fdm_params& p = h->d.p;
+    fdm_dev_scalars s;
+    fdm_status st;
+    if ((st = read_scalars(h, &s))) return st;
+    double eps = 0.0, sig = 0.0;
+    host_loading(p, s.step, s.t, s.mean_up13, &eps, &sig);
+    const bool stress = p.loading_mode == FDM_LOAD_STRESS || p.loading_mode == FDM_LOAD_ZERO_MEAN_STRESS;
+    FDM_DISPATCH(h->prec, st = hetero_solve<T>(h->d, h->hetero, h->hetero_mu0, stress, stress ? sig : eps,
+                                               h->hetero_tol, h->hetero_max_iter, h->stream, iterations, residual));
+    return st;
+}
+
+// one step with the heterogeneous static problem: the iteration, the CFL step from its
+// tau13, then the transport kernel (which advances step and time and flips the buffers)
+static fdm_status hetero_step(fdm_handle* h) {
+    int it = 0;
+    double r = 0.0;
+    fdm_status st = hetero_static(h, &it, &r);
+    if (st) return st;
+    FDM_DISPATCH(h->prec, launch_celerity_dt<T>(h->d, h->stream); launch_phase<T>(h->d, kKernelsPerStep - 1, h->stream));
+    FDM_CK(cudaGetLastError());
+    return FDM_OK;
+}
+
+fdm_status fdm_set_shear_modulus_field(fdm_handle* h, const double* mu_factor, double tol, int32_t max_iter) {
+    if (!h) return FDM_ERR_INVALID_ARG;
+    if (!mu_factor) {
+        h->hetero_on = false;
+        return FDM_OK;
+    }
+    const fdm_params& p = h->d.p;
+    if (p.nh != p.nz || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1) return FDM_ERR_INVALID_ARG;
+    const size_t n = h->n;
+    const double mu = p.E / (2.0 * (1.0 + p.nu));
+    std::vector<double> m(n);
+    double mmin = HUGE_VAL, mmax = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!(mu_factor[i] > 0.0) || !std::isfinite(mu_factor[i])) return FDM_ERR_INVALID_ARG;
+        m[i] = mu * mu_factor[i];
+        mmin = std::fmin(mmin, m[i]);
+        mmax = std::fmax(mmax, m[i]);
+    }
+    if (h->next_phase != 0) return FDM_ERR_STATE;
+    fdm_status st;
+    const size_t bytes = n * elt_size(&p);
+    void** bufs[5] = {&h->hetero.mu, &h->hetero.g1, &h->hetero.g2, &h->hetero.t1, &h->hetero.t2};
+    for (void** b : bufs)
+        if (!*b && (st = h->arena.alloc(b, bytes))) return st;
+    FDM_CK(cudaStreamSynchronize(h->stream));
+    if ((st = upload_field(h->hetero.mu, m.data(), n, h->prec, 0.0, h->stream))) return st;
+    h->hetero_mu0 = 0.5 * (mmin + mmax);
+    h->hetero_tol = tol;
+    h->hetero_max_iter = max_iter;
+    h->hetero_on = true;
+    return FDM_OK;
+}
+
 fdm_status fdm_static_solve(fdm_handle* h) {
     if (!h) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
+    if (h->hetero_on) {
+        int it = 0;
+        double r = 0.0;
+        fdm_status st = hetero_static(h, &it, &r);
+        if (st) return st;
+        FDM_CK(cudaStreamSynchronize(h->stream));
+        return FDM_OK;
+    }
     Dev& d = h->d;
     FDM_DISPATCH(h->prec, launch_static<T>(d, h->stream));
     FDM_CK(cudaGetLastError());
@@ -603,6 +673,13 @@ fdm_status fdm_enqueue_steps(fdm_handle* h, int32_t nsteps) {
     if (!h || nsteps < 0) return FDM_ERR_INVALID_ARG;
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
     if (nsteps == 0) return FDM_OK;
+    if (h->hetero_on) {   // the iteration decides on the host: steps run on the host's loop
+        for (int32_t k = 0; k < nsteps; ++k) {
+            fdm_status st = hetero_step(h);
+            if (st) return st;
+        }
+        return FDM_OK;
+    }
     std::vector<Dev*> groups{&h->d};
     std::vector<int> prec{h->prec};
     fdm_status st = build_step_graphs(h->graphs, groups, prec);
@@ -612,7 +689,7 @@ fdm_status fdm_enqueue_steps(fdm_handle* h, int32_t nsteps) {
 
 fdm_status fdm_enqueue_phase(fdm_handle* h, int32_t phase) {
     if (!h || phase < 0 || phase >= kKernelsPerStep) return FDM_ERR_INVALID_ARG;
-    if (!h->has_state || phase != h->next_phase) return FDM_ERR_STATE;
+    if (!h->has_state || phase != h->next_phase || h->hetero_on) return FDM_ERR_STATE;
     FDM_DISPATCH(h->prec, launch_phase<T>(h->d, phase, h->stream));
     FDM_CK(cudaGetLastError());
     h->next_phase = (phase + 1) % kKernelsPerStep;
@@ -757,6 +834,11 @@ fdm_status fdm_static_solve_heterogeneous(fdm_handle* h, const double* mu_factor
     FDM_DISPATCH(h->prec, st = hetero_solve<T>(h->d, h->hetero, 0.5 * (mmin + mmax), stress, stress ? sig : eps, tol,
                                                max_iter, h->stream, &it, &r));
     if (st) return st;
+    if (h->hetero_on) {   // the uploaded field replaces the stepping field
+        h->hetero_mu0 = 0.5 * (mmin + mmax);
+        h->hetero_tol = tol;
+        h->hetero_max_iter = max_iter;
+    }
     if (sigma13 && (st = download_field(sigma13, h->d.tau, n, h->prec, 0.0, h->stream))) return st;
     if (sigma23 && (st = download_field(sigma23, h->hetero.t2, n, h->prec, 0.0, h->stream))) return st;
     FDM_CK(cudaStreamSynchronize(h->stream));

@@ -496,6 +496,51 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     }
 }
 
+// max |v0| of the celerity law over the nodes of a single instance for a tau13 computed outside
+// the step kernels (the heterogeneous static problem), then this step's dt by the last block,
+// as the inverse row kernel does after its rows
+template <typename T>
+__global__ void celerity_dt_kernel(const T* __restrict__ tau, const T* phi0, const T* phi1, size_t n, VelLaw<T> vel,
+                                   fdm_dev_scalars* sc, double cfl, double dx, double dt_max) {
+    const int cur = sc->cur;
+    const T* up = cur ? phi1 : phi0;
+    const double phi_ref = vel.friction ? sc->phi_ref : 0.0;
+    T vmax = T(0);
+    bool bad = false;
+    unsigned long long vbits = 0ull;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T c = celerity(vel, tau[i], vel.friction ? up[i] : T(0), phi_ref);
+        if (vel.mfac) c = c * vel.mfac[i];
+        if constexpr (std::is_same<T, double>::value) {
+            const unsigned long long m = ubits(c) & kMagBits;
+            vbits = m > vbits ? m : vbits;
+        } else {
+            vmax = tmax(vmax, tabs(c));
+            bad |= (c != c);
+        }
+    }
+    unsigned long long bits = vbits;
+    if constexpr (!std::is_same<T, double>::value) bits = bad ? 0x7ff8000000000000ull : abs_bits((double)vmax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = other > bits ? other : bits;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&sc->vmax_bits, bits);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&sc->ri_count, 1u) == gridDim.x - 1) {
+            __threadfence();
+            const double vm = __longlong_as_double((long long)atomicAdd(&sc->vmax_bits, 0ull));
+            const double dtd = cfl_dt(vm, cfl, dx, dt_max);
+            sc->dt_next = dtd;
+            sc->dt_h_next = dtd / dx;
+            sc->ri_count = 0u;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ KNP stencil
 constexpr int TX = 32;  // stencil block width (threads along x1)
 
@@ -1077,6 +1122,16 @@ void launch_fft_inverse(const Dev& d, void* spec, T* dst, cudaStream_t s) {
     launch_row_inverse<T>(d, (const cpx<T>*)spec, dst, ROW_PLAIN, 0.0, 1, s);
 }
 
+// the step's dt from d.tau (single instance): see celerity_dt_kernel
+template <typename T>
+void launch_celerity_dt(const Dev& d, cudaStream_t s) {
+    const size_t n = (size_t)d.p.n1 * d.p.n2;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    celerity_dt_kernel<T><<<blocks, 256, 0, s>>>((const T*)d.tau, (const T*)d.phi[0], (const T*)d.phi[1], n,
+                                                 make_vel<T>(d.p, d.mfac), d.sc, d.p.cfl, d.p.dx, d.p.dt_max);
+}
+
 // static solve only: tau for the current state of every instance
 template <typename T>
 void launch_static(const Dev& d, cudaStream_t s) {
@@ -1169,6 +1224,7 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_static_to<T>(const Dev&, T*, cudaStream_t);                                        \
     template void launch_stress_to<T>(const Dev&, int, T*, cudaStream_t);                                   \
     template void launch_fft_forward<T>(const Dev&, const T*, void*, cudaStream_t);                         \
+    template void launch_celerity_dt<T>(const Dev&, cudaStream_t);                                          \
     template void launch_fft_inverse<T>(const Dev&, void*, T*, cudaStream_t);                               \
     template void launch_alpha<T>(const Dev&, const T*, T*, T*, cudaStream_t);                              \
     template void launch_curl_inverse<T>(const Dev&, const T*, const T*, T*, double, double, double*, int, \

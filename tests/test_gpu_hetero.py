@@ -115,3 +115,68 @@ def test_hetero_invalid_arguments():
         with pytest.raises(FDMError) as e:
             sim.static_solve_heterogeneous(bad)
         assert e.value.status == B.FDM_ERR_INVALID_ARG
+
+
+def coupled_hetero(n1, n2, precision, loading=B.LOAD_STRAIN_RAMP):
+    return Params(n1=n1, n2=n2, nz=8, nh=8, velocity_mode=B.V_STRESS, loading_mode=loading, eps_bar13_rate=1e-4,
+                  sigma_bar13=0.0, cfl=0.4, theta=1.0, precision=precision)
+
+
+@pytest.mark.parametrize("precision,tol", [(B.FP64, 1e-11), (B.DF64, 1e-11), (B.MIXED, 1e-5)])
+def test_hetero_steps_match_oracle(precision, tol):
+    """Eight coupled steps (stress-driven, strain ramp, CFL 0.4) with the heterogeneous static
+    problem in every step, 20 iterations each, against the oracle's time loop."""
+    n1, n2 = 64, 32
+    up0 = inputs.random_up(64, seed=24, ell=4.0)[:n2, :n1].copy()
+    f = modulus_factor(n2, n1, 25)
+    p = coupled_hetero(n1, n2, precision)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.set_shear_modulus_field(f, tol=0.0, max_iter=20)
+        info = sim.step(8)
+        got = sim.read_fields("up13", "tau13")
+    op = oracle.Params(n1=n1, n2=n2, nz=8, nh=8, velocity_mode=1, loading_mode=1, eps_bar13_rate=1e-4, cfl=0.4,
+                       theta=1.0)
+    ref, rc = oracle.run(op, up0, 8, shear_modulus=MU * f, hetero_tol=0.0, hetero_max_iter=20)
+    assert rc == 0 and info.step == 8
+    assert rel(got["up13"], ref.up13) < tol
+    assert rel(got["tau13"], ref.tau13) < (tol if precision != B.MIXED else 1e-4)
+    assert info.t == pytest.approx(ref.t, rel=tol)
+
+
+def test_hetero_uniform_modulus_steps_equal_layer_steps():
+    n = 64
+    up0 = inputs.random_up(n, seed=26, ell=4.0)
+    p = coupled_hetero(n, n, B.FP64)
+    with FDM(p) as a, FDM(p) as b:
+        a.set_plastic_distortion(up0)
+        b.set_plastic_distortion(up0)
+        b.set_shear_modulus_field(np.ones((n, n)), tol=1e-14, max_iter=5)
+        ia, ib = a.step(10), b.step(10)
+        ua, ub = a.read_fields("up13")["up13"], b.read_fields("up13")["up13"]
+        with pytest.raises(FDMError) as e:
+            b.enqueue_phase(0)
+        assert e.value.status == B.FDM_ERR_STATE
+        b.set_shear_modulus_field(None)
+        b.enqueue_phase(0)
+    assert rel(ub, ua) < 1e-11
+    assert ib.t == pytest.approx(ia.t, rel=1e-11)
+
+
+def test_hetero_steps_at_scale_never_increase_the_energy():
+    """512^2, contrast 4, zero macroscopic stress, stress-driven motion: the stored energy
+    1/2 sum (sigma13^2 + sigma23^2) / mu falls between checkpoints."""
+    n = 512
+    up0 = inputs.random_up(n, seed=27, ell=16.0)
+    f = modulus_factor(n, n, 28, ell=24.0)
+    p = coupled_hetero(n, n, B.FP64, loading=B.LOAD_STRESS)
+    w = []
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.set_shear_modulus_field(f, tol=1e-12, max_iter=200)
+        for _ in range(5):
+            s13, s23, it, r = sim.static_solve_heterogeneous(f, tol=1e-12, max_iter=200)
+            w.append(0.5 * float(np.sum((s13 ** 2 + s23 ** 2) / (MU * f))))
+            sim.step(10)
+    w = np.array(w)
+    assert (np.diff(w) < 0).all(), w
