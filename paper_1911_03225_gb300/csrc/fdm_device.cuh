@@ -11,7 +11,9 @@
 
 namespace fdm {
 
-template <typename T> struct cpx { T x, y; };
+// aligned to its size, so that a complex value moves in one 64-bit (FP32) or 128-bit (FP64,
+// double-word) access
+template <typename T> struct alignas(2 * sizeof(T)) cpx { T x, y; };
 
 template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
 template <typename T> __host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }

@@ -20,7 +20,7 @@
 
 namespace fdm {
 
-struct df {
+struct alignas(8) df {   // one 64-bit access per value
     float hi, lo;
     df() = default;
     __host__ __device__ __forceinline__ constexpr df(float h, float l) : hi(h), lo(l) {}
