@@ -93,6 +93,23 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
 template <typename T> struct FftBounds { static constexpr int threads = 1024, minb = 1; };
 template <> struct FftBounds<float> { static constexpr int threads = 512, minb = 3; };
 
+// The FP32 transforms read their pass twiddles from shared memory, staged once per block
+// behind the data (visible after the block's next barrier): those kernels are latency bound,
+// and a shared load waits less than a global one.  Other types keep the global tables.
+template <typename T> __host__ __device__ __forceinline__ size_t staged_twiddle_bytes(int L) {
+    return std::is_same<T, float>::value ? (size_t)pass_table_len(L) * sizeof(cpx<T>) : 0;
+}
+template <typename T>
+__device__ __forceinline__ const cpx<T>* stage_twiddles(const cpx<T>* pt, cpx<T>* slot, int L) {
+    if constexpr (std::is_same<T, float>::value) {
+        const int len = pass_table_len(L);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) slot[i] = pt[i];
+        return slot;
+    } else {
+        return pt;
+    }
+}
+
 // ------------------------------------------------------------------ row forward (R2C)
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional FP64 sum of each row
 // (for <U13>), in an order fixed by the row alone, so that results do not depend on R.
@@ -115,6 +132,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     const int L = n1 >> 1;
     const int ld = padded_len(L);  // padded sequence stride (bank spread for the transposed store)
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);  // R * ld elements
+    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + R * ld, L);
     const int y0 = blockIdx.x * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
             if (lane == 0) row_partials[y0 + r] = rs;
         }
     }
-    smem_fft_ip<-1>(A, L, R, ld, pt1);
+    smem_fft_ip<-1>(A, L, R, ld, ptw);
     const int half = L / 2 + 1;
     for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
         int r = e / half, k = e - r * half;  // half = L/2 + 1 is not a power of two
@@ -244,6 +262,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     }
     __syncthreads();
     if (!s_run) return;
+    const cpx<T>* ptw = stage_twiddles<T>(pt2, A + C * ld, n2);
     const size_t half_n = (size_t)n1 * n2 / 2;
     in += inst * half_n;
     out += inst * half_n;
@@ -292,7 +311,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
         }
     }
     __syncthreads();
-    if (a.mode != COL_INV) smem_fft_ip<-1>(A, n2, C, ld, pt2);
+    if (a.mode != COL_INV) smem_fft_ip<-1>(A, n2, C, ld, ptw);
     if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N || a.mode == COL_SYM) {
         // in place: a thread owns the pair (ky, n2 - ky) of one column
         const int hp = n2 / 2 + 1;
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
         }
         __syncthreads();
     }
-    if (a.mode != COL_FWD) smem_fft_ip<+1>(A, n2, C, ld, pt2);
+    if (a.mode != COL_FWD) smem_fft_ip<+1>(A, n2, C, ld, ptw);
     cpx<T>* dst = out + (size_t)kx0 * n2;
     for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = A[(e >> ln2) * ld + swz(e & (n2 - 1))];
 }
@@ -404,6 +423,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     }
     __syncthreads();
     if (!s_run) return;
+    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + R * ld, L);
     const size_t nn = (size_t)n1 * n2;
     spec += inst * (nn / 2);
     dst += inst * nn;
@@ -433,7 +453,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
         c2r_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
     }
     __syncthreads();
-    smem_fft_ip<+1>(A, L, R, ld, pt1);
+    smem_fft_ip<+1>(A, L, R, ld, ptw);
     const cpx<T>* z = A;
     T vmax = T(0);
     bool bad = false;
@@ -894,10 +914,11 @@ constexpr size_t kMaxDynSmem = 200 * 1024;  // dynamic shared memory the FFT ker
 // bound (one radix-8 butterfly per thread) and the rows fit the shared-memory limit
 template <typename T> static bool row_ok(int n1, int n2, int R) {
     return R <= n2 && R <= 16 && R * (n1 / 2) <= 8 * FftBounds<T>::threads &&
-           (size_t)R * padded_len(n1 / 2) * sizeof(cpx<T>) <= kMaxDynSmem;
+           (size_t)R * padded_len(n1 / 2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n1 / 2) <= kMaxDynSmem;
 }
 template <typename T> static bool col_ok(int n1, int n2, int C) {
-    return C <= n1 / 2 && C <= 16 && C * n2 <= 8 * FftBounds<T>::threads && (size_t)C * padded_len(n2) * sizeof(cpx<T>) <= kMaxDynSmem;
+    return C <= n1 / 2 && C <= 16 && C * n2 <= 8 * FftBounds<T>::threads &&
+           (size_t)C * padded_len(n2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n2) <= kMaxDynSmem;
 }
 
 template <typename T>
@@ -934,8 +955,8 @@ LaunchGeom geometry(int n1, int n2, int R, int C, int knp_shape) {
     LaunchGeom g{};
     g.R = R > 0 ? R : pick_rows<T>(n1, n2);
     g.C = C > 0 ? C : pick_cols(n1, n2);
-    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>);
-    g.col_smem = (size_t)g.C * padded_len(n2) * sizeof(cpx<T>);
+    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n1 / 2);
+    g.col_smem = (size_t)g.C * padded_len(n2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n2);
     g.row_blocks = n2 / g.R;
     g.col_blocks = (n1 / 2) / g.C;
     // the in-place FFT needs at least one thread per radix-8 butterfly; at least a warp
