@@ -536,11 +536,24 @@ def run_serve(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 and f32 mix",
             "data": "synthetic (Poisson arrivals, seeded fields)",
             "config": {"workload": "served request mix: Poisson 200 req/s, side in {64..1024}, steps U[%d,%d], "
-                                   "50%% FP64 / 50%% mixed, 150 GB HBM budget, %d requests (window scaled "
-                                   "down from 2000)" % (args.serve_min_steps, args.serve_max_steps, R),
+                                   "50%% FP64 / 50%% mixed, 150 GB HBM budget, %d requests%s"
+                                   % (args.serve_min_steps, args.serve_max_steps, R,
+                                      "" if R >= 2000 else " (window scaled down from 2000)"),
                        "slots_per_class": args.serve_slots, "tick_steps": args.serve_tick},
             "serve": st, "gpu_launches": st["launches"], "clocks": clk.summary(),
         }), flush=True)
+
+
+def run_hetero(args, world, rank, local):
+    """The heterogeneous static problem alone (shear-modulus contrast 4, layer filling the
+    cell, n x n): a converged solve per precision and the time of one iteration."""
+    import torch
+    build_once(rank, world)
+    torch.cuda.set_device(local)
+    if rank == 0:
+        out = {"fp64": hetero_static(args.n, "fp64", tol=1e-12), "mixed": hetero_static(args.n, "mixed", tol=1e-6)}
+        print(json.dumps({"workload": "heterogeneous static problem, %dx%d, contrast 4, stress control" % (args.n, args.n),
+                          "hetero_static": out}), flush=True)
 
 
 def run_reference(args, world, rank):
@@ -582,7 +595,7 @@ def main():
     ap.add_argument("--precision", default="all", choices=["fp64", "df64", "mixed", "all"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="coupled", choices=["coupled", "batched", "serve"])
+    ap.add_argument("--workload", default="coupled", choices=["coupled", "batched", "serve", "hetero"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-min-steps", type=int, default=100)
@@ -599,6 +612,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "hetero":
+        run_hetero(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     from paper_1911_03225_gb300.replicas import finalize
