@@ -590,6 +590,19 @@ fdm_status fdm_set_clock(fdm_handle* h, int64_t step, double t) {
     return FDM_OK;
 }
 
+// buffers of the heterogeneous static problem, allocated on first use
+static fdm_status alloc_hetero(fdm_handle* h) {
+    const fdm_params& p = h->d.p;
+    const size_t bytes = h->n * elt_size(&p);
+    const size_t tab = (size_t)3 * (p.n1 / 2 + 1) * (p.n2 / 2 + 1) * (h->prec == FDM_MIXED ? sizeof(float) : sizeof(double));
+    void** bufs[6] = {&h->hetero.mu, &h->hetero.g1, &h->hetero.g2, &h->hetero.t1, &h->hetero.t2, &h->hetero.gam};
+    const size_t sizes[6] = {bytes, bytes, bytes, bytes, bytes, tab};
+    fdm_status st;
+    for (int i = 0; i < 6; ++i)
+        if (!*bufs[i] && (st = h->arena.alloc(bufs[i], sizes[i]))) return st;
+    return FDM_OK;
+}
+
 // the static problem of the current step with the handle's shear-modulus field (tau13 in d.tau)
 static fdm_status hetero_static(fdm_handle* h, int* iterations, double* residual) {
     const fdm_params& p = h->d.p;
@@ -636,10 +649,7 @@ fdm_status fdm_set_shear_modulus_field(fdm_handle* h, const double* mu_factor, d
     }
     if (h->next_phase != 0) return FDM_ERR_STATE;
     fdm_status st;
-    const size_t bytes = n * elt_size(&p);
-    void** bufs[5] = {&h->hetero.mu, &h->hetero.g1, &h->hetero.g2, &h->hetero.t1, &h->hetero.t2};
-    for (void** b : bufs)
-        if (!*b && (st = h->arena.alloc(b, bytes))) return st;
+    if ((st = alloc_hetero(h))) return st;
     FDM_CK(cudaStreamSynchronize(h->stream));
     if ((st = upload_field(h->hetero.mu, m.data(), n, h->prec, 0.0, h->stream))) return st;
     h->hetero_mu0 = 0.5 * (mmin + mmax);
@@ -818,10 +828,7 @@ fdm_status fdm_static_solve_heterogeneous(fdm_handle* h, const double* mu_factor
     }
     if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
     fdm_status st;
-    const size_t bytes = n * elt_size(&p);
-    void** bufs[5] = {&h->hetero.mu, &h->hetero.g1, &h->hetero.g2, &h->hetero.t1, &h->hetero.t2};
-    for (void** b : bufs)
-        if (!*b && (st = h->arena.alloc(b, bytes))) return st;
+    if ((st = alloc_hetero(h))) return st;
     if ((st = upload_field(h->hetero.mu, m.data(), n, h->prec, 0.0, h->stream))) return st;
     // the loading of the current step: sigma_bar13 (stress, zero mean stress) or eps_bar13
     fdm_dev_scalars s;

@@ -82,6 +82,26 @@ __global__ void hetero_polarisation_kernel(StateRef st, const T* __restrict__ mu
 template <typename T>
 using sym_t = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
 
+// Green operator without the modulus, on the quarter (kx in [0, n1/2], ky in [0, n2/2]):
+// xi1^2 / |xi|^2, xi1 xi2 / |xi|^2 (the odd product zeroed at the Nyquist indices) and
+// xi2^2 / |xi|^2 at ky >= 0; the sign of the odd product follows ky's.  Zero at the origin.
+template <typename S>
+__global__ void hetero_gamma_table_kernel(S* __restrict__ tab, int n1, int n2) {
+    const int w = n2 / 2 + 1;
+    const int total = (n1 / 2 + 1) * w;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int kx = i / w, ky = i - kx * w;
+        const S x1 = S(6.283185307179586476925286766559) * S(kx) / S(n1);
+        const S x2 = S(6.283185307179586476925286766559) * S(ky) / S(n2);
+        const S o1 = (2 * kx == n1) ? S(0) : x1, o2 = (2 * ky == n2) ? S(0) : x2;
+        const S q = x1 * x1 + x2 * x2;
+        const S iq = q > S(0) ? S(1) / q : S(0);
+        tab[3 * i] = x1 * x1 * iq;
+        tab[3 * i + 1] = o1 * o2 * iq;
+        tab[3 * i + 2] = x2 * x2 * iq;
+    }
+}
+
 struct GammaArgs {
     int stress_control;
     double G1, G2;        // strain control: the prescribed mean of g
@@ -95,23 +115,21 @@ struct GammaArgs {
 template <typename T>
 __global__ void hetero_gamma0_kernel(const cpx<T>* __restrict__ sa, const cpx<T>* __restrict__ sb,
                                      cpx<T>* __restrict__ oa, cpx<T>* __restrict__ ob, int n1, int n2,
-                                     GammaArgs a) {
+                                     const sym_t<T>* __restrict__ tab, GammaArgs a) {
     using S = sym_t<T>;
-    const int L = n1 / 2;
+    const int L = n1 / 2, w = n2 / 2 + 1;
     const size_t total = (size_t)L * n2;
     const double N = (double)n1 * (double)n2;
-    const S scl = S(1.0 / N), mu0 = S(a.mu0);
-    const S two_pi = S(6.283185307179586476925286766559);
+    const S c = S(1.0 / (N * a.mu0));   // normalisation and 1/mu0
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int kx = (int)(i / n2), ky = (int)(i - (size_t)kx * n2);
-        const int kys = ky <= n2 / 2 ? ky : ky - n2;
-        const S x2 = two_pi * S(kys) / S(n2);
-        const S o2 = (2 * ky == n2) ? S(0) : x2;
+        const bool neg = ky > n2 / 2;
+        const int kyf = neg ? n2 - ky : ky;
         const cpx<T> za = sa[i], zb = sb[i];
         if (kx > 0) {
-            const S x1 = two_pi * S(kx) / S(n1);
-            const S iq = S(1) / (mu0 * (x1 * x1 + x2 * x2));
-            const T a11 = T(x1 * x1 * iq * scl), a12 = T(x1 * o2 * iq * scl), a22 = T(x2 * x2 * iq * scl);
+            const S* t = tab + 3 * ((size_t)kx * w + kyf);
+            const S t12 = neg ? -t[1] : t[1];
+            const T a11 = T(t[0] * c), a12 = T(t12 * c), a22 = T(t[2] * c);
             oa[i] = mk(-(a11 * za.x + a12 * zb.x), -(a11 * za.y + a12 * zb.y));
             ob[i] = mk(-(a12 * za.x + a22 * zb.x), -(a12 * za.y + a22 * zb.y));
         } else {
@@ -131,14 +149,13 @@ __global__ void hetero_gamma0_kernel(const cpx<T>* __restrict__ sa, const cpx<T>
                 g10 = mk(T(G1), T(0));
                 g20 = mk(T(G2), T(0));
             } else {   // xi1 = 0: the x1 part of Gamma0 vanishes, the x2 part is 1/mu0
-                const T c = T(scl / mu0);
+                const T c0 = T(c);
                 g10 = mk(T(0), T(0));
-                g20 = mk(-(c * B0.x), -(c * B0.y));
+                g20 = mk(-(c0 * B0.x), -(c0 * B0.y));
             }
             // kx = n1/2: xi1 = pi (even use), zero in the odd product
-            const S xN = S(3.14159265358979323846);
-            const S iqN = S(1) / (mu0 * (xN * xN + x2 * x2));
-            const T b11 = T(xN * xN * iqN * scl), b22 = T(x2 * x2 * iqN * scl);
+            const S* tN = tab + 3 * ((size_t)L * w + kyf);
+            const T b11 = T(tN[0] * c), b22 = T(tN[2] * c);
             const cpx<T> g1N = mk(-(b11 * AN.x), -(b11 * AN.y)), g2N = mk(-(b22 * BN.x), -(b22 * BN.y));
             oa[i] = mk(g10.x - g1N.y, g10.y + g1N.x);   // repack G0 + i GN
             ob[i] = mk(g20.x - g2N.y, g20.y + g2N.x);
@@ -225,6 +242,9 @@ fdm_status hetero_solve(const Dev& d, const HeteroBuffers& hb, double mu0, bool 
     ga.mu0 = mu0;
     const int eblk = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
     const int sblk = (int)std::min<size_t>((n / 2 + 255) / 256, 152 * 16);
+    const int nq = (d.p.n1 / 2 + 1) * (d.p.n2 / 2 + 1);
+    hetero_gamma_table_kernel<sym_t<T>><<<std::min((nq + 255) / 256, 152 * 16), 256, 0, s>>>((sym_t<T>*)hb.gam,
+                                                                                           d.p.n1, d.p.n2);
     int it = 0;
     double r = 0.0;
     while (it < max_iter) {
@@ -234,7 +254,7 @@ fdm_status hetero_solve(const Dev& d, const HeteroBuffers& hb, double mu0, bool 
         launch_fft_forward<T>(d, (const T*)hb.t1, d.spec, s);
         launch_fft_forward<T>(d, (const T*)hb.t2, d.spec2, s);
         hetero_gamma0_kernel<T><<<sblk, 256, 0, s>>>((const cpx<T>*)d.spec, (const cpx<T>*)d.spec2, (cpx<T>*)hb.t1,
-                                                    (cpx<T>*)hb.t2, d.p.n1, d.p.n2, ga);
+                                                    (cpx<T>*)hb.t2, d.p.n1, d.p.n2, (const sym_t<T>*)hb.gam, ga);
         launch_fft_inverse<T>(d, hb.t1, (T*)d.spec, s);
         launch_fft_inverse<T>(d, hb.t2, (T*)d.spec2, s);
         hetero_update_kernel<T><<<nblk, 256, 0, s>>>((const T*)d.spec, (const T*)d.spec2, (T*)hb.g1, (T*)hb.g2, n,

@@ -187,9 +187,11 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
 fdm_status upload_field(void* dst, const double* src, size_t n, int prec, double offset, cudaStream_t s);
 
 // Heterogeneous antiplane static problem (fdm_hetero.cu): device fields of type T, n each:
-// the shear modulus, the iterate g (two components) and two work fields.
+// the shear modulus, the iterate g (two components) and two work fields; gam: the Green
+// operator's ratios on the quarter spectrum, 3 (n1/2+1)(n2/2+1) values (FP32 for FP32 fields,
+// FP64 otherwise).
 struct HeteroBuffers {
-    void *mu, *g1, *g2, *t1, *t2;
+    void *mu, *g1, *g2, *t1, *t2, *gam;
 };
 // Runs the fixed-point iteration for the current state of the single-instance group d and
 // writes sigma13 to d.tau and sigma23 to hb.t2.  stress_control: load = sigma_bar13, else
