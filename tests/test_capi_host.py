@@ -88,6 +88,9 @@ def test_null_arguments(lib):
         binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_read_stress13_planes(None, 0, None, None) == binding.FDM_ERR_INVALID_ARG
     assert lib.fdm_batch_sync_status(None, None, None) == binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_static_solve_heterogeneous(None, None, 0.0, 1, None, None, None, None) == \
+        binding.FDM_ERR_INVALID_ARG
+    assert lib.fdm_set_shear_modulus_field(None, None, 0.0, 1) == binding.FDM_ERR_INVALID_ARG
     lib.fdm_destroy(None)   # NULL-safe
 
 
