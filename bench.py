@@ -468,10 +468,12 @@ def run_batched(args, world, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             barrier(world)
+            torch.cuda.nvtx.range_push("fdm_timed")
             e0.record(stream)
             b.enqueue_steps(K)
             e1.record(stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             barrier(world)
         left = b.sync()
         assert (left == 0).all()
