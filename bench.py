@@ -32,12 +32,7 @@ METRIC = "FDM cell-steps/s (FFT stress + Godunov transport), %HBM roofline; p50/
 UNIT = "cell-steps/s"
 PHASES = ["row_forward", "col_pass", "row_inverse", "knp_step"]
 FALLBACK_HBM_GBS = 6800.0
-FP64_NOMINAL_GFLOPS = 1250.0            # GB300 FP64 rate (profiling recipe table)
-# FP32 operations behind one double-word operation (an addition: TwoSum 6, two more sums and
-# a fast TwoSum 2 = 10; a product: exact product 2, cross terms 3, sum 1, fast TwoSum 2 = 8),
-# rounded to the mean of the stencil's mix: the double-word path's arithmetic roofline
-DF_FP32_OPS_PER_OP = 9
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x 2 (FMA) x max SM clock [GHz]
+NORTH_STAR_HBM_FRAC = 0.6   # target fraction of the HBM roofline for the FP64 path at 2048^2
 
 
 def workload_params(n, precision):
@@ -63,9 +58,16 @@ def bytes_per_cell(elt, pair=False):
             "knp_step": (2 * w + 1) * elt}    # read U13 and tau13, write U13^{n+1}
 
 
-# FP arithmetic per node of the KNP update (counted from knp_node in fdm_device.cuh:
-# +,-,*,min,max,compare = 1, multiply-add = 2, rsqrt and reciprocal = 1 each).
-KNP_FLOPS_PER_CELL = 380
+# Algorithmic floating-point operations per node of the KNP update (Steps 1-4 as knp_node in
+# fdm_device.cuh evaluates them; add, subtract and multiply 1, multiply-add 2, reciprocal
+# and reciprocal square root 1; comparisons, min, max and sign flips 0):
+#   first differences 8; limited second differences 20; one-sided derivatives 8;
+#   one-sided speeds (three |(p,q)|^-1 and four products) 19; projection weights 4;
+#   v0 dt and v0 dt / 2 2; the row and column quadratics of the two sides 20 + 20;
+#   four corners of 36 (mixed difference 3, value 5, gradient 4, midpoint predictor 15,
+#   |grad| 5, Psi and its weight 4) 144; projection 5.  Total 250, of which 11 reciprocal
+#   square roots and one reciprocal.
+KNP_FLOPS_PER_CELL = 250
 
 
 KERNEL_SOURCES = ["fdm_kernels.cu", "fdm_device.cuh", "fdm_df.cuh", "fdm_internal.h"]
@@ -109,6 +111,19 @@ def read_peaks():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def measured_arith_peaks(local):
+    """FP64, FP32 and double-word multiply-add rates of this GPU, measured now by the
+    library's FMA-chain kernel (fdm_measure_arith_rate), with the SM clock sampled meanwhile."""
+    from paper_1911_03225_gb300 import binding as B
+    with ClockSampler(local) as clk:
+        out = {"fp64": B.measure_arith_rate(B.FP64), "fp32": B.measure_arith_rate(B.MIXED),
+               "df64": B.measure_arith_rate(B.DF64)}
+    out = {k: round(v, 1) for k, v in out.items()}
+    out["unit"] = "GFLOP/s (multiply-add = 2)"
+    out["clocks"] = clk.summary()
+    return out
 
 
 class ClockSampler:
@@ -232,6 +247,7 @@ def run_ours(args, world, rank, local):
     cells = n * n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     hbm_peak, peak_src = read_peaks()
+    peaks = measured_arith_peaks(local)
     up0 = workload_input(n, seed=rank)
 
     results = {}
@@ -261,21 +277,47 @@ def run_ours(args, world, rank, local):
     primary = args.precision if args.precision != "all" else "fp64"
     r = results[primary]
     value = cells * K * world / (r["total_ms"] / 1e3)
-    dom = r["dominant"]
-    elt = 4 if primary == "mixed" else 8
-    dom_ms = r["phase_ms"][dom]
-    if dom == "knp_step" and primary == "fp64":
-        roof = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (dom_ms / 1e3) / 1e9,
-                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; FMA-chain probe 1.20)"}
-    else:
-        roof = {"bound": "hbm", "achieved": r["bpc"][dom] * cells / (dom_ms / 1e3) / 1e9,
-                "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    roof["traffic"] = profiled_traffic(dom, primary, n)
-    roof["algorithmic_bytes"] = r["bpc"][dom] * cells
-    roof["hbm_frac_of_step"] = (sum(r["bpc"].values()) * cells / (r["total_ms"] / K / 1e3) / 1e9) / hbm_peak
+
+    def roofline(prec, rr):
+        """Roofline of the step's dominant kernel: the stencil against the measured multiply-add
+        rate of its arithmetic (it is bound by arithmetic, not by HBM), the transforms
+        against the HBM peak."""
+        d = rr["dominant"]
+        d_ms = rr["phase_ms"][d]
+        hbm_gbs = rr["bpc"][d] * cells / (d_ms / 1e3) / 1e9
+        if d == "knp_step":
+            key = {"fp64": "fp64", "df64": "df64", "mixed": "fp32"}[prec]
+            rl = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (d_ms / 1e3) / 1e9, "peak": peaks[key],
+                  "unit": "GFLOP/s", "flops_per_cell": KNP_FLOPS_PER_CELL,
+                  "peak_source": "measured in this run (of measured): %s multiply-add chains on every SM, "
+                                 "fdm_measure_arith_rate, SM clock %s MHz" % (
+                                     {"fp64": "FP64", "fp32": "FP32", "df64": "double-word"}[key],
+                                     peaks["clocks"].get("sm_mhz"))}
+        else:
+            rl = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src}
+        rl["frac"] = rl["achieved"] / rl["peak"]
+        rl["kernel"] = d
+        rl["traffic"] = profiled_traffic(d, prec, n)
+        rl["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the committed "
+                                "profile summary (profiles/*.md) taken on the same kernel sources; not measured "
+                                "in this run" if rl["traffic"] is not None else
+                                "no committed profile of the current kernel sources")
+        rl["algorithmic_bytes"] = rr["bpc"][d] * cells
+        rl["hbm_GBs"] = hbm_gbs
+        rl["hbm_frac"] = hbm_gbs / hbm_peak
+        step_gbs = sum(rr["bpc"].values()) * cells / (rr["total_ms"] / K / 1e3) / 1e9
+        rl["hbm_frac_of_step"] = step_gbs / hbm_peak
+        return rl
+
+    roof = roofline(primary, r)
+    if primary == "fp64":
+        roof["north_star_hbm_target"] = {
+            "target_frac": NORTH_STAR_HBM_FRAC, "achieved_frac": roof["hbm_frac_of_step"],
+            "met": roof["hbm_frac_of_step"] >= NORTH_STAR_HBM_FRAC,
+            "why": "the FP64 step is bound by the FP64 pipe, not by HBM: its %d B per cell take %.0f us of HBM "
+                   "time at the peak, its stencil alone %.0f us of FP64 multiply-adds at the measured rate" % (
+                       sum(r["bpc"].values()), sum(r["bpc"].values()) * cells / hbm_peak / 1e3,
+                       KNP_FLOPS_PER_CELL * cells / peaks["fp64"] / 1e3)}
 
     # end to end through the public API with host buffers (rank-local)
     sim = r["sim"]
@@ -296,26 +338,10 @@ def run_ours(args, world, rank, local):
 
     extra = {}
     for prec, rr in results.items():
-        d = rr["dominant"]
-        d_ms = rr["phase_ms"][d]
-        if d == "knp_step":
-            pk = {"fp64": FP64_NOMINAL_GFLOPS, "df64": FP32_PEAK_GFLOPS / DF_FP32_OPS_PER_OP}.get(prec,
-                                                                                              FP32_PEAK_GFLOPS)
-            rl = {"bound": "alu", "achieved": KNP_FLOPS_PER_CELL * cells / (d_ms / 1e3) / 1e9, "peak": pk,
-                  "unit": "GFLOP/s",
-                  "peak_source": {"fp64": "nominal FP64 rate",
-                                  "df64": "FP32 rate / %d FP32 operations per double-word operation" %
-                                          DF_FP32_OPS_PER_OP}.get(prec, "FP32 rate (152 SMs x 128 lanes x 2 x 2.07 GHz)")}
-        else:
-            rl = {"bound": "hbm", "achieved": rr["bpc"][d] * cells / (d_ms / 1e3) / 1e9, "peak": hbm_peak,
-                  "unit": "GB/s"}
-        rl["frac"] = rl["achieved"] / rl["peak"]
-        rl["kernel"] = d
-        rl["traffic"] = profiled_traffic(d, prec, n)
         extra[prec] = {"value": cells * K * world / (rr["total_ms"] / 1e3),
                        "ms_per_step": rr["total_ms"] / K,
                        "phase_ms": {k: round(v, 5) for k, v in rr["phase_ms"].items()},
-                       "roofline": rl, "launch": rr["launch"],
+                       "roofline": roofline(prec, rr), "launch": rr["launch"],
                        "t_end": rr["info"].t, "clocks": rr["clocks"]}
 
     if rank == 0:
@@ -347,11 +373,20 @@ def run_ours(args, world, rank, local):
         # the mixed path's iterates stop improving at FP32 rounding (~1e-7)
         line["hetero_static"] = {"fp64": hetero_static(n, "fp64", tol=1e-12),
                                  "mixed": hetero_static(n, "mixed", tol=1e-6)}
+    for rr in results.values():
+        rr["sim"].close()
+    if args.sub_records:
+        # configurations 4 and 5 on the same GPU, in the same run (every rank, weak scaling)
+        batched = batched_record(world, rank, local, args.instances, max(K, 100), W)
+        served = serve_record(world, rank, local, args.sub_serve_requests, 100, args.sub_serve_max_steps,
+                              args.serve_slots, args.serve_tick)
+    if rank == 0:
+        if args.sub_records:
+            line["batched"] = batched
+            line["serve"] = served
         if args.cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
-    for rr in results.values():
-        rr["sim"].close()
 
 
 def hetero_static(n, precision, tol=1e-12, contrast=4.0):
@@ -412,26 +447,41 @@ def cufft_static_solve_ms(n, dtype, reps=20):
     return statistics.median(ts)
 
 
-def cpu_baseline(seconds):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload:
-    the same coupled configuration on a 512 x 512 grid (layer kernel precompute excluded),
-    stepped until about `seconds` of CPU time has passed."""
+def oracle_sample(seconds, threads, n=512, steps=None):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the same coupled
+    configuration on an n x n grid (the layer-kernel precompute excluded), stepped until
+    about `seconds` of wall time have passed (or exactly `steps` steps), its loops over
+    independent rows and nodes on `threads` host threads (< 1: every core; the results are
+    the same for every count).  Returns (cell-steps/s, steps, seconds, threads used)."""
     import oracle
-    n = 512
-    p = workload_params(n, "fp64")
-    op = oracle.Params(**{k: getattr(p, k) for k in oracle.Params.__dataclass_fields__})
-    K = oracle.kernel_table(n, n, n, p.nh, p.E / (2 * (1 + p.nu)), p.nu)
-    up = workload_input(n, seed=0)
-    st = oracle.State(up13=up.copy())
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds or steps < 2:
-        st, rc = oracle.run(op, None, 1, K=K, state=st)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": n * n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "coupled random-field workload on a %dx%d grid, %d steps (%.1f s), single thread, "
-                      "layer-kernel precompute excluded" % (n, n, steps, dt)}
+    prev = oracle.threads()
+    used = oracle.set_threads(threads)
+    try:
+        p = workload_params(n, "fp64")
+        op = oracle.Params(**{k: getattr(p, k) for k in oracle.Params.__dataclass_fields__})
+        K = oracle.kernel_table(n, n, n, p.nh, p.E / (2 * (1 + p.nu)), p.nu)
+        st = oracle.State(up13=workload_input(n, seed=0).copy())
+        t0 = time.perf_counter()
+        k = 0
+        while (steps is None and (time.perf_counter() - t0 < seconds or k < 2)) or (steps is not None and k < steps):
+            st, rc = oracle.run(op, None, 1, K=K, state=st)
+            k += 1
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(prev)
+    return n * n * k / dt, k, dt, used
+
+
+def cpu_baseline(seconds):
+    """The oracle timed on the host's cores (every core, and one thread), a reported
+    baseline beside the GPU numbers."""
+    v_all, k_all, t_all, used = oracle_sample(seconds, 0)
+    v_one, k_one, t_one, _ = oracle_sample(seconds, 1)
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle", "nproc": os.cpu_count(),
+            "sample": "coupled random-field workload on a 512x512 grid (bounded sample of the 2048x2048 workload), "
+                      "%d steps (%.1f s) on %d threads, layer-kernel precompute excluded" % (k_all, t_all, used),
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": "the same, %d steps (%.1f s) on one thread" % (k_one, t_one)}}
 
 
 def batched_workload(count=256, rank=0):
@@ -447,15 +497,16 @@ def batched_workload(count=256, rank=0):
     return out
 
 
-def run_batched(args, world, rank, local):
+def batched_record(world, rank, local, count, K, W):
+    """Configuration 4 measured: `count` instances in one batch (mixed precision, one launch
+    per kernel and size class, steps replayed from CUDA graphs), K timed steps after W; then
+    the plain per-instance FP64 form of a sample of the same instances on the same GPU, and
+    the mixed results' error against it."""
     import torch
-    import __graft_entry__
     from paper_1911_03225_gb300 import Batch, FDM
-    build_once(rank, world)
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    K, W = args.steps, args.warmup
-    inst = batched_workload(args.instances, rank)
+    inst = batched_workload(count, rank)
     cells = sum(n * n for n, _ in inst)
     params = [workload_params(n, "mixed") for n, _ in inst]
     with Batch(params, stream=stream.cuda_stream) as b:
@@ -498,59 +549,82 @@ def run_batched(args, world, rank, local):
             ref = sim.read_fields("up13")["up13"]
         errs.append(float(np.linalg.norm(mixed_out[i] - ref) / np.linalg.norm(ref)))
     value = cells * K * world / (ms / 1e3)
+    plain = fp64_cells * K / (fp64_ms / 1e3)
+    return {"value": value, "unit": UNIT, "steps": K, "warmup": W, "ms_per_step": ms / K,
+            "workload": "batched uneven instances: %d coupled simulations, side per seed in {64,128,256,512}, "
+                        "mixed precision, one batched launch per kernel and size class, CUDA-graph steps" % len(inst),
+            "instances": len(inst), "cells_per_step": cells,
+            "l2": "working set %.0f MB > L2" % (cells * 4 * 5 / 1e6),
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "plain_fp64_per_instance": {"value": plain, "unit": UNIT, "sample_instances": len(sample)},
+            "batched_mixed_over_plain_fp64": value / world / plain,
+            "mixed_vs_fp64_rel_l2": {"max": max(errs), "mean": sum(errs) / len(errs), "after_steps": W + K,
+                                     "stated_tolerance": 1e-5}}
+
+
+def run_batched(args, world, rank, local):
+    build_once(rank, world)
+    rec = batched_record(world, rank, local, args.instances, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (FP64 scalars)", "data": "synthetic (seeded random U13 fields)",
-            "config": {"workload": "batched uneven instances: %d coupled simulations, side per seed in "
-                                   "{64,128,256,512}, mixed precision, one batched launch per kernel and size "
-                                   "class, CUDA-graph steps" % len(inst),
-                       "cells_per_step": cells, "l2": "working set %.0f MB > L2" % (cells * 4 * 5 / 1e6)},
-            "gpu_launches": launches, "clocks": clk.summary(),
-            "plain_fp64_per_instance": {"value": fp64_cells * K / (fp64_ms / 1e3), "unit": UNIT,
-                                        "sample_instances": len(sample)},
-            "mixed_vs_fp64_rel_l2": {"max": max(errs), "mean": sum(errs) / len(errs), "after_steps": W + K},
+            "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 scalars)", "data": "synthetic (seeded random U13 fields)",
+            "config": {"workload": rec["workload"], "cells_per_step": rec["cells_per_step"], "l2": rec["l2"]},
+            "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
+            "plain_fp64_per_instance": rec["plain_fp64_per_instance"],
+            "mixed_vs_fp64_rel_l2": rec["mixed_vs_fp64_rel_l2"],
         }), flush=True)
 
 
-def run_serve(args, world, rank, local):
+def serve_record(world, rank, local, R, min_steps, max_steps, slots, tick, group_size=8):
+    """Configuration 5 measured: R Poisson arrivals (200 req/s, seeded), side uniform in
+    {64, ..., 1024}, steps uniform in [min_steps, max_steps], half FP64 and half mixed, served
+    under a 150 GB HBM budget with `slots` resident simulations per class at most."""
     import torch
-    import __graft_entry__
     from paper_1911_03225_gb300.binding import FP64, MIXED
     from paper_1911_03225_gb300.serve import Request, Server, poisson_arrivals
-    build_once(rank, world)
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
-    R = args.serve_requests
     rng = np.random.default_rng(1234 + rank)
     sizes = [64, 128, 256, 512, 1024]
     arr = poisson_arrivals(200.0, R, seed=77 + rank)
     reqs = []
     for k in range(R):
         n = int(rng.choice(sizes))
-        steps = int(rng.integers(args.serve_min_steps, args.serve_max_steps + 1))
+        steps = int(rng.integers(min_steps, max_steps + 1))
         prec = FP64 if rng.random() < 0.5 else MIXED
         reqs.append(Request(k, n, steps, prec, float(arr[k]), workload_input(n, seed=10_000 + k)))
-    classes = {(n, p): args.serve_slots for n in sizes for p in (FP64, MIXED)}
-    srv = Server(workload_params(64, "fp64"), classes, hbm_budget=150e9, tick_steps=args.serve_tick,
-                 stream=stream.cuda_stream, keep_fields=False)
+    classes = {(n, p): slots for n in sizes for p in (FP64, MIXED)}
+    srv = Server(workload_params(64, "fp64"), classes, hbm_budget=150e9, tick_steps=tick, keep_fields=False,
+                 group_size=group_size)
+    warmed = srv.warm()
     barrier(world)
     with ClockSampler(local) as clk:
         results, st = srv.run(reqs)
     srv.close()
     value = max_over_ranks(st["elapsed_s"], world)
+    st = dict(st)
+    st["warm_groups"] = warmed
+    return {"value": st["cell_steps"] * world / value, "unit": UNIT,
+            "workload": "served request mix: Poisson 200 req/s, side in {64..1024}, steps U[%d,%d], 50%% FP64 / "
+                        "50%% mixed, 150 GB HBM budget, %d requests%s" % (
+                            min_steps, max_steps, R, "" if R >= 2000 else " (window scaled down from 2000)"),
+            "slots_per_class": slots, "group_size": group_size, "tick_steps": tick,
+            "serve": st, "gpu_launches": st["launches"], "clocks": clk.summary()}
+
+
+def run_serve(args, world, rank, local):
+    build_once(rank, world)
+    rec = serve_record(world, rank, local, args.serve_requests, args.serve_min_steps, args.serve_max_steps,
+                       args.serve_slots, args.serve_tick)
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": st["cell_steps"] * world / value, "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 and f32 mix",
             "data": "synthetic (Poisson arrivals, seeded fields)",
-            "config": {"workload": "served request mix: Poisson 200 req/s, side in {64..1024}, steps U[%d,%d], "
-                                   "50%% FP64 / 50%% mixed, 150 GB HBM budget, %d requests%s"
-                                   % (args.serve_min_steps, args.serve_max_steps, R,
-                                      "" if R >= 2000 else " (window scaled down from 2000)"),
-                       "slots_per_class": args.serve_slots, "tick_steps": args.serve_tick},
-            "serve": st, "gpu_launches": st["launches"], "clocks": clk.summary(),
+            "config": {"workload": rec["workload"], "slots_per_class": rec["slots_per_class"],
+                       "group_size": rec["group_size"], "tick_steps": rec["tick_steps"]},
+            "serve": rec["serve"], "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
         }), flush=True)
 
 
@@ -567,30 +641,21 @@ def run_hetero(args, world, rank, local):
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 CPU oracle (the paper publishes no code or timings)."""
+    """Reference arm: the FP64 CPU oracle on the host's cores (the paper publishes no code or
+    timings), each step a bounded sample of the workload (the coupled configuration at 512^2)."""
     if rank != 0:
         return
-    import oracle
-    n = 512
-    p = workload_params(n, "fp64")
-    op = oracle.Params(**{k: getattr(p, k) for k in oracle.Params.__dataclass_fields__})
-    K = oracle.kernel_table(n, n, n, p.nh, p.E / (2 * (1 + p.nu)), p.nu)
-    st = oracle.State(up13=workload_input(n, seed=0))
-    for _ in range(args.warmup):
-        st, _ = oracle.run(op, None, 1, K=K, state=st)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st, _ = oracle.run(op, None, 1, K=K, state=st)
-    dt = time.perf_counter() - t0
-    v = n * n * args.steps / dt
-    sample = ("coupled random-field workload on a %dx%d grid (bounded sample of the %dx%d workload), "
-              "single thread, layer-kernel precompute excluded" % (n, n, args.n, args.n))
+    oracle_sample(0.0, 0, steps=args.warmup)
+    v, k, dt, used = oracle_sample(0.0, 0, steps=args.steps)
+    sample = ("coupled random-field workload on a 512x512 grid (bounded sample of the %dx%d workload), "
+              "%d steps on %d threads, layer-kernel precompute excluded" % (args.n, args.n, k, used))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "coupled FDM under loading (oracle sample)", "n": n},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": "coupled FDM under loading (oracle sample)", "n": 512},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -604,7 +669,11 @@ def main():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--precision", default="all", choices=["fp64", "df64", "mixed", "all"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-sub-records", dest="sub_records", action="store_false",
+                    help="leave the batched and served configurations out of the default line")
+    ap.add_argument("--sub-serve-requests", type=int, default=48)
+    ap.add_argument("--sub-serve-max-steps", type=int, default=600)
     ap.add_argument("--workload", default="coupled", choices=["coupled", "batched", "serve", "hetero"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=100)

@@ -290,19 +290,37 @@ fdm_status fdm_set_launch_config(fdm_handle *h, const fdm_launch_config *cfg);
  * when max is 0) and returns count, or 0 for invalid parameters. */
 int32_t fdm_launch_candidates(const fdm_params *p, fdm_launch_config *out, int32_t max);
 
+/* Measured arithmetic rate of the current GPU, for the roofline fractions of kernels bound
+ * by arithmetic rather than by memory (not part of the paper's method).  A kernel of
+ * independent multiply-add chains occupies every SM for about 50 ms (after calibration
+ * launches) and is timed with CUDA events on `stream` (NULL = legacy default stream); the
+ * best of three launches is returned in *gflops as 1e9 flops per second, a multiply-add
+ * counting two flops.  precision: FDM_FP64 (FP64 fused multiply-add), FDM_MIXED (FP32 fused
+ * multiply-add) or FDM_DF64 (a double-word multiply then a double-word add, the library's
+ * FP32-pair arithmetic, counted as two FP64-equivalent flops).  The rate depends on the SM
+ * clock at the time of the call.  Allocates and frees a small device buffer and waits for
+ * the stream.  Errors: FDM_ERR_INVALID_ARG (bad precision, NULL gflops), FDM_ERR_OOM,
+ * FDM_ERR_DEVICE. */
+fdm_status fdm_measure_arith_rate(int32_t precision, void *stream, double *gflops);
+
 /* Static solve that allocates no device memory (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate -- e.g. a process whose HBM is already
  * fully handed out to other buffers, or an embedding that forbids allocations outside its
  * own pool).  Computes tau13 = IFFT(K FFT(U13)) + sigma_bar13 exactly like fdm_static_solve
  * with FDM_LOAD_STRESS, in FP64, for caller-owned DEVICE arrays d_up13 (input) and
- * d_tau13 (output), both [n2][n1] float64, not overlapping.  Only the grid, nz, nh, dx, E
- * and nu fields of p are used; p->precision must be FDM_FP64.
+ * d_tau13 (output), both [n2][n1] float64; the two ranges may not overlap
+ * (FDM_ERR_INVALID_ARG).  Only the grid, nz, nh, dx, E and nu fields of p are used;
+ * p->precision must be FDM_FP64.
  * Limits: n1, n2 <= 256 and nz <= 4096; larger grids return FDM_ERR_TOO_LARGE.
- * All intermediates live in one fixed device array of about 700 KB that every GPU which
+ * All intermediates live in one fixed device array of 692,992 bytes that every GPU which
  * loads this library holds until the process exits.  The first call on a device sets that
- * device up (resolves the array's address, sets kernel attributes); make that first call
- * before any stream capture.  Every call uses the same array: calls that overlap on the
- * GPU (different streams or threads at once) race and give wrong results; serialise them.
+ * device up (resolves the array's address, sets kernel attributes).  With CUDA's default
+ * lazy module loading that first call is also when the driver brings the library's device
+ * code and this array onto the device, which needs device memory: make one call (or set
+ * CUDA_MODULE_LOADING=EAGER) before committing the rest of the device memory, and before
+ * any stream capture.  If the driver cannot get that memory the call returns FDM_ERR_OOM.
+ * Every call uses the same array: calls that overlap on the GPU (different streams or
+ * threads at once) race and give wrong results; serialise them.
  * Work is enqueued on `stream` (NULL = legacy default stream) and the call returns without
  * waiting; no cudaMalloc, cudaFree or other allocating routine is called. */
 fdm_status fdm_static_solve_noalloc(const fdm_params *p, double sigma_bar13, const double *d_up13,

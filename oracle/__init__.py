@@ -47,7 +47,21 @@ def lib():
         _lib.oracle_run.restype = C.c_int
         _lib.oracle_run_hetero.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d, d, C.c_double, C.c_int]
         _lib.oracle_run_hetero.restype = C.c_int
+        _lib.oracle_set_threads.argtypes = [C.c_int]
+        _lib.oracle_set_threads.restype = C.c_int
+        _lib.oracle_threads.restype = C.c_int
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (independent rows, columns and nodes);
+    n < 1 takes every core.  Results are identical for every count.  Returns the count in
+    effect (1 when built without OpenMP).  The default is 1, the plain serial program."""
+    return lib().oracle_set_threads(int(n))
+
+
+def threads() -> int:
+    return lib().oracle_threads()
 
 
 def _p(a):

@@ -38,11 +38,37 @@
  *   G10 strain control: sigma_bar13 = 2 mu eps_bar13 - mu (nh/nz) <U13>.
  *
  * Layout: every 2-D field is row-major [n2][n1] (x1 fastest), FP64.
+ *
+ * Threads: built with OpenMP, the loops over independent rows, columns and nodes (the
+ * 2-D transform, the kernel table, the 2-D transport step) are split across threads.
+ * Every value is still computed by the same sequence of operations as in one thread, and
+ * every sum keeps its serial order, so results do not depend on the thread count
+ * (oracle_set_threads; 1 = the plain serial program).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;   /* threads of the parallel loops (1 = serial) */
+
+/* Sets the thread count of the parallel loops (n < 1: all available); returns the count
+ * in effect, 1 when the library was built without OpenMP. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n >= 1 ? n : omp_get_num_procs();
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+int oracle_threads(void) { return g_threads; }
 
 #define OR_PI 3.14159265358979323846
 
@@ -84,14 +110,19 @@ void oracle_fft1d(int n, double *re, double *im, int sign)
 /* 2-D transform of a complex [n2][n1] array: all rows, then all columns. */
 void oracle_fft2d(int n1, int n2, double *re, double *im, int sign)
 {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int y = 0; y < n2; y++) oracle_fft1d(n1, re + (size_t)y * n1, im + (size_t)y * n1, sign);
-    double *cr = malloc(sizeof(double) * n2), *ci = malloc(sizeof(double) * n2);
-    for (int x = 0; x < n1; x++) {
-        for (int y = 0; y < n2; y++) { cr[y] = re[(size_t)y * n1 + x]; ci[y] = im[(size_t)y * n1 + x]; }
-        oracle_fft1d(n2, cr, ci, sign);
-        for (int y = 0; y < n2; y++) { re[(size_t)y * n1 + x] = cr[y]; im[(size_t)y * n1 + x] = ci[y]; }
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+    {
+        double *cr = malloc(sizeof(double) * n2), *ci = malloc(sizeof(double) * n2);
+#pragma omp for schedule(static)
+        for (int x = 0; x < n1; x++) {
+            for (int y = 0; y < n2; y++) { cr[y] = re[(size_t)y * n1 + x]; ci[y] = im[(size_t)y * n1 + x]; }
+            oracle_fft1d(n2, cr, ci, sign);
+            for (int y = 0; y < n2; y++) { re[(size_t)y * n1 + x] = cr[y]; im[(size_t)y * n1 + x] = ci[y]; }
+        }
+        free(cr); free(ci);
     }
-    free(cr); free(ci);
 }
 
 /* signed frequency index k~ in (-n/2, n/2]; at Nyquist k~ = +n/2 */
@@ -125,6 +156,7 @@ double oracle_layer_symbol(double n1, double n2, double n3, double mu, double nu
  */
 void oracle_kernel_table(int n1, int n2, int nz, int nh, double mu, double nu, double *K)
 {
+#pragma omp parallel for schedule(dynamic, 4) num_threads(g_threads) if (g_threads > 1)
     for (int k2 = 0; k2 < n2; k2++) {
         for (int k1 = 0; k1 < n1; k1++) {
             /* frequencies on a cubic-voxel grid (dx cancels in the direction n) */
@@ -481,6 +513,7 @@ void oracle_knp2d_step(int n1, int n2, double h, double theta, double dt, int ti
                        const double *phi, const double *v0, double *out)
 {
 #define P(jj, kk) phi[(size_t)wrap((kk), n2) * n1 + wrap((jj), n1)]
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int k = 0; k < n2; k++) {
         for (int j = 0; j < n1; j++) {
             double f0 = P(j, k);

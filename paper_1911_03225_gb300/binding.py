@@ -48,7 +48,8 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_batch_destroy", "fdm_get_launch_config", "fdm_batch_get_launch_config",
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
-           "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field"]
+           "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field",
+           "fdm_measure_arith_rate"]
 
 
 class CParams(C.Structure):
@@ -169,6 +170,8 @@ def load():
     lib.fdm_sync.argtypes = [H]
     lib.fdm_static_solve_noalloc.argtypes = [C.POINTER(CParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fdm_static_solve_noalloc.restype = C.c_int
+    lib.fdm_measure_arith_rate.argtypes = [C.c_int32, C.c_void_p, d]
+    lib.fdm_measure_arith_rate.restype = C.c_int
     PP = C.POINTER(CParams)
     lib.fdm_batch_create.argtypes = [C.c_int32, PP, C.c_void_p, C.POINTER(H)]
     lib.fdm_batch_device_bytes.argtypes = [C.c_int32, PP]
@@ -245,6 +248,16 @@ def default_params(n1: int, n2: int) -> Params:
 
 def device_bytes(p: Params) -> int:
     return int(load().fdm_device_bytes(C.byref(p.to_c())))
+
+
+def measure_arith_rate(precision: int, stream: Optional[int] = None) -> float:
+    """Measured multiply-add rate of the current GPU in GFLOP/s (multiply-add = 2 flops):
+    FP64, FP32 (``MIXED``) or double-word (``DF64``, two FP64-equivalent flops per
+    double-word multiply-add).  About 0.2 s of GPU time."""
+    out = C.c_double(0.0)
+    _check(load().fdm_measure_arith_rate(int(precision), C.c_void_p(stream or 0), C.byref(out)),
+           "fdm_measure_arith_rate")
+    return float(out.value)
 
 
 def static_solve_noalloc(params: Params, sigma_bar13: float, d_up13: int, d_tau13: int,

@@ -9,7 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfdm_gb300.so")
-SOURCES = ["fdm_kernels.cu", "fdm_tune.cu", "fdm_capi.cu", "fdm_batch.cu", "fdm_noalloc.cu", "fdm_hetero.cu"]
+SOURCES = ["fdm_kernels.cu", "fdm_tune.cu", "fdm_capi.cu", "fdm_batch.cu", "fdm_noalloc.cu", "fdm_hetero.cu", "fdm_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 

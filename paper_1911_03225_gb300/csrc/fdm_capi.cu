@@ -15,39 +15,19 @@ namespace fdm {
 
 const double kPi = 3.14159265358979323846;
 
+// twiddle tables exp(-2 pi i m / n) and the pass tables of an L-point transform, built on
+// the device by the one routine every path uses (launch_twiddle_tables)
 template <typename T>
 static fdm_status upload_twiddles(void* dst, int n, cudaStream_t s) {
-    std::vector<T> tw(2 * (size_t)n);
-    for (int m = 0; m < n; ++m) {
-        double a = 2.0 * kPi * (double)m / (double)n;
-        tw[2 * m] = (T)std::cos(a);
-        tw[2 * m + 1] = (T)(-std::sin(a));
-    }
-    FDM_CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    FDM_CK(cudaStreamSynchronize(s));
+    launch_twiddle_tables<T>(dst, n, nullptr, 0, s);
+    FDM_CK(cudaGetLastError());
     return FDM_OK;
 }
 
-// per-pass twiddle tables of an L-point transform (layout: see pass_table_len)
 template <typename T>
 static fdm_status upload_pass_twiddles(void* dst, int L, cudaStream_t s) {
-    const int len = pass_table_len(L);
-    std::vector<T> tw(2 * (size_t)len);
-    int off = 0, Ns = 1;
-    auto emit = [&](int R) {
-        for (int r = 1; r < R; ++r)
-            for (int k = 0; k < Ns; ++k) {
-                double a = 2.0 * kPi * (double)r * (double)k / ((double)Ns * R);
-                tw[2 * (size_t)(off + (r - 1) * Ns + k)] = (T)std::cos(a);
-                tw[2 * (size_t)(off + (r - 1) * Ns + k) + 1] = (T)(-std::sin(a));
-            }
-        off += (R - 1) * Ns;
-    };
-    while (Ns * 8 <= L) { emit(8); Ns *= 8; }
-    if (Ns * 4 == L) emit(4);
-    else if (Ns * 2 == L) emit(2);
-    FDM_CK(cudaMemcpyAsync(dst, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
-    FDM_CK(cudaStreamSynchronize(s));
+    launch_twiddle_tables<T>(nullptr, 0, dst, L, s);
+    FDM_CK(cudaGetLastError());
     return FDM_OK;
 }
 
@@ -94,17 +74,11 @@ fdm_status build_group(Dev& d, Arena& A, const fdm_params& p, int count, int gat
     if ((st = upload_pass_twiddles<T>(d.pt1, p.n1 / 2, s))) return st;
     if ((st = upload_pass_twiddles<T>(d.pt2, p.n2, s))) return st;
     // layer weights |chi-hat(k3)|^2, k3 in [0, nz/2] (Sec. 3.2.1 layer of nh voxels)
-    std::vector<double> w3((size_t)p.nz / 2 + 1);
-    for (int k3 = 0; k3 <= p.nz / 2; ++k3) {
-        if (k3 == 0) { w3[k3] = (double)p.nh * p.nh; continue; }
-        double sn = std::sin(kPi * (double)k3 * p.nh / p.nz), sd = std::sin(kPi * (double)k3 / p.nz);
-        w3[k3] = (sn * sn) / (sd * sd);
-    }
     void* dw3 = nullptr;
     void* dK64 = nullptr;
-    if ((st = A.alloc(&dw3, w3.size() * sizeof(double)))) return st;
+    if ((st = A.alloc(&dw3, ((size_t)p.nz / 2 + 1) * sizeof(double)))) return st;
     if ((st = A.alloc(&dK64, nk * sizeof(double)))) return st;
-    FDM_CK(cudaMemcpyAsync(dw3, w3.data(), w3.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_layer_weights((double*)dw3, p.nz, p.nh, s);
     const double mu = p.E / (2.0 * (1.0 + p.nu));
     launch_kernel_table((double*)dK64, p.n1, p.n2, p.nz, p.nh, mu, p.nu, (const double*)dw3, s);
     FDM_CK(cudaGetLastError());

@@ -81,16 +81,33 @@ __host__ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15);
 // sequence stride for L elements (one extra slot so that rows start on different banks)
 __host__ __device__ __forceinline__ int padded_len(int L) { return L + 1; }
 
+// Pass plan of an L-point transform (L a power of two): radix 8 while Ns * 8 <= L, then one
+// radix-4 or radix-2 pass.  pass_radix(L, Ns) is the radix of the pass at sub-length Ns, 0
+// once the transform is complete.  The transform, its twiddle-table length and the tables'
+// contents all follow this one function.
+__host__ __device__ __forceinline__ int pass_radix(int L, int Ns) {
+    return Ns * 8 <= L ? 8 : (Ns * 4 == L ? 4 : (Ns * 2 == L ? 2 : 0));
+}
+
 // Twiddles of the in-place FFT, one table per pass: for the pass of radix R at sub-length Ns,
 // entry (r - 1) * Ns + k holds exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns, so that a warp
-// reads consecutive k.  Passes: radix 8 while Ns * 8 <= L, then one radix-4 or radix-2 pass.
-// pass_table_len(L) = total entries for all passes of an L-point transform.
+// reads consecutive k.  pass_table_len(L) = total entries for all passes of an L-point
+// transform.
 __host__ __device__ __forceinline__ int pass_table_len(int L) {
-    int n = 0, Ns = 1;
-    while (Ns * 8 <= L) { n += 7 * Ns; Ns *= 8; }
-    if (Ns * 4 == L) n += 3 * Ns;
-    else if (Ns * 2 == L) n += Ns;
+    int n = 0;
+    for (int Ns = 1, R; (R = pass_radix(L, Ns)) != 0; Ns *= R) n += (R - 1) * Ns;
     return n;
+}
+// Entry i < pass_table_len(L) of those tables is exp(-2 pi i num / den).
+__host__ __device__ __forceinline__ void pass_table_entry(int L, int i, int* num, int* den) {
+    int Ns = 1, R = pass_radix(L, 1);
+    while (i >= (R - 1) * Ns) {
+        i -= (R - 1) * Ns;
+        Ns *= R;
+        R = pass_radix(L, Ns);
+    }
+    *num = (i / Ns + 1) * (i % Ns);
+    *den = Ns * R;
 }
 
 // Batched in-place FFT in shared memory: Stockham autosort passes (Govindaraju et al., SC'08)
@@ -141,13 +158,14 @@ __device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int
 template <int S, typename T>
 __device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, const cpx<T>* __restrict__ pt) {
     int Ns = 1;
-    while (Ns * 8 <= L) {
+    while (pass_radix(L, Ns) == 8) {
         stockham_pass_ip<T, 8, 1, S>(a, L, nseq, ld, Ns, pt);
         pt += 7 * Ns;
         Ns *= 8;
     }
-    if (Ns * 4 == L) stockham_pass_ip<T, 4, 2, S>(a, L, nseq, ld, Ns, pt);
-    else if (Ns * 2 == L) stockham_pass_ip<T, 2, 4, S>(a, L, nseq, ld, Ns, pt);
+    const int R = pass_radix(L, Ns);
+    if (R == 4) stockham_pass_ip<T, 4, 2, S>(a, L, nseq, ld, Ns, pt);
+    else if (R == 2) stockham_pass_ip<T, 2, 4, S>(a, L, nseq, ld, Ns, pt);
 }
 
 // ---------------------------------------------------------------------------------

@@ -100,6 +100,11 @@ template <typename T>
 void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
                      cudaStream_t s);
 void launch_pair_to_double(const float* hi, const float* lo, double* out, size_t n, cudaStream_t s);
+// twiddles exp(-2 pi i m / n) into tw (cpx<T> [n]) and the pass tables of an L-point
+// transform into pt (cpx<T> [pass_table_len(L)]); either may be null
+template <typename T> void launch_twiddle_tables(void* tw, int n, void* pt, int L, cudaStream_t s);
+// |chi-hat(k3)|^2 of a layer of nh voxels in a cell of nz, k3 in [0, nz/2] (double [nz/2 + 1])
+void launch_layer_weights(double* w3, int nz, int nh, cudaStream_t s);
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
                          cudaStream_t s);
 void launch_stress_table(double* Kh, int n1, int n2, int nz, int comp, double mu, double nu, const double* w3,

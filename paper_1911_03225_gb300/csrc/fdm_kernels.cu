@@ -1191,6 +1191,48 @@ void launch_curl_inverse(const Dev& d, const T* a11, const T* a12, T* phi_out, d
     launch_row_inverse<T>(d, spec, phi_out, ROW_PLAIN, 0.0, 1, s);
 }
 
+// Twiddle tables, computed in FP64 from exact rational angles (sincospi takes the fraction of
+// pi, so no rounded multiple of pi enters) and rounded once to the field type:
+// tw[m] = exp(-2 pi i m / n) for m < n; pt = the pass tables of an L-point transform
+// (pass_table_entry).  Every path that needs these tables builds them here.
+template <typename T>
+__global__ void twiddle_tables_kernel(cpx<T>* __restrict__ tw, int n, cpx<T>* __restrict__ pt, int L) {
+    const int len = pt ? pass_table_len(L) : 0;
+    const int top = n > len ? n : len;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < top; i += gridDim.x * blockDim.x) {
+        double sn, cs;
+        if (tw && i < n) {
+            sincospi(2.0 * (double)i / (double)n, &sn, &cs);
+            tw[i] = mk(T(cs), T(-sn));
+        }
+        if (i < len) {
+            int num, den;
+            pass_table_entry(L, i, &num, &den);
+            sincospi(2.0 * (double)num / (double)den, &sn, &cs);
+            pt[i] = mk(T(cs), T(-sn));
+        }
+    }
+}
+template <typename T> void launch_twiddle_tables(void* tw, int n, void* pt, int L, cudaStream_t s) {
+    twiddle_tables_kernel<T><<<8, 256, 0, s>>>((cpx<T>*)tw, n, (cpx<T>*)pt, L);
+}
+
+// layer weights |chi-hat(k3)|^2 = sin^2(pi k3 nh / nz) / sin^2(pi k3 / nz) for k3 in
+// [0, nz/2] (nh^2 at k3 = 0): the transform of the layer's indicator (Sec. 3.2.1)
+__global__ void layer_weights_kernel(double* __restrict__ w3, int nz, int nh) {
+    for (int k3 = blockIdx.x * blockDim.x + threadIdx.x; k3 <= nz / 2; k3 += gridDim.x * blockDim.x) {
+        if (k3 == 0) {
+            w3[0] = (double)nh * (double)nh;
+        } else {
+            const double sn = sinpi((double)k3 * (double)nh / (double)nz), sd = sinpi((double)k3 / (double)nz);
+            w3[k3] = (sn * sn) / (sd * sd);
+        }
+    }
+}
+void launch_layer_weights(double* w3, int nz, int nh, cudaStream_t s) {
+    layer_weights_kernel<<<8, 256, 0, s>>>(w3, nz, nh);
+}
+
 void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, double nu, const double* w3,
                          cudaStream_t s) {
     int total = (n1 / 2 + 1) * (n2 / 2 + 1);
@@ -1253,7 +1295,8 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     template void launch_convert<T>(const double*, T*, size_t, double, cudaStream_t);                       \
     template void launch_alpha_sums<T>(const Dev&, int, double*, int, cudaStream_t);                        \
     template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
-                                     cudaStream_t);
+                                     cudaStream_t);                                                     \
+    template void launch_twiddle_tables<T>(void*, int, void*, int, cudaStream_t);
 FDM_INST(double)
 FDM_INST(float)
 FDM_INST(df)

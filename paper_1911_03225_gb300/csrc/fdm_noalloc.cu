@@ -31,51 +31,15 @@ constexpr size_t kOffPart = kOffW3 + round_up((size_t)kMaxNz / 2 + 1);
 constexpr size_t kOffSc = kOffPart + round_up((size_t)kMaxSide);
 constexpr size_t kScratchDoubles = kOffSc + round_up(sizeof(fdm_dev_scalars) / sizeof(double) + 1);
 
-// The scratch (about 710 KB).  In host code this name is only a stand-in for the device
+// The scratch: 692,992 bytes.  In host code this name is only a stand-in for the device
 // symbol; kernels get its device address from cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+static_assert(kScratchDoubles * sizeof(double) == 692992, "the size stated in include/fdm.h");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
 bool g_ready[kMaxDevices] = {};
-
-// twiddles exp(-2 pi i m / n) and the layer weights |chi-hat(k3)|^2 (Sec. 3.2.1)
-__global__ void noalloc_tables_kernel(double* tw1, int n1, double* tw2, int n2, double* w3, int nz, int nh) {
-    const int top = max(max(n1, n2), nz / 2 + 1);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < top; i += gridDim.x * blockDim.x) {
-        double s, c;
-        if (i < n1) { sincospi(2.0 * (double)i / (double)n1, &s, &c); tw1[2 * i] = c; tw1[2 * i + 1] = -s; }
-        if (i < n2) { sincospi(2.0 * (double)i / (double)n2, &s, &c); tw2[2 * i] = c; tw2[2 * i + 1] = -s; }
-        if (i <= nz / 2) {
-            if (i == 0) {
-                w3[0] = (double)nh * (double)nh;
-            } else {
-                double sn = sinpi((double)i * (double)nh / (double)nz), sd = sinpi((double)i / (double)nz);
-                w3[i] = (sn * sn) / (sd * sd);
-            }
-        }
-    }
-}
-
-// per-pass twiddle tables of an L-point transform (entry layout as in pass_table_len)
-__global__ void noalloc_pass_table_kernel(double* pt, int L) {
-    const int len = pass_table_len(L);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-        int off = 0, Ns = 1, R = 8;
-        while (true) {
-            R = (Ns * 8 <= L) ? 8 : (Ns * 4 == L ? 4 : 2);
-            if (i < off + (R - 1) * Ns) break;
-            off += (R - 1) * Ns;
-            Ns *= R;
-        }
-        const int r = (i - off) / Ns + 1, k = (i - off) % Ns;
-        double sn, cs;
-        sincospi(2.0 * (double)r * (double)k / ((double)Ns * R), &sn, &cs);
-        pt[2 * i] = cs;
-        pt[2 * i + 1] = -sn;
-    }
-}
 
 bool pow2_between(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
@@ -84,14 +48,16 @@ bool pow2_between(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v 
 fdm_status setup_device(int dev, double** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_ready[dev]) {
+        // resolving the symbol loads the library's device code onto this device if it is not
+        // there yet (CUDA loads modules lazily by default): that allocation by the driver is
+        // why the first call should come before the caller commits its memory
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e == cudaSuccess && ptr == nullptr) e = cudaErrorInvalidSymbol;
+        if (e == cudaSuccess) e = configure_kernels<double>();
+        if (e != cudaSuccess) {
             cudaGetLastError();
-            return FDM_ERR_DEVICE;
-        }
-        if (configure_kernels<double>() != cudaSuccess) {
-            cudaGetLastError();
-            return FDM_ERR_DEVICE;
+            return e == cudaErrorMemoryAllocation ? FDM_ERR_OOM : FDM_ERR_DEVICE;
         }
         g_scratch_ptr[dev] = static_cast<double*>(ptr);
         g_ready[dev] = true;
@@ -107,13 +73,20 @@ using namespace fdm;
 
 extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma_bar13, const double* d_up13,
                                                double* d_tau13, void* stream) {
-    if (!p || !d_up13 || !d_tau13 || d_up13 == d_tau13) return FDM_ERR_INVALID_ARG;
+    if (!p || !d_up13 || !d_tau13) return FDM_ERR_INVALID_ARG;
     if (p->precision != FDM_FP64 || !std::isfinite(sigma_bar13)) return FDM_ERR_INVALID_ARG;
     const int nz = p->nz == 0 ? p->n1 : p->nz;
     if (!pow2_between(p->n1, 16, 1 << 30) || !pow2_between(p->n2, 16, 1 << 30)) return FDM_ERR_INVALID_ARG;
     if (p->n1 > kMaxSide || p->n2 > kMaxSide || nz > kMaxNz) return FDM_ERR_TOO_LARGE;
     if (nz < 1 || p->nh < 1 || p->nh > nz) return FDM_ERR_INVALID_ARG;
-    if (!(p->E > 0.0) || !(p->nu > -1.0 && p->nu < 0.5) || !(p->dx > 0.0)) return FDM_ERR_INVALID_ARG;
+    if (!(p->E > 0.0) || !(p->nu > -1.0 && p->nu < 0.5) || !(p->dx > 0.0) || !std::isfinite(p->dx) ||
+        !std::isfinite(p->E))
+        return FDM_ERR_INVALID_ARG;
+    {   // the output is written while the input is still being read: the arrays may not overlap
+        const size_t n = (size_t)p->n1 * p->n2;
+        const uintptr_t a = (uintptr_t)d_up13, b = (uintptr_t)d_tau13;
+        if (a < b + n * sizeof(double) && b < a + n * sizeof(double)) return FDM_ERR_INVALID_ARG;
+    }
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -155,12 +128,14 @@ extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma
         cudaGetLastError();
         return FDM_ERR_DEVICE;
     }
-    noalloc_tables_kernel<<<8, 256, 0, s>>>(base + kOffTw1, p->n1, base + kOffTw2, p->n2, base + kOffW3, nz, p->nh);
-    noalloc_pass_table_kernel<<<1, 256, 0, s>>>(base + kOffPt1, p->n1 / 2);
-    noalloc_pass_table_kernel<<<1, 256, 0, s>>>(base + kOffPt2, p->n2);
+    // the same table routines as the handle path (fdm_create)
+    launch_twiddle_tables<double>(base + kOffTw1, p->n1, base + kOffPt1, p->n1 / 2, s);
+    launch_twiddle_tables<double>(base + kOffTw2, p->n2, base + kOffPt2, p->n2, s);
+    launch_layer_weights(base + kOffW3, nz, p->nh, s);
     const double mu = p->E / (2.0 * (1.0 + p->nu));
     launch_kernel_table(base + kOffK, p->n1, p->n2, nz, p->nh, mu, p->nu, base + kOffW3, s);
     launch_static<double>(d, s);
-    if (cudaGetLastError() != cudaSuccess) return FDM_ERR_DEVICE;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FDM_ERR_OOM : FDM_ERR_DEVICE;
     return FDM_OK;
 }

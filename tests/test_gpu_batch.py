@@ -139,6 +139,57 @@ def test_server_retires_failed_requests_and_keeps_the_others():
         assert by_id[k].t == info.t
 
 
+def test_hbm_budget_bounds_admission_while_slots_are_free():
+    """The budget is a ledger of device memory actually held: with room for one group of the
+    class, a second request waits although the class allows four resident simulations, and
+    runs once the first has finished (its idle group then serves it).  After every tick the
+    ledger equals the device bytes of the allocated groups and the device's used memory
+    follows it; closing the server returns the memory.  A request of a class the server does
+    not offer, and one whose group alone is over the budget, are retired at arrival."""
+    import torch
+    n = 64
+    base = coupled(n)
+    ups = [inputs.random_up(n, seed=300 + k, ell=6.0) for k in range(3)]
+    probe = Server(base, {(n, B.FP64): 4, (256, B.FP64): 1}, hbm_budget=1e12, tick_steps=4, group_size=1)
+    one = probe.group_bytes((n, B.FP64))
+    big = probe.group_bytes((256, B.FP64))
+    assert big > 2 * one
+    reqs = [Request(rid=k, n=n, steps=12 + 4 * k, precision=B.FP64, arrival=0.0, up13=ups[k]) for k in range(3)]
+    reqs.append(Request(rid=3, n=128, steps=8, precision=B.FP64, arrival=0.0, up13=inputs.random_up(128, seed=1)))
+    reqs.append(Request(rid=4, n=256, steps=8, precision=B.FP64, arrival=0.0, up13=inputs.random_up(256, seed=2)))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    seen = []
+
+    def monitor(srv):
+        torch.cuda.synchronize()
+        assert srv.bytes_in_use == sum(g.nbytes for g in srv.groups) <= srv.hbm_budget
+        assert srv.resident <= 1
+        seen.append((srv.bytes_in_use, free0 - torch.cuda.mem_get_info()[0]))
+
+    srv = Server(base, {(n, B.FP64): 4, (256, B.FP64): 1}, hbm_budget=1.5 * one, tick_steps=4, group_size=1)
+    try:
+        results, stats = srv.run(reqs, monitor=monitor)
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+    assert stats["completed"] == 3 and stats["max_resident"] == 1 and stats["peak_bytes"] == one
+    assert {r.rid: r.status for r in srv.failed} == {3: B.FDM_ERR_INVALID_ARG, 4: B.FDM_ERR_OOM}
+    assert stats["groups_allocated"] == 1    # the idle group of the finished request is reused
+    # small buffers share the driver's pages, so the device's used memory can sit a little
+    # below or above the ledger; it never holds more than the one group
+    for ledger, used in seen:
+        assert ledger == one and used < one + (64 << 20)
+    by_id = {r.rid: r for r in results}
+    fin = sorted(results, key=lambda r: r.finished)
+    assert [r.rid for r in fin] == [0, 1, 2]
+    assert by_id[1].admitted >= by_id[0].finished and by_id[2].admitted >= by_id[1].finished
+    for k in range(3):
+        ref, info = alone(base, ups[k], reqs[k].steps)
+        np.testing.assert_array_equal(by_id[k].up13, ref["up13"])
+
+
 def test_allocation_failures_release_everything():
     """Host-side fault injection: each allocation of a handle or a batch in turn fails; the
     call returns FDM_ERR_OOM with no handle and no device memory left behind."""

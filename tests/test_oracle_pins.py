@@ -963,3 +963,31 @@ def test_zero_mean_stress_stage_then_strain_rate_stage():
     st2, _ = oracle.run(p2, None, 10, state=st1)
     assert st2.step == 25 and st2.t > st1.t
     assert st2.eps_bar13 == pytest.approx(1e-3 * st2.t, rel=1e-14)
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's loops over independent rows, columns and nodes may run on several threads;
+    every value is still formed by the same operations and every sum in its serial order, so
+    the transform, the Green-kernel table and whole coupled and ring runs are bit-identical
+    for every thread count."""
+    prev = oracle.threads()
+    n1, n2 = 64, 32
+    up0 = inputs.random_up(64, seed=21, ell=5.0)[:n2, :n1].copy()
+    a11, a12 = inputs.ring_alpha(64, r0=15.0, sigma=2.0)
+    coupled = oracle.Params(n1=n1, n2=n2, velocity_mode=1, loading_mode=1, eps_bar13_rate=1e-3, cfl=0.4)
+    ring = oracle.Params(n1=64, n2=64, v0=-1.0, theta=2.0, cfl=0.4)
+    runs = []
+    try:
+        for threads in (1, 3, 0):
+            oracle.set_threads(threads)
+            u_ring, _, _ = oracle.curl_inverse(a11, a12, 0.1)
+            st_c, rc_c = oracle.run(coupled, up0, 12)
+            st_r, rc_r = oracle.run(ring, u_ring, 12)
+            assert rc_c == rc_r == 0
+            runs.append((oracle.fft2d(up0), oracle.kernel_table(n1, n2, 16, 3, 0.4, 0.25), st_c.up13, st_c.tau13,
+                         st_c.t, st_r.up13, st_r.tau13))
+    finally:
+        oracle.set_threads(prev)
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            np.testing.assert_array_equal(a, b)

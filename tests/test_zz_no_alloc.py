@@ -63,6 +63,44 @@ def test_noalloc_static_solve_matches_handle_path_twice(shape, nh):
         assert got.mean() == pytest.approx(sig, abs=1e-13)
 
 
+def test_noalloc_calls_allocate_no_device_memory():
+    """After one warm-up call (which lets the driver load the library's device code and its
+    fixed array), further calls leave the device's free memory and the caller's allocator
+    untouched: the entry point is usable by a process whose memory is fully committed."""
+    import torch
+    n2, n1 = 128, 256
+    p = Params(n1=n1, n2=n2, nh=3)
+    ups = [torch.from_numpy(inputs.random_up(256, seed=s, ell=4.0)[:n2, :n1].copy()).cuda() for s in (23, 24)]
+    outs = [torch.empty_like(u) for u in ups]
+    stream = torch.cuda.current_stream().cuda_stream
+    B.static_solve_noalloc(p, 0.01, ups[0].data_ptr(), outs[0].data_ptr(), stream)   # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for k in range(4):
+        B.static_solve_noalloc(p, 0.01 * k, ups[k % 2].data_ptr(), outs[k % 2].data_ptr(), stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    ref = _reference_tau(p, ups[1].cpu().numpy(), 0.03)
+    got = outs[1].cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL
+
+
+def test_noalloc_rejects_overlapping_arrays():
+    import torch
+    p = Params(n1=64, n2=64)
+    d = torch.zeros(2 * 64 * 64, dtype=torch.float64, device="cuda")
+    for off in (0, 1, 64 * 64 - 1):
+        with pytest.raises(B.FDMError) as e:
+            B.static_solve_noalloc(p, 0.0, d.data_ptr(), d[off:].data_ptr())
+        assert e.value.status == B.FDM_ERR_INVALID_ARG
+    with pytest.raises(B.FDMError) as e:
+        B.static_solve_noalloc(Params(n1=64, n2=64, dx=float("inf")), 0.0, d.data_ptr(), d[64 * 64:].data_ptr())
+    assert e.value.status == B.FDM_ERR_INVALID_ARG
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     import torch
     p = Params(n1=512, n2=64)
