@@ -421,4 +421,156 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
     return acc * inv_w;
 }
 
+// ---------------------------------------------------------------------------------
+// Packed FP32 pairs.  Blackwell issues two FP32 additions, multiplications or fused
+// multiply-adds as one instruction (add/sub/mul/fma .rn.f32x2), each lane rounded exactly
+// as the scalar operation.  The FP32 stencil updates two nodes at once in the two lanes:
+// every lane's result is the one the same operations give on that node alone, so it does
+// not depend on which node shares its pair.  Comparisons, min/max, selects and the
+// special-function reciprocal (square root) stay per lane.
+// ---------------------------------------------------------------------------------
+struct f2 { float x, y; };
+__device__ __forceinline__ f2 mkf2(float a, float b) { f2 r; r.x = a; r.y = b; return r; }
+__device__ __forceinline__ f2 bcast(float a) { return mkf2(a, a); }
+__device__ __forceinline__ unsigned long long pk2(f2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ f2 upk2(unsigned long long v) {
+    f2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(r);
+}
+__device__ __forceinline__ f2 operator-(f2 a) { return mkf2(-a.x, -a.y); }
+// a b + c, one rounding per lane
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(r);
+}
+__device__ __forceinline__ f2 sel2(bool cx, bool cy, f2 a, f2 b) { return mkf2(cx ? a.x : b.x, cy ? a.y : b.y); }
+__device__ __forceinline__ f2 fmax2(f2 a, f2 b) { return mkf2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 fmin2(f2 a, f2 b) { return mkf2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+
+// minmod of three floats: the argument of least magnitude when all three are nonzero and of
+// one sign, else zero; computed from the magnitudes' minimum and the sign bits
+__device__ __forceinline__ float minmod3_bits(float a, float b, float c) {
+    const unsigned ua = __float_as_uint(a), ub = __float_as_uint(b), uc = __float_as_uint(c);
+    const float m = fminf(fminf(fabsf(a), fabsf(b)), fabsf(c));
+    const bool agree = (((ua ^ ub) | (ua ^ uc)) & 0x80000000u) == 0u;
+    return agree ? __uint_as_float(__float_as_uint(m) | (ua & 0x80000000u)) : 0.0f;
+}
+__device__ __forceinline__ f2 minmod3(f2 a, f2 b, f2 c) {
+    return mkf2(minmod3_bits(a.x, b.x, c.x), minmod3_bits(a.y, b.y, c.y));
+}
+// v / |(p, q)| per lane from r2 = p^2 + q^2, zero at the origin (guarded as tguard)
+__device__ __forceinline__ f2 scaled_rsqrt2(f2 r2, f2 v) {
+    return mkf2(tguard(r2.x) ? v.x * rsqrtf(r2.x) : 0.0f, tguard(r2.y) ? v.y * rsqrtf(r2.y) : 0.0f);
+}
+
+// The KNP update of two nodes (Sec. 3.2.3 Steps 1-4, readings G1-G7), in cell units as
+// knp_node, for FP32 fields given as differences to each node's own value: f(i, j) returns
+// the pair (U(node a + (i, j)) - U(a), U(node b + (i, j)) - U(b)), so f(0, 0) = 0; returns
+// the two increments U^{n+1} - U^n.
+template <typename F>
+__device__ __forceinline__ f2 knp_node_x2(F f, f2 v0, float dt_h, float theta, int time_level) {
+    const f2 th = bcast(theta), hf = bcast(0.5f);
+    // Step 1: first differences (f(0, 0) = 0) and limited second differences
+    const f2 xm1 = f(-1, 0), xp1 = f(1, 0), ym1 = f(0, -1), yp1 = f(0, 1);
+    const f2 dxm3 = xm1 - f(-2, 0), dxm1 = -xm1, dxp1 = xp1, dxp3 = f(2, 0) - xp1;
+    const f2 dym3 = ym1 - f(0, -2), dym1 = -ym1, dyp1 = yp1, dyp3 = f(0, 2) - yp1;
+    const f2 cxl = th * (dxp1 - dxm1), cyl = th * (dyp1 - dym1);
+    const f2 Sxp = minmod3(th * (dxp3 - dxp1), hf * (dxp3 - dxm1), cxl);
+    const f2 Sxm = minmod3(cxl, hf * (dxp1 - dxm3), th * (dxm1 - dxm3));
+    const f2 Syp = minmod3(th * (dyp3 - dyp1), hf * (dyp3 - dym1), cyl);
+    const f2 Sym = minmod3(cyl, hf * (dyp1 - dym3), th * (dym1 - dym3));
+    // one-sided derivatives at the node (times h)
+    const f2 px0 = fma2(-hf, Sxp, dxp1), px1 = fma2(hf, Sxm, dxm1);
+    const f2 qy0 = fma2(-hf, Syp, dyp1), qy1 = fma2(hf, Sym, dym1);
+    // Step 2: one-sided speeds over the four pairs, from the three pairs that attain the
+    // extremes (the q of least magnitude for dH/dp, the p of least magnitude for dH/dq)
+    const bool tqx = fabsf(qy1.x) < fabsf(qy0.x), tqy = fabsf(qy1.y) < fabsf(qy0.y);
+    const bool tpx = fabsf(px1.x) < fabsf(px0.x), tpy = fabsf(px1.y) < fabsf(px0.y);
+    const f2 qm = sel2(tqx, tqy, qy1, qy0), qo = sel2(tqx, tqy, qy0, qy1), pm = sel2(tpx, tpy, px1, px0);
+    const f2 r0 = scaled_rsqrt2(fma2(px0, px0, qm * qm), v0);
+    const f2 r1 = scaled_rsqrt2(fma2(px1, px1, qm * qm), v0);
+    const f2 rc = scaled_rsqrt2(fma2(pm, pm, qo * qo), v0);
+    const f2 z = bcast(0.0f);
+    const f2 hp0 = r0 * px0, hp1 = r1 * px1, hq0 = sel2(tpx, tpy, r1, r0) * qm, hq1 = rc * qo;
+    const f2 ap = fmax2(fmax2(z, hp0), hp1), am = fmin2(fmin2(z, hp0), hp1);
+    const f2 bp = fmax2(fmax2(z, hq0), hq1), bm = fmin2(fmin2(z, hq0), hq1);
+    // Step 4 weights (G1, G5), each direction normalised on its own
+    f2 dxw = ap - am, dyw = bp - bm;
+    const bool gx0 = tguard(dxw.x), gx1 = tguard(dxw.y), gy0 = tguard(dyw.x), gy1 = tguard(dyw.y);
+    const f2 ix = mkf2(gx0 ? trcp(dxw.x) : 1.0f, gx1 ? trcp(dxw.y) : 1.0f);
+    const f2 iy = mkf2(gy0 ? trcp(dyw.x) : 1.0f, gy1 ? trcp(dyw.y) : 1.0f);
+    const f2 nx[2] = {sel2(gx0, gx1, -am, hf) * ix, sel2(gx0, gx1, ap, hf) * ix};
+    const f2 ny[2] = {sel2(gy0, gy1, -bm, hf) * iy, sel2(gy0, gy1, bp, hf) * iy};
+    const f2 dth = bcast(dt_h);
+    const f2 vdt = v0 * dth;          // v0 dt / h
+    const f2 hvdt = hf * vdt;         // v0 dt / (2 h)
+    // Step 3: values at the four intermediate points (G2, G3), the limited quadratics of
+    // each side in cell units: X(e) = D e + S e (e + sg) / 2, h X'(e) = D + S (e + sg / 2)
+    const f2 Dy[2] = {dyp1, dym1}, Sy[2] = {Syp, Sym};
+    f2 Y[2], dY[2], ey[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float sg = (t == 0) ? -1.0f : 1.0f;
+        ey[t] = (t == 0 ? bp : bm) * dth;
+        Y[t] = fma2(Dy[t], ey[t], hf * ((Sy[t] * ey[t]) * (ey[t] + bcast(sg))));
+        dY[t] = fma2(Sy[t], ey[t] + bcast(0.5f * sg), Dy[t]);
+    }
+    const f2 Dx[2] = {dxp1, dxm1}, Sxs[2] = {Sxp, Sxm};
+    f2 acc = z;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int cx = (s == 0) ? 1 : -1;
+        const float sg = (s == 0) ? -1.0f : 1.0f;
+        const f2 ex = (s == 0 ? ap : am) * dth;
+        const f2 X = fma2(Dx[s], ex, hf * ((Sxs[s] * ex) * (ex + bcast(sg))));
+        const f2 dX = fma2(Sxs[s], ex + bcast(0.5f * sg), Dx[s]);
+        const f2 fx = f(cx, 0);
+        f2 accs = z;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int cy = (t == 0) ? 1 : -1;
+            // h^2 times the bilinear cross term of the quadrant cell
+            const f2 mixed = (f(cx, cy) - f(0, cy)) - fx;
+            const f2 cross = (cx * cy > 0) ? mixed : -mixed;
+            const f2 val = fma2(cross * ex, ey[t], X + Y[t]);
+            f2 p = fma2(cross, ey[t], dX);
+            f2 q = fma2(cross, ex, dY[t]);
+            if (time_level == 0) {
+                // (p, q) -= dt/2 Hess grad_(p,q) H, grad H = v0 (p, q) / |(p, q)|
+                const f2 w = scaled_rsqrt2(fma2(p, p, q * q), -hvdt);
+                const f2 np = fma2(w, fma2(Sxs[s], p, cross * q), p);
+                const f2 nq = fma2(w, fma2(cross, p, Sy[t] * q), q);
+                p = np;
+                q = nq;
+            }
+            const f2 s2 = fma2(p, p, q * q);
+            const f2 g = mkf2(tguard(s2.x) ? s2.x * rsqrtf(s2.x) : 0.0f, tguard(s2.y) ? s2.y * rsqrtf(s2.y) : 0.0f);
+            accs = fma2(ny[t], fma2(-vdt, g, val), accs);
+        }
+        acc = fma2(nx[s], accs, acc);
+    }
+    return acc;
+}
+
 }  // namespace fdm

@@ -564,6 +564,19 @@ __global__ void celerity_dt_kernel(const T* __restrict__ tau, const T* phi0, con
 // ------------------------------------------------------------------ KNP stencil
 constexpr int TX = 32;  // stencil block width (threads along x1)
 
+// one element global -> shared without passing through registers (sizeof(T) = 4 or 8)
+template <typename T> __device__ __forceinline__ void copy_async(T* smem_dst, const T* gmem_src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(sizeof(T)) : "memory");
+}
+// waits for all of this thread's asynchronous copies (the block barrier that follows makes
+// every thread's copies visible to all)
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T>
 struct KnpArgs {
     VelLaw<T> vel;
@@ -581,9 +594,9 @@ struct KnpArgs {
 // with a register budget that keeps minb blocks resident per SM.  Shape 0 is the default;
 // the autotuner times all of them.  Every shape computes the same node values.
 template <typename T> struct KnpShapes;
-template <> struct KnpShapes<float> {
+template <> struct KnpShapes<float> {   // nodes are updated two at a time (packed FP32)
     static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {4, 2, 2, 4},
-                         minb[kKnpShapes] = {4, 4, 2, 3};
+                         minb[kKnpShapes] = {2, 3, 1, 3};
 };
 template <> struct KnpShapes<double> {
     static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 4},
@@ -660,14 +673,17 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (k < npt) tv[k] = tau[(size_t)(by + threadIdx.y + k * TY) * n1 + x];
+    // the tile and its halo go straight from global to shared memory with asynchronous
+    // copies, all of a thread's in flight at once (no register staging, no wait per element)
     for (int ly = threadIdx.y; ly < rows + 4; ly += TY) {
         const int gy = (by + ly - 2) & (n2 - 1);
         for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
             const int gx = (bx + lx - 2) & (n1 - 1);
-            tile[ly][lx] = phi[(size_t)gy * n1 + gx];
-            if constexpr (kPair) tile_lo[ly][lx] = lo_in[(size_t)gy * n1 + gx];
+            copy_async<T>(&tile[ly][lx], phi + (size_t)gy * n1 + gx);
+            if constexpr (kPair) copy_async<T>(&tile_lo[ly][lx], lo_in + (size_t)gy * n1 + gx);
         }
     }
+    copy_async_wait_all();
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (k < npt) s_tau[threadIdx.y + k * TY][threadIdx.x] = tv[k];
@@ -675,25 +691,46 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     const T dt = s_dt;
     const int lx = threadIdx.x + 2;
     const double phi_ref = a.vel.friction ? sc->phi_ref : 0.0;
+    if constexpr (kPair) {
+        // two nodes per pass, (x, y) and (x, y + TY), one in each lane of the packed FP32
+        // arithmetic; an odd last node is paired with itself and written once
 #pragma unroll 1
-    for (int k = 0; k < npt; ++k) {
-        const int y = by + threadIdx.y + k * TY;
-        const int ly = threadIdx.y + k * TY + 2;
-        const T tau_k = s_tau[threadIdx.y + k * TY][threadIdx.x];
-        if constexpr (kPair) {
-            const T h0 = tile[ly][lx], l0 = tile_lo[ly][lx];
-            T v0 = celerity(a.vel, tau_k, h0 + l0, phi_ref);
-            if (a.vel.mfac) v0 = v0 * a.vel.mfac[inst * nn + (size_t)y * n1 + x];
-            // differences to the node value, exact in the high words for nearby values;
-            // the offset-equivariant update then returns the increment of U13
-            auto g = [&](int i, int j) -> T { return (tile[ly + j][lx + i] - h0) + (tile_lo[ly + j][lx + i] - l0); };
-            const T inc = knp_node<T>(g, v0, dt, a.theta, a.theta_code, a.time_level);
+        for (int k = 0; k < npt; k += 2) {
+            const int k2 = (k + 1 < npt) ? k + 1 : k;
+            const int ya = by + threadIdx.y + k * TY, yb = by + threadIdx.y + k2 * TY;
+            const int la = threadIdx.y + k * TY + 2, lb = threadIdx.y + k2 * TY + 2;
+            const float ha = tile[la][lx], lo_a = tile_lo[la][lx], hb = tile[lb][lx], lo_b = tile_lo[lb][lx];
+            f2 v0 = mkf2(celerity(a.vel, s_tau[la - 2][threadIdx.x], ha + lo_a, phi_ref),
+                         celerity(a.vel, s_tau[lb - 2][threadIdx.x], hb + lo_b, phi_ref));
+            if (a.vel.mfac)
+                v0 = mkf2(v0.x * a.vel.mfac[inst * nn + (size_t)ya * n1 + x],
+                          v0.y * a.vel.mfac[inst * nn + (size_t)yb * n1 + x]);
+            // differences to each node's value, exact in the high words for nearby values;
+            // the offset-equivariant update then returns the increments of U13
+            const f2 h0 = mkf2(ha, hb), l0 = mkf2(lo_a, lo_b);
+            auto g = [&](int i, int j) -> f2 {
+                return (mkf2(tile[la + j][lx + i], tile[lb + j][lx + i]) - h0) +
+                       (mkf2(tile_lo[la + j][lx + i], tile_lo[lb + j][lx + i]) - l0);
+            };
+            const f2 inc = knp_node_x2(g, v0, dt, a.theta, a.time_level);
             float s1, e1, hi, lo;
-            two_sum(h0, inc, s1, e1);
-            two_sum(s1, DF_ADD(l0, e1), hi, lo);
-            out[(size_t)y * n1 + x] = hi;
-            lo_out[(size_t)y * n1 + x] = lo;
-        } else {
+            two_sum(ha, inc.x, s1, e1);
+            two_sum(s1, DF_ADD(lo_a, e1), hi, lo);
+            out[(size_t)ya * n1 + x] = hi;
+            lo_out[(size_t)ya * n1 + x] = lo;
+            if (k2 != k) {
+                two_sum(hb, inc.y, s1, e1);
+                two_sum(s1, DF_ADD(lo_b, e1), hi, lo);
+                out[(size_t)yb * n1 + x] = hi;
+                lo_out[(size_t)yb * n1 + x] = lo;
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int k = 0; k < npt; ++k) {
+            const int y = by + threadIdx.y + k * TY;
+            const int ly = threadIdx.y + k * TY + 2;
+            const T tau_k = s_tau[threadIdx.y + k * TY][threadIdx.x];
             const T up = tile[ly][lx];
             T v0 = celerity(a.vel, tau_k, up, phi_ref);
             if (a.vel.mfac) v0 = v0 * a.vel.mfac[inst * nn + (size_t)y * n1 + x];
