@@ -308,8 +308,8 @@ fdm_status fdm_measure_arith_rate(int32_t precision, void *stream, double *gflop
  * fully handed out to other buffers, or an embedding that forbids allocations outside its
  * own pool).  Computes tau13 = IFFT(K FFT(U13)) + sigma_bar13 exactly like fdm_static_solve
  * with FDM_LOAD_STRESS, in FP64, for caller-owned DEVICE arrays d_up13 (input) and
- * d_tau13 (output), both [n2][n1] float64; the two ranges may not overlap
- * (FDM_ERR_INVALID_ARG).  Only the grid, nz, nh, dx, E and nu fields of p are used;
+ * d_tau13 (output), both [n2][n1] float64 and 16-byte aligned; the two ranges may not
+ * overlap (FDM_ERR_INVALID_ARG otherwise).  Only the grid, nz, nh, dx, E and nu fields of p are used;
  * p->precision must be FDM_FP64.
  * Limits: n1, n2 <= 256 and nz <= 4096; larger grids return FDM_ERR_TOO_LARGE.
  * All intermediates live in one fixed device array of 692,992 bytes that every GPU which

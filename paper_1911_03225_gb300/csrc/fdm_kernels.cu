@@ -87,6 +87,19 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     s = t;
 }
 
+// one element global -> shared without passing through registers (4, 8 or 16 bytes)
+template <typename T> __device__ __forceinline__ void copy_async(T* smem_dst, const T* gmem_src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "4-, 8- or 16-byte elements");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(sizeof(T)) : "memory");
+}
+// waits for all of this thread's asynchronous copies (the block barrier that follows makes
+// every thread's copies visible to all)
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Thread and residency bounds of the FFT kernels.  The FP32 kernels are latency bound: a
 // block of at most 512 threads with three resident per SM caps them at 40 registers, which
 // keeps 48 warps per SM instead of 32 (no spills).
@@ -103,7 +116,7 @@ template <typename T>
 __device__ __forceinline__ const cpx<T>* stage_twiddles(const cpx<T>* pt, cpx<T>* slot, int L) {
     if constexpr (std::is_same<T, float>::value) {
         const int len = pass_table_len(L);
-        for (int i = threadIdx.x; i < len; i += blockDim.x) slot[i] = pt[i];
+        for (int i = threadIdx.x; i < len; i += blockDim.x) copy_async(slot + i, pt + i);
         return slot;
     } else {
         return pt;
@@ -137,19 +150,9 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
     const int total = R * L, step = blockDim.x;
-    for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
-        cpx<T> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int e = e0 + u * step;
-            if (e < total) v[u] = src2[e];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            int e = e0 + u * step;
-            if (e < total) A[(e >> lL) * ld + swz(e & (L - 1))] = v[u];
-        }
-    }
+    // every element (and the staged twiddles) by asynchronous copies, all in flight at once
+    for (int e = threadIdx.x; e < total; e += step) copy_async(A + (e >> lL) * ld + swz(e & (L - 1)), src2 + e);
+    copy_async_wait_all();
     __syncthreads();
     if (row_partials) {
         // one warp per row: lane l sums the pairs l, l + 32, ... (compensated, in the field's
@@ -272,17 +275,8 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     const cpx<T>* src = in + (size_t)kx0 * n2;
     {
         const int total = C * n2, step = blockDim.x;
-        for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
-            cpx<T> v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e0 + u * step < total) v[u] = src[e0 + u * step];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * step;
-                if (e < total) A[(e >> ln2) * ld + swz(e & (n2 - 1))] = v[u];
-            }
-        }
+        for (int e = threadIdx.x; e < total; e += step) copy_async(A + (e >> ln2) * ld + swz(e & (n2 - 1)), src + e);
+        copy_async_wait_all();
     }
     if (a.mode == COL_K && kx0 == 0) {
         // <U13> from the row sums, then the loading state of this step (Sec. 5.1).  The
@@ -432,19 +426,9 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     {
         const int total = R * L, step = blockDim.x;
-        for (int e0 = threadIdx.x; e0 < total; e0 += 4 * step) {
-            cpx<T> v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int e = e0 + u * step;
-                if (e < total) v[u] = spec[(size_t)(e >> lR) * n2 + y0 + (e & (R - 1))];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int e = e0 + u * step;
-                if (e < total) A[(e & (R - 1)) * ld + swz(e >> lR)] = v[u];
-            }
-        }
+        for (int e = threadIdx.x; e < total; e += step)
+            copy_async(A + (e & (R - 1)) * ld + swz(e >> lR), spec + (size_t)(e >> lR) * n2 + y0 + (e & (R - 1)));
+        copy_async_wait_all();
     }
     __syncthreads();
     const int half = L / 2 + 1;
@@ -564,19 +548,6 @@ __global__ void celerity_dt_kernel(const T* __restrict__ tau, const T* phi0, con
 // ------------------------------------------------------------------ KNP stencil
 constexpr int TX = 32;  // stencil block width (threads along x1)
 
-// one element global -> shared without passing through registers (sizeof(T) = 4 or 8)
-template <typename T> __device__ __forceinline__ void copy_async(T* smem_dst, const T* gmem_src) {
-    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(sizeof(T)) : "memory");
-}
-// waits for all of this thread's asynchronous copies (the block barrier that follows makes
-// every thread's copies visible to all)
-__device__ __forceinline__ void copy_async_wait_all() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 template <typename T>
 struct KnpArgs {
     VelLaw<T> vel;
@@ -588,7 +559,6 @@ struct KnpArgs {
     fdm_dev_scalars* sc;     // scalars of instance 0
     int gated;
 };
-
 
 // Stencil block shapes: block (TX, ty) threads, each updating npt nodes stacked along x2,
 // with a register budget that keeps minb blocks resident per SM.  Shape 0 is the default;

@@ -74,6 +74,7 @@ using namespace fdm;
 extern "C" fdm_status fdm_static_solve_noalloc(const fdm_params* p, double sigma_bar13, const double* d_up13,
                                                double* d_tau13, void* stream) {
     if (!p || !d_up13 || !d_tau13) return FDM_ERR_INVALID_ARG;
+    if (((uintptr_t)d_up13 | (uintptr_t)d_tau13) & 15u) return FDM_ERR_INVALID_ARG;   // 16-byte aligned
     if (p->precision != FDM_FP64 || !std::isfinite(sigma_bar13)) return FDM_ERR_INVALID_ARG;
     const int nz = p->nz == 0 ? p->n1 : p->nz;
     if (!pow2_between(p->n1, 16, 1 << 30) || !pow2_between(p->n2, 16, 1 << 30)) return FDM_ERR_INVALID_ARG;
