@@ -47,6 +47,9 @@ def lib():
         _lib.oracle_run.restype = C.c_int
         _lib.oracle_run_hetero.argtypes = [C.c_void_p, d, d, C.c_void_p, C.c_int, d, d, d, d, C.c_double, C.c_int]
         _lib.oracle_run_hetero.restype = C.c_int
+        _lib.oracle_hetero_layer.argtypes = [C.c_int] * 4 + [C.c_double, C.c_double, d, d, C.c_int, C.c_double,
+                                                              C.c_double, C.c_int, d, d, d]
+        _lib.oracle_hetero_layer.restype = C.c_int
         _lib.oracle_set_threads.argtypes = [C.c_int]
         _lib.oracle_set_threads.restype = C.c_int
         _lib.oracle_threads.restype = C.c_int
@@ -266,6 +269,22 @@ def hetero_antiplane(mu, up13, stress_control, load, tol=0.0, max_iter=50):
     it = lib().oracle_hetero_antiplane(n1, n2, _p(m), _p(u), int(bool(stress_control)), float(load), float(tol),
                                        int(max_iter), _p(s13), _p(s23), C.byref(r))
     return s13, s23, it, r.value
+
+
+def hetero_layer(factor, up13, nz, nh, mu, nu, stress_control, load, tol=0.0, max_iter=50, planes=False):
+    """Static problem of a plastic layer of nh planes in a cell of nz with a modulus field
+    f(x1, x2) uniform through the depth (Sec. 3.1.2 heterogeneous medium, layer of Sec. 3.2.1):
+    returns (tau13 = layer average of sigma13, sigma13 of every plane or None, iterations,
+    residual).  ``load``: sigma_bar13 under stress control, else eps_bar13."""
+    fa, u = _f64(factor), _f64(up13)
+    n2, n1 = u.shape
+    tau = np.zeros((n2, n1))
+    s13 = np.zeros((int(nz), n2, n1)) if planes else None
+    r = C.c_double(0.0)
+    it = lib().oracle_hetero_layer(n1, n2, int(nz), int(nh), float(mu), float(nu), _p(fa), _p(u),
+                                   int(bool(stress_control)), float(load), float(tol), int(max_iter), _p(tau),
+                                   None if s13 is None else _p(s13), C.byref(r))
+    return tau, s13, it, r.value
 
 
 def run(params: Params, up13, nsteps, K=None, state: State = None, mobility_factor=None, shear_modulus=None,

@@ -880,5 +880,185 @@ int oracle_hetero_antiplane(int n1, int n2, const double *mu, const double *up13
     return it;
 }
 
+/*
+ * Heterogeneous elasticity with a plastic layer thinner than the cell (Sec. 3.1.2,
+ * heterogeneous medium; the layer of Sec. 3.2.1).  Periodic cell of n1 x n2 x nz cubic
+ * voxels; the eigen-distortion U^p = U13(x1, x2) chi(x3) e1 (x) e3, chi = 1 on the planes
+ * x3 = 0 .. nh-1, i.e. the eigenstrain eps^p_13 = eps^p_31 = U13 chi / 2.  The medium is
+ * isotropic, C(x) = f(x1, x2) C_iso(lambda, mu) with lambda = 2 mu nu / (1 - 2 nu): the
+ * modulus field varies in the plane and is uniform through the cell's depth (reading H5).
+ * Reference medium C0 = f0 C_iso, f0 = (min f + max f) / 2.  Unknown: the strain eps (3x3,
+ * symmetric).  The paper's series expansion is summed by the fixed-point iteration, from
+ * eps = 0,
+ *   tau = (C - C0) : eps - C : eps^p,
+ *   eps-hat(xi) = -Gamma0-hat(xi) : tau-hat(xi) (xi != 0),   eps-hat(0) = E,
+ *   Gamma0-hat_ijkl = (delta_ik xi_j xi_l + delta_il xi_j xi_k + delta_jk xi_i xi_l
+ *                      + delta_jl xi_i xi_k) / (4 mu0 |xi|^2)
+ *                     - (lambda0 + mu0) / (mu0 (lambda0 + 2 mu0)) xi_i xi_j xi_k xi_l / |xi|^4,
+ * with every product of frequency components that contains an axis's Nyquist frequency an
+ * odd number of times set to zero (reading G8: a real field cannot carry it).  Loading:
+ * strain control E = eps_bar13 (e1 (x) e3 + e3 (x) e1); stress control <sigma> = sigma_bar13
+ * (e1 (x) e3 + e3 (x) e1), i.e. E = C0^-1 : (Sigma - <tau>) from each iterate's tau.
+ * Stops when rms(eps_new - eps) <= tol max(rms(eps_new), rms(eps^p - <eps^p>)) (rms over the
+ * cell of the tensor's Frobenius norm) or after max_iter iterations (tol = 0: exactly
+ * max_iter).  Outputs the layer average of sigma13 = 2 f mu (eps13 - eps^p13) over the nh
+ * planes, tau13[n2][n1], and (may be NULL) sigma13 of every plane, s13_planes[nz][n2][n1].
+ * Returns the iterations done; *res (may be NULL) the last ratio.
+ */
+static double gamma_term(const int *idx, int nidx, const double xi[3], const int nyq[3])
+{
+    /* product of xi over the listed axes; zero when an axis at its Nyquist frequency occurs
+       an odd number of times */
+    int count[3] = {0, 0, 0};
+    double p = 1.0;
+    for (int t = 0; t < nidx; t++) { count[idx[t]]++; p *= xi[idx[t]]; }
+    for (int a = 0; a < 3; a++) if (nyq[a] && (count[a] & 1)) return 0.0;
+    return p;
+}
+
+int oracle_hetero_layer(int n1, int n2, int nz, int nh, double mu, double nu, const double *f, const double *up13,
+                        int stress_control, double load, double tol, int max_iter, double *tau13, double *s13_planes,
+                        double *res)
+{
+    const size_t n2d = (size_t)n1 * n2, n = n2d * nz;
+    const double lam = 2.0 * mu * nu / (1.0 - 2.0 * nu);
+    double flo = f[0], fhi = f[0];
+    for (size_t i = 1; i < n2d; i++) { if (f[i] < flo) flo = f[i]; if (f[i] > fhi) fhi = f[i]; }
+    const double f0 = 0.5 * (flo + fhi), mu0 = f0 * mu, lam0 = f0 * lam;
+    const double cc = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+    /* strain components e[c] for c = (i, j) with i <= j: 00 11 22 12 02 01 */
+    static const int ci[6] = {0, 1, 2, 1, 0, 0}, cj[6] = {0, 1, 2, 2, 2, 1};
+    double *eps = calloc(6 * n, sizeof(double));
+    double *re = malloc(sizeof(double) * 6 * n), *im = malloc(sizeof(double) * 6 * n);
+    double *zr = malloc(sizeof(double) * nz), *zi = malloc(sizeof(double) * nz);
+    /* eigenstrain 13 component and its rms about the mean */
+    double pmean = 0.0;
+    for (int z = 0; z < nh; z++) for (size_t q = 0; q < n2d; q++) pmean += 0.5 * up13[q];
+    pmean /= (double)n;
+    double prms = 0.0;
+    for (int z = 0; z < nz; z++)
+        for (size_t q = 0; q < n2d; q++) {
+            double e = (z < nh ? 0.5 * up13[q] : 0.0) - pmean;
+            prms += 2.0 * e * e;   /* eps^p_13 and eps^p_31 */
+        }
+    prms = sqrt(prms / (double)n);
+    int it = 0;
+    double r = 0.0;
+    while (it < max_iter) {
+        it++;
+        /* polarisation tau = (C - C0) : eps - C : eps^p (isotropic: lambda tr + 2 mu) */
+        double tmean[6] = {0, 0, 0, 0, 0, 0};
+        for (int z = 0; z < nz; z++)
+            for (size_t q = 0; q < n2d; q++) {
+                size_t x = (size_t)z * n2d + q;
+                double dl = (f[q] - f0) * lam, dm = (f[q] - f0) * mu;
+                double tr = eps[0 * n + x] + eps[1 * n + x] + eps[2 * n + x];
+                for (int c = 0; c < 6; c++) {
+                    double t = 2.0 * dm * eps[c * n + x] + (c < 3 ? dl * tr : 0.0);
+                    if (c == 4 && z < nh) t -= 2.0 * f[q] * mu * 0.5 * up13[q];   /* - C : eps^p */
+                    re[c * n + x] = t;
+                    im[c * n + x] = 0.0;
+                    tmean[c] += t;
+                }
+            }
+        for (int c = 0; c < 6; c++) tmean[c] /= (double)n;
+        /* macroscopic strain of this iterate */
+        double E[6] = {0, 0, 0, 0, 0, 0};
+        if (stress_control) {
+            /* E = C0^-1 : (Sigma - <tau>), isotropic compliance: e = (s - nu0/(1+nu0) tr s I)/(2 mu0) */
+            double S[6];
+            for (int c = 0; c < 6; c++) S[c] = (c == 4 ? load : 0.0) - tmean[c];
+            double nu0 = lam0 / (2.0 * (lam0 + mu0));
+            double trs = S[0] + S[1] + S[2];
+            for (int c = 0; c < 6; c++) E[c] = (S[c] - (c < 3 ? nu0 / (1.0 + nu0) * trs : 0.0)) / (2.0 * mu0);
+        } else {
+            E[4] = load;
+        }
+        /* 3-D transform of each component: planes, then along x3 */
+        for (int c = 0; c < 6; c++) {
+            for (int z = 0; z < nz; z++) oracle_fft2d(n1, n2, re + c * n + (size_t)z * n2d, im + c * n + (size_t)z * n2d, -1);
+            for (size_t q = 0; q < n2d; q++) {
+                for (int z = 0; z < nz; z++) { zr[z] = re[c * n + (size_t)z * n2d + q]; zi[z] = im[c * n + (size_t)z * n2d + q]; }
+                oracle_fft1d(nz, zr, zi, -1);
+                for (int z = 0; z < nz; z++) { re[c * n + (size_t)z * n2d + q] = zr[z]; im[c * n + (size_t)z * n2d + q] = zi[z]; }
+            }
+        }
+        /* Green operator */
+        for (int k3 = 0; k3 < nz; k3++)
+            for (int k2 = 0; k2 < n2; k2++)
+                for (int k1 = 0; k1 < n1; k1++) {
+                    size_t x = (size_t)k3 * n2d + (size_t)k2 * n1 + k1;
+                    if (k1 == 0 && k2 == 0 && k3 == 0) {
+                        for (int c = 0; c < 6; c++) { re[c * n + x] = E[c] * (double)n; im[c * n + x] = 0.0; }
+                        continue;
+                    }
+                    double xi[3] = {2.0 * OR_PI * signed_index(k1, n1) / n1, 2.0 * OR_PI * signed_index(k2, n2) / n2,
+                                    2.0 * OR_PI * signed_index(k3, nz) / nz};
+                    int nyq[3] = {2 * k1 == n1, 2 * k2 == n2, 2 * k3 == nz};
+                    double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+                    double tr_[3][3], ti_[3][3];
+                    for (int c = 0; c < 6; c++) {
+                        tr_[ci[c]][cj[c]] = tr_[cj[c]][ci[c]] = re[c * n + x];
+                        ti_[ci[c]][cj[c]] = ti_[cj[c]][ci[c]] = im[c * n + x];
+                    }
+                    for (int c = 0; c < 6; c++) {
+                        int i = ci[c], j = cj[c];
+                        double sr = 0.0, si = 0.0;
+                        for (int k = 0; k < 3; k++)
+                            for (int l = 0; l < 3; l++) {
+                                double g = 0.0;
+                                int a2[2];
+                                if (i == k) { a2[0] = j; a2[1] = l; g += gamma_term(a2, 2, xi, nyq); }
+                                if (i == l) { a2[0] = j; a2[1] = k; g += gamma_term(a2, 2, xi, nyq); }
+                                if (j == k) { a2[0] = i; a2[1] = l; g += gamma_term(a2, 2, xi, nyq); }
+                                if (j == l) { a2[0] = i; a2[1] = k; g += gamma_term(a2, 2, xi, nyq); }
+                                g /= 4.0 * mu0 * q2;
+                                int a4[4] = {i, j, k, l};
+                                g -= cc * gamma_term(a4, 4, xi, nyq) / (q2 * q2);
+                                sr += g * tr_[k][l];
+                                si += g * ti_[k][l];
+                            }
+                        re[c * n + x] = -sr;
+                        im[c * n + x] = -si;
+                    }
+                }
+        /* back to real space */
+        for (int c = 0; c < 6; c++) {
+            for (size_t q = 0; q < n2d; q++) {
+                for (int z = 0; z < nz; z++) { zr[z] = re[c * n + (size_t)z * n2d + q]; zi[z] = im[c * n + (size_t)z * n2d + q]; }
+                oracle_fft1d(nz, zr, zi, +1);
+                for (int z = 0; z < nz; z++) { re[c * n + (size_t)z * n2d + q] = zr[z]; im[c * n + (size_t)z * n2d + q] = zi[z]; }
+            }
+            for (int z = 0; z < nz; z++) oracle_fft2d(n1, n2, re + c * n + (size_t)z * n2d, im + c * n + (size_t)z * n2d, +1);
+        }
+        double dd = 0.0, ee = 0.0;
+        for (int c = 0; c < 6; c++) {
+            double w = (c < 3) ? 1.0 : 2.0;   /* off-diagonal components count twice */
+            for (size_t x = 0; x < n; x++) {
+                double v = re[c * n + x] / (double)n;
+                double d = v - eps[c * n + x];
+                dd += w * d * d;
+                ee += w * v * v;
+                eps[c * n + x] = v;
+            }
+        }
+        double scale = fmax(sqrt(ee / (double)n), prms);
+        r = scale > 0.0 ? sqrt(dd / (double)n) / scale : 0.0;
+        if (tol > 0.0 && r <= tol) break;
+    }
+    for (size_t q = 0; q < n2d; q++) {
+        double acc = 0.0;
+        for (int z = 0; z < nz; z++) {
+            double s = 2.0 * f[q] * mu * (eps[4 * n + (size_t)z * n2d + q] - (z < nh ? 0.5 * up13[q] : 0.0));
+            if (s13_planes) s13_planes[(size_t)z * n2d + q] = s;
+            if (z < nh) acc += s;
+        }
+        if (tau13) tau13[q] = acc / (double)nh;
+    }
+    if (res) *res = r;
+    free(eps); free(re); free(im); free(zr); free(zi);
+    return it;
+}
+
 /* size check used by the wrapper */
 int oracle_valid_size(int n) { return is_pow2(n) && n >= 4; }

@@ -991,3 +991,67 @@ def test_thread_count_does_not_change_results():
     for other in runs[1:]:
         for a, b in zip(runs[0], other):
             np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------------------------ heterogeneous layer thinner than the cell
+def _layer_case(seed=3):
+    n1, n2 = 32, 16
+    u = inputs.random_up(32, seed=seed, ell=4.0)[:n2, :n1].copy()
+    f = inputs.modulus_factor(n1, n2, seed=1, lo=0.25, hi=1.0, ell=6.0)
+    return u, f
+
+
+@pytest.mark.parametrize("stress_control,load", [(1, 0.013), (0, 0.002)])
+def test_hetero_layer_homogeneous_limit_is_the_layer_solve(stress_control, load):
+    """Uniform modulus: the polarisation is -C0 : eps^p whatever the strain, so one iteration
+    gives the exact solution, whose layer average is the layer solve's tau13 (Sec. 3.2.1 K
+    table) and whose planes are the 3-D cell's sigma13 (both pinned above)."""
+    u, _ = _layer_case()
+    n2, n1 = u.shape
+    nz, nh, mu, nu = 16, 3, 1 / 2.6, 0.3
+    tau, planes, it, _ = oracle.hetero_layer(np.ones((n2, n1)), u, nz, nh, mu, nu, stress_control, load,
+                                             tol=0.0, max_iter=2, planes=True)
+    sig = load if stress_control else 2 * mu * load - mu * (nh / nz) * u.mean()
+    ref = oracle.static_tau(u, oracle.kernel_table(n1, n2, nz, nh, mu, nu), sig)
+    assert it == 2 and np.linalg.norm(tau - ref) / np.linalg.norm(ref) < 1e-13
+    ps = oracle.stress13_planes(u, nz, nh, mu, nu, sig, list(range(nz)))
+    assert np.linalg.norm(planes - ps) / np.linalg.norm(ps) < 1e-13
+
+
+@pytest.mark.parametrize("stress_control,load", [(1, 0.013), (0, 0.002)])
+def test_hetero_layer_filling_the_cell_is_the_antiplane_problem(stress_control, load):
+    """Layer filling the cell (nh = nz): U^p is uniform along x3, only the x3-independent part
+    of the strain is forced, and the iteration is the antiplane one iterate for iterate (same
+    reference medium, same loading): sigma13 on every plane equals the antiplane solution."""
+    u, f = _layer_case()
+    mu, nu = 1 / 2.6, 0.3
+    tau, planes, it, r = oracle.hetero_layer(f, u, 8, 8, mu, nu, stress_control, load, tol=0.0, max_iter=15,
+                                             planes=True)
+    s13, _, it2, r2 = oracle.hetero_antiplane(mu * f, u, stress_control, load, tol=0.0, max_iter=15)
+    assert it == it2 == 15 and r == pytest.approx(r2, rel=1e-9)
+    assert np.linalg.norm(tau - s13) / np.linalg.norm(s13) < 1e-13
+    assert np.abs(planes - s13[None]).max() < 1e-13 * np.abs(s13).max()
+
+
+def test_hetero_layer_thin_layer_converges_with_reflection_symmetry():
+    """A layer of 3 planes in a cell of 16 with a contrast-4 modulus field: the iteration
+    contracts at no more than (kappa - 1) / (kappa + 1) per step and converges; the converged
+    sigma13 is even about the layer's mid-plane (the medium is uniform through the depth and
+    the eigen-distortion symmetric about that plane), and its layer average differs from the
+    homogeneous layer solve (the heterogeneity matters)."""
+    u, f = _layer_case()
+    mu, nu, nz, nh = 1 / 2.6, 0.3, 16, 3
+    kappa = f.max() / f.min()
+    rs = []
+    for k in (30, 31):
+        rs.append(oracle.hetero_layer(f, u, nz, nh, mu, nu, 1, 0.013, tol=0.0, max_iter=k)[3])
+    assert rs[1] / rs[0] <= (kappa - 1) / (kappa + 1) + 1e-3
+    tau, planes, it, r = oracle.hetero_layer(f, u, nz, nh, mu, nu, 1, 0.013, tol=1e-12, max_iter=400, planes=True)
+    assert it < 400 and r <= 1e-12
+    scale = np.abs(planes).max()
+    for z in range(nz):
+        zr = (nh - 1 - z) % nz
+        assert np.abs(planes[z] - planes[zr]).max() < 1e-10 * scale
+    assert np.isfinite(tau).all()
+    ref = oracle.static_tau(u, oracle.kernel_table(32, 16, nz, nh, mu, nu), 0.013)
+    assert np.linalg.norm(tau - ref) / np.linalg.norm(ref) > 1e-2
