@@ -532,6 +532,19 @@ def batched_record(world, rank, local, count, K, W):
         launches = b.launches_per_step() * K
         sample = list(range(0, len(inst), max(1, len(inst) // 8)))[:8]
         mixed_out = {i: b.read_fields(i, "up13")["up13"] for i in sample}
+        # trial: the same steps as one persistent cooperative launch (all phases of all size
+        # classes, grid barriers between phases) against the graph-replayed launches above
+        for i in range(len(inst)):
+            b.set_budget(i, W + K)
+        b.enqueue_steps_persistent(W)
+        b.sync()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        b.enqueue_steps_persistent(K)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        assert (b.sync() == 0).all()
+        ms_persist = max_over_ranks(p0.elapsed_time(p1), world)
     # the plain per-instance FP64 form on the same GPU: one handle per instance, stepped alone
     fp64_cells, fp64_ms, errs = 0, 0.0, []
     for i in sample:
@@ -557,6 +570,10 @@ def batched_record(world, rank, local, count, K, W):
             "l2": "working set %.0f MB > L2" % (cells * 4 * 5 / 1e6),
             "gpu_launches": launches, "clocks": clk.summary(),
             "plain_fp64_per_instance": {"value": plain, "unit": UNIT, "sample_instances": len(sample)},
+            "persistent_trial": {"ms_per_step": ms_persist / K, "value": cells * K * world / (ms_persist / 1e3),
+                                 "over_graph": ms / ms_persist, "launches": 1,
+                                 "form": "one cooperative launch for all K steps: the four phases of every size "
+                                         "class, grid barriers between phases (fdm_batch_enqueue_steps_persistent)"},
             "batched_mixed_over_plain_fp64": value / world / plain,
             "mixed_vs_fp64_rel_l2": {"max": max(errs), "mean": sum(errs) / len(errs), "after_steps": W + K,
                                      "stated_tolerance": 1e-5}}
@@ -574,6 +591,7 @@ def run_batched(args, world, rank, local):
             "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
             "plain_fp64_per_instance": rec["plain_fp64_per_instance"],
             "mixed_vs_fp64_rel_l2": rec["mixed_vs_fp64_rel_l2"],
+            "persistent_trial": rec["persistent_trial"],
         }), flush=True)
 
 

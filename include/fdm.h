@@ -372,6 +372,24 @@ fdm_status fdm_batch_get_info(fdm_batch *b, int32_t i, fdm_step_info *info);
 /* Copies U13 and/or tau13 of instance i (mask of FDM_FIELD_UP13 | FDM_FIELD_TAU13). */
 fdm_status fdm_batch_read_fields(fdm_batch *b, int32_t i, uint32_t mask, double *up13, double *tau13);
 
+/* Enqueues nsteps batched steps (as fdm_batch_enqueue_steps) as ONE persistent launch: a
+ * cooperative grid of resident blocks runs, step after step, the four phases of the step
+ * (row transforms, column pass with the Green kernel, inverse rows with max |v0| and dt,
+ * transport; Sec. 3.1.1) for every group, the blocks taking the phase's tiles of every
+ * instance in turn, with a grid-wide barrier between phases.  Results equal those of
+ * fdm_batch_enqueue_steps bit for bit.  Every barrier wait is bounded (1 s by default): a
+ * block that gives up records FDM_ERR_TIMEOUT, all blocks leave, the next fdm_batch_sync*
+ * returns FDM_ERR_TIMEOUT, and the batch's states are then undefined until set again.
+ * Requires every instance to be FDM_MIXED with n1 >= 32 (FDM_ERR_INVALID_ARG otherwise);
+ * the first call allocates the launch's descriptors.  Returns without waiting. */
+fdm_status fdm_batch_enqueue_steps_persistent(fdm_batch *b, int32_t nsteps);
+
+/* Test hook of the persistent step's barrier: from the next launch on, each barrier waits for
+ * extra_arrivals more blocks than the grid holds (so with extra_arrivals > 0 no wait ever
+ * completes) and a wait gives up after limit_seconds (<= 0: the default 1 s).  Process-wide;
+ * fdm_debug_barrier(0, 0) restores the defaults. */
+void fdm_debug_barrier(int32_t extra_arrivals, double limit_seconds);
+
 /* Kernel launches one batched step issues (kernels per step x groups). */
 int32_t fdm_batch_launches_per_step(const fdm_batch *b);
 

@@ -49,7 +49,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
            "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field",
-           "fdm_measure_arith_rate"]
+           "fdm_measure_arith_rate", "fdm_batch_enqueue_steps_persistent", "fdm_debug_barrier"]
 
 
 class CParams(C.Structure):
@@ -170,6 +170,10 @@ def load():
     lib.fdm_sync.argtypes = [H]
     lib.fdm_static_solve_noalloc.argtypes = [C.POINTER(CParams), C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fdm_static_solve_noalloc.restype = C.c_int
+    lib.fdm_batch_enqueue_steps_persistent.argtypes = [C.c_void_p, C.c_int32]
+    lib.fdm_batch_enqueue_steps_persistent.restype = C.c_int
+    lib.fdm_debug_barrier.argtypes = [C.c_int32, C.c_double]
+    lib.fdm_debug_barrier.restype = None
     lib.fdm_measure_arith_rate.argtypes = [C.c_int32, C.c_void_p, d]
     lib.fdm_measure_arith_rate.restype = C.c_int
     PP = C.POINTER(CParams)
@@ -227,6 +231,12 @@ def load():
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+def debug_barrier(extra_arrivals: int, limit_seconds: float = 0.0):
+    """Test hook: barriers of the persistent batched step wait for extra_arrivals more blocks
+    than the grid holds (> 0: none completes) and give up after limit_seconds (<= 0: 1 s)."""
+    load().fdm_debug_barrier(int(extra_arrivals), float(limit_seconds))
 
 
 def debug_fail_allocation(n: int):
@@ -529,6 +539,11 @@ class Batch:
 
     def enqueue_steps(self, nsteps: int):
         _check(self.lib.fdm_batch_enqueue_steps(self.h, int(nsteps)), "fdm_batch_enqueue_steps")
+
+    def enqueue_steps_persistent(self, nsteps: int):
+        """The same steps as ``enqueue_steps`` in one persistent launch (mixed precision)."""
+        _check(self.lib.fdm_batch_enqueue_steps_persistent(self.h, int(nsteps)),
+               "fdm_batch_enqueue_steps_persistent")
 
     def sync(self) -> np.ndarray:
         """Wait; return every instance's remaining step budget (raises on device errors)."""

@@ -24,7 +24,19 @@ struct fdm_batch {
     cudaStream_t stream = nullptr;
     int count = 0;
     std::vector<bool> has_state;
+    // persistent step (fdm_batch_enqueue_steps_persistent): group descriptors and the barrier
+    void* persist_desc = nullptr;
+    PersistBarrier* persist_bar = nullptr;
+    size_t persist_smem = 0;
+    bool persist_used = false;
 };
+
+namespace fdm {
+// test hook of the persistent step's barrier (fdm_debug_barrier): arrivals expected beyond
+// the grid, and the wait limit in seconds
+int g_barrier_extra = 0;
+double g_barrier_limit_s = 1.0;
+}
 
 namespace {
 
@@ -156,9 +168,59 @@ fdm_status fdm_batch_enqueue_steps(fdm_batch* b, int32_t nsteps) {
     return replay_steps(b->graphs, nsteps, b->stream);
 }
 
+// FDM_ERR_TIMEOUT if a persistent launch of the batch gave up at a barrier (waits)
+static fdm_status persist_status(fdm_batch* b) {
+    if (!b->persist_used) return FDM_OK;
+    int st = 0;
+    FDM_CK(cudaMemcpyAsync(&st, &b->persist_bar->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    FDM_CK(cudaStreamSynchronize(b->stream));
+    return (fdm_status)st;
+}
+
+fdm_status fdm_batch_enqueue_steps_persistent(fdm_batch* b, int32_t nsteps) {
+    if (!b || nsteps < 0) return FDM_ERR_INVALID_ARG;
+    if (nsteps == 0) return FDM_OK;
+    const int ng = (int)b->groups.size();
+    std::vector<const Dev*> devs;
+    for (auto& G : b->groups) devs.push_back(&G.d);
+    fdm_status st;
+    if (!b->persist_desc) {
+        std::vector<unsigned char> host(persist_group_bytes() * ng);
+        size_t smem = 0;
+        if ((st = persist_prepare(devs.data(), ng, host.data(), &smem))) return st;
+        void* desc = nullptr;
+        void* bar = nullptr;
+        if ((st = b->arena.alloc(&desc, host.size()))) return st;
+        if ((st = b->arena.alloc(&bar, sizeof(PersistBarrier)))) return st;
+        FDM_CK(cudaMemcpyAsync(desc, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream));
+        FDM_CK(cudaStreamSynchronize(b->stream));
+        b->persist_desc = desc;
+        b->persist_bar = (PersistBarrier*)bar;
+        b->persist_smem = smem;
+    }
+    // a fresh barrier for this launch
+    int dev = 0, khz = 0;
+    FDM_CK(cudaGetDevice(&dev));
+    FDM_CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    PersistBarrier pb;
+    std::memset(&pb, 0, sizeof(pb));
+    pb.extra = g_barrier_extra;
+    pb.limit_cycles = (long long)(g_barrier_limit_s * (double)khz * 1e3);
+    FDM_CK(cudaMemcpyAsync(b->persist_bar, &pb, sizeof(pb), cudaMemcpyHostToDevice, b->stream));
+    FDM_CK(cudaStreamSynchronize(b->stream));
+    FDM_CK(persist_launch(b->persist_desc, ng, nsteps, b->persist_bar, b->persist_smem, b->stream));
+    b->persist_used = true;
+    return FDM_OK;
+}
+
+void fdm_debug_barrier(int32_t extra_arrivals, double limit_seconds) {
+    g_barrier_extra = extra_arrivals > 0 ? extra_arrivals : 0;
+    g_barrier_limit_s = limit_seconds > 0.0 ? limit_seconds : 1.0;
+}
+
 fdm_status fdm_batch_sync(fdm_batch* b, int64_t* steps_left) {
     if (!b) return FDM_ERR_INVALID_ARG;
-    fdm_status first = FDM_OK;
+    fdm_status first = persist_status(b);
     for (auto& G : b->groups) {
         std::vector<fdm_dev_scalars> s(G.members.size());
         FDM_CK(cudaMemcpyAsync(s.data(), G.d.sc, s.size() * sizeof(fdm_dev_scalars), cudaMemcpyDeviceToHost,
@@ -174,6 +236,7 @@ fdm_status fdm_batch_sync(fdm_batch* b, int64_t* steps_left) {
 
 fdm_status fdm_batch_sync_status(fdm_batch* b, int64_t* steps_left, int32_t* status) {
     if (!b) return FDM_ERR_INVALID_ARG;
+    if (fdm_status pst = persist_status(b)) return pst;
     for (auto& G : b->groups) {
         std::vector<fdm_dev_scalars> s(G.members.size());
         FDM_CK(cudaMemcpyAsync(s.data(), G.d.sc, s.size() * sizeof(fdm_dev_scalars), cudaMemcpyDeviceToHost,

@@ -110,6 +110,24 @@ void launch_kernel_table(double* Kh, int n1, int n2, int nz, int nh, double mu, 
 void launch_stress_table(double* Kh, int n1, int n2, int nz, int comp, double mu, double nu, const double* w3,
                          cudaStream_t s);
 
+// Persistent batched step (mixed precision groups): every phase of every group in one
+// cooperative launch of resident blocks, phases separated by a bounded grid barrier.
+constexpr int kPersistThreads = 512;
+struct PersistBarrier {
+    unsigned int count;       // arrivals in the current round
+    unsigned int gen;         // completed rounds
+    int status;               // FDM_OK, or FDM_ERR_TIMEOUT once a wait gave up
+    int extra;                // arrivals expected beyond the grid (a test hook; 0 normally)
+    long long limit_cycles;   // a barrier wait gives up after this many SM clock cycles
+};
+// bytes of one group descriptor; fills host_desc[ngroups] (FDM_ERR_INVALID_ARG unless every
+// group is FDM_MIXED with n1 >= 32) and the dynamic shared memory the launch needs
+size_t persist_group_bytes();
+fdm_status persist_prepare(const Dev* const* groups, int ngroups, void* host_desc, size_t* smem);
+// dev_desc: the descriptors in device memory; bar: reset by the caller (count, status = 0)
+cudaError_t persist_launch(const void* dev_desc, int ngroups, int nsteps, PersistBarrier* bar, size_t smem,
+                           cudaStream_t s);
+
 struct df;  // double-word type (fdm_df.cuh)
 
 // Runs BODY with T bound to the storage/arithmetic type of precision PREC.

@@ -126,15 +126,15 @@ __device__ __forceinline__ const cpx<T>* stage_twiddles(const cpx<T>* pt, cpx<T>
 // ------------------------------------------------------------------ row forward (R2C)
 // grid: n2 / R blocks; block b handles rows [b R, b R + R).  Optional FP64 sum of each row
 // (for <U13>), in an order fixed by the row alone, so that results do not depend on R.
+// body of one block: rows [tile R, tile R + R) of instance inst (also run as a task of the
+// persistent batched step)
 template <typename T>
-__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
-                                                          int n1, int n2, int R,
-                                                          const cpx<T>* __restrict__ tw1,
-                                                          const cpx<T>* __restrict__ pt1,
-                                                          double* row_partials, InstCtl ctl) {
+__device__ __forceinline__ void row_forward_body(const T* src0, const T* src1, cpx<T>* spec, int n1, int n2, int R,
+                                                 const cpx<T>* __restrict__ tw1, const cpx<T>* __restrict__ pt1,
+                                                 double* row_partials, InstCtl ctl, int tile, int inst) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_run, s_cur;
-    const int inst = blockIdx.y;
+    
     if (threadIdx.x == 0) inst_state(ctl, inst, &s_run, &s_cur);
     __syncthreads();
     if (!s_run) return;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     const int ld = padded_len(L);  // padded sequence stride (bank spread for the transposed store)
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);  // R * ld elements
     const cpx<T>* ptw = stage_twiddles<T>(pt1, A + R * ld, L);
-    const int y0 = blockIdx.x * R;
+    const int y0 = tile * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
     const int total = R * L, step = blockDim.x;
@@ -182,6 +182,15 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
         int kx = e >> lR, r = e & (R - 1);
         spec[(size_t)kx * n2 + y0 + r] = A[r * ld + swz(kx)];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_forward_kernel(const T* src0, const T* src1, cpx<T>* spec,
+                                                          int n1, int n2, int R,
+                                                          const cpx<T>* __restrict__ tw1,
+                                                          const cpx<T>* __restrict__ pt1,
+                                                          double* row_partials, InstCtl ctl) {
+    row_forward_body<T>(src0, src1, spec, n1, n2, R, tw1, pt1, row_partials, ctl, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------ column pass
@@ -246,11 +255,11 @@ __device__ __forceinline__ cpx<T> col_apply(const ColArgs<T>& a, const T* __rest
     return mk(-(m.y * z.y), m.y * z.x);
 }
 
+// body of one block: columns [tile C, tile C + C) of instance inst
 template <typename T>
-__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
-                                                       int n1, int n2, int C,
-                                                       const cpx<T>* __restrict__ pt2, const T* __restrict__ Kh,
-                                                       ColArgs<T> a) {
+__device__ __forceinline__ void col_pass_body(const cpx<T>* in, cpx<T>* out, int n1, int n2, int C,
+                                              const cpx<T>* __restrict__ pt2, const T* __restrict__ Kh,
+                                              ColArgs<T> a, int tile, int inst) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ld = padded_len(n2);
     const int ln2 = 31 - __clz(n2);
@@ -258,7 +267,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     __shared__ double s_sigma;
     __shared__ double s_red[kRedLanes];
     __shared__ int s_run, s_cur;
-    const int inst = blockIdx.y;
+    
     if (threadIdx.x == 0) {
         InstCtl ctl{a.mode == COL_K ? a.sc : nullptr, a.gated};
         inst_state(ctl, inst, &s_run, &s_cur);
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     out += inst * half_n;
     fdm_dev_scalars* sci = a.sc ? a.sc + inst : nullptr;
     const double* parts = a.row_partials ? a.row_partials + (size_t)inst * a.nparts : nullptr;
-    const int kx0 = blockIdx.x * C;
+    const int kx0 = tile * C;
     const cpx<T>* src = in + (size_t)kx0 * n2;
     {
         const int total = C * n2, step = blockDim.x;
@@ -341,6 +350,14 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col
     for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = A[(e >> ln2) * ld + swz(e & (n2 - 1))];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) col_pass_kernel(const cpx<T>* in, cpx<T>* out,  // may alias (in place)
+                                                       int n1, int n2, int C,
+                                                       const cpx<T>* __restrict__ pt2, const T* __restrict__ Kh,
+                                                       ColArgs<T> a) {
+    col_pass_body<T>(in, out, n1, n2, C, pt2, Kh, a, blockIdx.x, blockIdx.y);
+}
+
 // ------------------------------------------------------------------ row inverse (C2R)
 // grid: n2 / R blocks.  mode ROW_PLAIN: write the real rows (+ offset).  ROW_TAU: write
 // tau13 and reduce max |v0| of the celerity law into sc->vmax_bits.
@@ -400,17 +417,18 @@ struct RowArgs {
     double cfl, dx, dt_max;    // ROW_TAU: time-step rule (FP64)
 };
 
+// body of one block: rows [tile R, tile R + R) of instance inst; ntiles = row blocks per
+// instance (the last of them to finish computes the step's dt)
 template <typename T>
-__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_inverse_kernel(const cpx<T>* spec, T* dst,
-                                                          int n1, int n2, int R,
-                                                          const cpx<T>* __restrict__ tw1,
-                                                          const cpx<T>* __restrict__ pt1, RowArgs<T> a) {
+__device__ __forceinline__ void row_inverse_body(const cpx<T>* spec, T* dst, int n1, int n2, int R,
+                                                 const cpx<T>* __restrict__ tw1, const cpx<T>* __restrict__ pt1,
+                                                 RowArgs<T> a, int tile, int inst, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = n1 >> 1;
     const int ld = padded_len(L);
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
     __shared__ int s_run, s_cur;
-    const int inst = blockIdx.y;
+    
     if (threadIdx.x == 0) {
         InstCtl ctl{a.mode == ROW_TAU ? a.sc : nullptr, a.gated};
         inst_state(ctl, inst, &s_run, &s_cur);
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
     spec += inst * (nn / 2);
     dst += inst * nn;
     fdm_dev_scalars* sci = (a.mode == ROW_TAU) ? a.sc + inst : nullptr;
-    const int y0 = blockIdx.x * R;
+    const int y0 = tile * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     {
         const int total = R * L, step = blockDim.x;
@@ -488,7 +506,7 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (atomicAdd(&sci->ri_count, 1u) == gridDim.x - 1) {
+            if (atomicAdd(&sci->ri_count, 1u) == (unsigned)ntiles - 1u) {
                 __threadfence();
                 const double vmax = __longlong_as_double((long long)atomicAdd(&sci->vmax_bits, 0ull));
                 const double dtd = cfl_dt(vmax, a.cfl, a.dx, a.dt_max);
@@ -498,6 +516,14 @@ __global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row
             }
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FftBounds<T>::threads, FftBounds<T>::minb) row_inverse_kernel(const cpx<T>* spec, T* dst,
+                                                          int n1, int n2, int R,
+                                                          const cpx<T>* __restrict__ tw1,
+                                                          const cpx<T>* __restrict__ pt1, RowArgs<T> a) {
+    row_inverse_body<T>(spec, dst, n1, n2, R, tw1, pt1, a, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // max |v0| of the celerity law over the nodes of a single instance for a tau13 computed outside
@@ -579,10 +605,12 @@ template <> struct KnpShapes<df> {
 
 // grid (n1 / tx, n2 / (ty npt), instances); block (tx, ty); thread (i, j) updates the
 // nodes (bx + i, by + j + k ty), k < npt
+// body of one block: the tile (tbx, tby) of instance inst, ntiles tiles per instance (the
+// last to start advances the clock); thread (tx_, ty_) of a tx x TY block
 template <typename T, int V>
-__global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V])
-    knp_step_kernel(const T* phi0, const T* phi1, const T* __restrict__ tau0, int n1, int n2, int npt,
-                    KnpArgs<T> a) {
+__device__ __forceinline__ void knp_step_body(const T* phi0, const T* phi1, const T* __restrict__ tau0, int n1, int n2,
+                                              int npt, KnpArgs<T> a, int tbx, int tby, int inst, int ntiles, int tx_,
+                                              int ty_, int tx) {
     constexpr int TY = KnpShapes<T>::ty[V];
     constexpr int NPT = KnpShapes<T>::npt[V];
     // FP32 carries the state as a pair of words, U13 = hi + lo: the node update works on
@@ -594,11 +622,9 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     __shared__ T s_tau[TY * NPT][TX];
     __shared__ T s_dt;
     __shared__ int s_run, s_cur;
-    const int inst = blockIdx.z;
-    const int tx = blockDim.x;  // TX, or n1 when n1 < TX
     const int rows = TY * npt;
-    const int bx = blockIdx.x * tx, by = blockIdx.y * rows;
-    const int tid = threadIdx.y * tx + threadIdx.x;
+    const int bx = tbx * tx, by = tby * rows;
+    const int tid = ty_ * tx + tx_;
     fdm_dev_scalars* sc = a.sc + inst;
     if (tid == 0) {
         InstCtl ctl{a.sc, a.gated};
@@ -613,7 +639,7 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
             // fenced counter increment)
             s_dt = T(sc->dt_h_next);
             __threadfence();
-            const unsigned int total = gridDim.x * gridDim.y;
+            const unsigned int total = (unsigned)ntiles;
             if (atomicAdd(&sc->done_count, 1u) == total - 1) {
                 __threadfence();
                 const double vmax = __longlong_as_double((long long)sc->vmax_bits);
@@ -638,16 +664,16 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     const T* tau = tau0 + inst * nn;
     const T* lo_in = kPair ? (s_cur ? a.lo1 : a.lo0) + inst * nn : nullptr;
     T* lo_out = kPair ? const_cast<T*>(s_cur ? a.lo0 : a.lo1) + inst * nn : nullptr;
-    const int x = bx + threadIdx.x;
+    const int x = bx + tx_;
     T tv[NPT];   // tau13 at this thread's nodes: loads issued ahead of the tile's
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (k < npt) tv[k] = tau[(size_t)(by + threadIdx.y + k * TY) * n1 + x];
+        if (k < npt) tv[k] = tau[(size_t)(by + ty_ + k * TY) * n1 + x];
     // the tile and its halo go straight from global to shared memory with asynchronous
     // copies, all of a thread's in flight at once (no register staging, no wait per element)
-    for (int ly = threadIdx.y; ly < rows + 4; ly += TY) {
+    for (int ly = ty_; ly < rows + 4; ly += TY) {
         const int gy = (by + ly - 2) & (n2 - 1);
-        for (int lx = threadIdx.x; lx < tx + 4; lx += tx) {
+        for (int lx = tx_; lx < tx + 4; lx += tx) {
             const int gx = (bx + lx - 2) & (n1 - 1);
             copy_async<T>(&tile[ly][lx], phi + (size_t)gy * n1 + gx);
             if constexpr (kPair) copy_async<T>(&tile_lo[ly][lx], lo_in + (size_t)gy * n1 + gx);
@@ -656,10 +682,10 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     copy_async_wait_all();
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (k < npt) s_tau[threadIdx.y + k * TY][threadIdx.x] = tv[k];
+        if (k < npt) s_tau[ty_ + k * TY][tx_] = tv[k];
     __syncthreads();
     const T dt = s_dt;
-    const int lx = threadIdx.x + 2;
+    const int lx = tx_ + 2;
     const double phi_ref = a.vel.friction ? sc->phi_ref : 0.0;
     if constexpr (kPair) {
         // two nodes per pass, (x, y) and (x, y + TY), one in each lane of the packed FP32
@@ -667,11 +693,11 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
 #pragma unroll 1
         for (int k = 0; k < npt; k += 2) {
             const int k2 = (k + 1 < npt) ? k + 1 : k;
-            const int ya = by + threadIdx.y + k * TY, yb = by + threadIdx.y + k2 * TY;
-            const int la = threadIdx.y + k * TY + 2, lb = threadIdx.y + k2 * TY + 2;
+            const int ya = by + ty_ + k * TY, yb = by + ty_ + k2 * TY;
+            const int la = ty_ + k * TY + 2, lb = ty_ + k2 * TY + 2;
             const float ha = tile[la][lx], lo_a = tile_lo[la][lx], hb = tile[lb][lx], lo_b = tile_lo[lb][lx];
-            f2 v0 = mkf2(celerity(a.vel, s_tau[la - 2][threadIdx.x], ha + lo_a, phi_ref),
-                         celerity(a.vel, s_tau[lb - 2][threadIdx.x], hb + lo_b, phi_ref));
+            f2 v0 = mkf2(celerity(a.vel, s_tau[la - 2][tx_], ha + lo_a, phi_ref),
+                         celerity(a.vel, s_tau[lb - 2][tx_], hb + lo_b, phi_ref));
             if (a.vel.mfac)
                 v0 = mkf2(v0.x * a.vel.mfac[inst * nn + (size_t)ya * n1 + x],
                           v0.y * a.vel.mfac[inst * nn + (size_t)yb * n1 + x]);
@@ -698,9 +724,9 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
     } else {
 #pragma unroll 1
         for (int k = 0; k < npt; ++k) {
-            const int y = by + threadIdx.y + k * TY;
-            const int ly = threadIdx.y + k * TY + 2;
-            const T tau_k = s_tau[threadIdx.y + k * TY][threadIdx.x];
+            const int y = by + ty_ + k * TY;
+            const int ly = ty_ + k * TY + 2;
+            const T tau_k = s_tau[ty_ + k * TY][tx_];
             const T up = tile[ly][lx];
             T v0 = celerity(a.vel, tau_k, up, phi_ref);
             if (a.vel.mfac) v0 = v0 * a.vel.mfac[inst * nn + (size_t)y * n1 + x];
@@ -708,6 +734,14 @@ __global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V
             out[(size_t)y * n1 + x] = knp_node<T>(f, v0, dt, a.theta, a.theta_code, a.time_level);
         }
     }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(TX * KnpShapes<T>::ty[V], KnpShapes<T>::minb[V])
+    knp_step_kernel(const T* phi0, const T* phi1, const T* __restrict__ tau0, int n1, int n2, int npt,
+                    KnpArgs<T> a) {
+    knp_step_body<T, V>(phi0, phi1, tau0, n1, n2, npt, a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y,
+                        threadIdx.x, threadIdx.y, blockDim.x);
 }
 
 // ------------------------------------------------------------------ set-up / readout helpers
@@ -1025,9 +1059,7 @@ void launch_row_forward(const Dev& d, const T* src0, const T* src1, cpx<T>* spec
 }
 
 template <typename T>
-void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, int count, cudaStream_t s,
-                int sym_odd2 = 0, int sym_imag = 0) {
-    const LaunchGeom& g = d.geom;
+ColArgs<T> col_args(const Dev& d, int mode, bool with_mean, int sym_odd2 = 0, int sym_imag = 0) {
     ColArgs<T> a;
     a.p = d.p;
     a.mode = mode;
@@ -1040,15 +1072,20 @@ void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with
     a.xi2_unit = T(6.283185307179586476925286766559 / ((double)d.p.n2 * d.p.dx));
     a.sym_odd2 = sym_odd2;
     a.sym_imag = sym_imag;
+    return a;
+}
+template <typename T>
+void launch_col(const Dev& d, const cpx<T>* in, cpx<T>* out, int mode, bool with_mean, int count, cudaStream_t s,
+                int sym_odd2 = 0, int sym_imag = 0) {
+    const LaunchGeom& g = d.geom;
     dim3 grid(g.col_blocks, count);
-    col_pass_kernel<T><<<grid, g.col_threads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C,
-                                                             (const cpx<T>*)d.pt2, (const T*)d.Kh, a);
+    col_pass_kernel<T><<<grid, g.col_threads, g.col_smem, s>>>(in, out, d.p.n1, d.p.n2, g.C, (const cpx<T>*)d.pt2,
+                                                             (const T*)d.Kh,
+                                                             col_args<T>(d, mode, with_mean, sym_odd2, sym_imag));
 }
 
 template <typename T>
-void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, double offset, int count,
-                        cudaStream_t s) {
-    const LaunchGeom& g = d.geom;
+RowArgs<T> row_args(const Dev& d, int mode, double offset) {
     RowArgs<T> a;
     a.vel = make_vel<T>(d.p, d.mfac);
     a.mode = mode;
@@ -1060,9 +1097,16 @@ void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, doub
     a.cfl = d.p.cfl;
     a.dx = d.p.dx;
     a.dt_max = d.p.dt_max;
+    return a;
+}
+template <typename T>
+void launch_row_inverse(const Dev& d, const cpx<T>* spec, T* dst, int mode, double offset, int count,
+                        cudaStream_t s) {
+    const LaunchGeom& g = d.geom;
     dim3 grid(g.row_blocks, count);
     row_inverse_kernel<T><<<grid, g.row_threads, g.row_smem, s>>>(spec, dst, d.p.n1, d.p.n2, g.R,
-                                                                (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1, a);
+                                                                (const cpx<T>*)d.tw1, (const cpx<T>*)d.pt1,
+                                                                row_args<T>(d, mode, offset));
 }
 
 template <typename T, int V>
@@ -1077,7 +1121,7 @@ void launch_knp_shape(const Dev& d, const KnpArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_knp(const Dev& d, cudaStream_t s) {
+KnpArgs<T> knp_args(const Dev& d) {
     KnpArgs<T> a;
     a.vel = make_vel<T>(d.p, d.mfac);
     a.lo0 = (const T*)d.phi_lo[0];
@@ -1087,6 +1131,11 @@ void launch_knp(const Dev& d, cudaStream_t s) {
     a.time_level = d.p.time_level;
     a.sc = d.sc;
     a.gated = d.gated;
+    return a;
+}
+template <typename T>
+void launch_knp(const Dev& d, cudaStream_t s) {
+    const KnpArgs<T> a = knp_args<T>(d);
     switch (d.geom.knp_shape) {
         case 1: launch_knp_shape<T, 1>(d, a, s); break;
         case 2: launch_knp_shape<T, 2>(d, a, s); break;
@@ -1278,6 +1327,173 @@ void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, con
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
     velocity_kernel<T><<<blocks, 256, 0, s>>>(a11, a12, tau, phi, v1, v2, n, make_vel<T>(d.p, d.mfac), d.phi_ref_host);
+}
+
+// ------------------------------------------------------------------ persistent batched step
+// All phases of all groups of a mixed-precision batch in ONE cooperative launch of resident
+// blocks: for each step, the four phases in order; in a phase the blocks take the tasks
+// (group, instance, tile) round-robin and run the same block bodies as the separate kernels;
+// a grid-wide barrier separates the phases.  Every barrier wait is bounded: a block that waits
+// longer than the limit records FDM_ERR_TIMEOUT and every block then leaves the kernel.
+struct PersistGroup {
+    const float* phi0;
+    const float* phi1;
+    float* tau;
+    cpx<float>* spec;
+    const float* Kh;
+    const cpx<float>* tw1;
+    const cpx<float>* pt1;
+    const cpx<float>* pt2;
+    double* row_partials;
+    int n1, n2, count;
+    int R, C;                     // rows / columns per transform task
+    int row_tiles, col_tiles;     // transform tasks per instance
+    int knp_gx, knp_gy, knp_npt;  // stencil tasks per instance (gx x gy) and nodes per thread
+    InstCtl ctl;
+    ColArgs<float> col;
+    RowArgs<float> row;
+    KnpArgs<float> knp;
+};
+
+// grid barrier with a bounded wait (state in device memory, reset before each launch)
+__device__ bool grid_barrier(PersistBarrier* b) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* gen = &b->gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == (unsigned int)(gridDim.x + b->extra) - 1u) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            volatile int* st = &b->status;
+            while (*gen == g) {
+                if (*st != 0 || clock64() - t0 > b->limit_cycles) {
+                    atomicCAS(&b->status, 0, (int)FDM_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)&b->status != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+constexpr int kPersistShape = 2;   // the FP32 stencil shape of TX x 16 threads, two nodes each
+
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    persistent_step_kernel(const PersistGroup* __restrict__ groups, int ngroups, int nsteps, PersistBarrier* bar) {
+    for (int step = 0; step < nsteps; ++step) {
+        for (int phase = 0; phase < kKernelsPerStep; ++phase) {
+            int task = blockIdx.x, base = 0;
+            for (int gi = 0; gi < ngroups; ++gi) {
+                const PersistGroup& G = groups[gi];
+                const int per = (phase == 0 || phase == 2) ? G.row_tiles : (phase == 1 ? G.col_tiles : G.knp_gx * G.knp_gy);
+                const int ntask = per * G.count;
+                for (; task < base + ntask; task += gridDim.x) {
+                    const int local = task - base, inst = local / per, tile = local - inst * per;
+                    if (phase == 0) {
+                        row_forward_body<float>(G.phi0, G.phi1, G.spec, G.n1, G.n2, G.R, G.tw1, G.pt1, G.row_partials,
+                                                G.ctl, tile, inst);
+                    } else if (phase == 1) {
+                        col_pass_body<float>(G.spec, G.spec, G.n1, G.n2, G.C, G.pt2, G.Kh, G.col, tile, inst);
+                    } else if (phase == 2) {
+                        row_inverse_body<float>(G.spec, G.tau, G.n1, G.n2, G.R, G.tw1, G.pt1, G.row, tile, inst, per);
+                    } else {
+                        knp_step_body<float, kPersistShape>(G.phi0, G.phi1, G.tau, G.n1, G.n2, G.knp_npt, G.knp,
+                                                            tile % G.knp_gx, tile / G.knp_gx, inst, per,
+                                                            threadIdx.x & (TX - 1), threadIdx.x / TX, TX);
+                    }
+                    __syncthreads();   // the next task reuses the block's shared memory
+                }
+                base += ntask;
+            }
+            if (!grid_barrier(bar)) return;
+        }
+    }
+}
+
+// persistent shapes of a group: transforms with one radix-8 butterfly per thread at most
+fdm_status persist_group(const Dev& d, PersistGroup* out, size_t* smem) {
+    const int n1 = d.p.n1, n2 = d.p.n2, L = n1 / 2;
+    if (n1 < TX || n2 < 16) return FDM_ERR_INVALID_ARG;
+    int R = 16, C = 16;
+    while (R > 1 && (R * L > 8 * kPersistThreads || R > n2)) R >>= 1;
+    while (C > 1 && (C * n2 > 8 * kPersistThreads || C > L)) C >>= 1;
+    if (R * L > 8 * kPersistThreads || C * n2 > 8 * kPersistThreads) return FDM_ERR_INVALID_ARG;
+    const LaunchGeom g = geometry<float>(n1, n2, R, C);
+    *smem = g.row_smem > g.col_smem ? g.row_smem : g.col_smem;
+    constexpr int TY = KnpShapes<float>::ty[kPersistShape];
+    int npt = KnpShapes<float>::npt[kPersistShape];
+    while (npt > 1 && n2 < TY * npt) npt >>= 1;
+    PersistGroup G;
+    G.phi0 = (const float*)d.phi[0];
+    G.phi1 = (const float*)d.phi[1];
+    G.tau = (float*)d.tau;
+    G.spec = (cpx<float>*)d.spec;
+    G.Kh = (const float*)d.Kh;
+    G.tw1 = (const cpx<float>*)d.tw1;
+    G.pt1 = (const cpx<float>*)d.pt1;
+    G.pt2 = (const cpx<float>*)d.pt2;
+    G.row_partials = d.row_partials;
+    G.n1 = n1;
+    G.n2 = n2;
+    G.count = d.count;
+    G.R = R;
+    G.C = C;
+    G.row_tiles = g.row_blocks;
+    G.col_tiles = g.col_blocks;
+    G.knp_gx = n1 / TX;
+    G.knp_gy = n2 / (TY * npt);
+    G.knp_npt = npt;
+    G.ctl = InstCtl{d.sc, d.gated};
+    G.col = col_args<float>(d, COL_K, true);
+    G.row = row_args<float>(d, ROW_TAU, 0.0);
+    G.knp = knp_args<float>(d);
+    *out = G;
+    return FDM_OK;
+}
+
+size_t persist_group_bytes() { return sizeof(PersistGroup); }
+
+fdm_status persist_prepare(const Dev* const* groups, int ngroups, void* host_desc, size_t* smem) {
+    *smem = 0;
+    PersistGroup* g = static_cast<PersistGroup*>(host_desc);
+    for (int i = 0; i < ngroups; ++i) {
+        if (groups[i]->p.precision != FDM_MIXED) return FDM_ERR_INVALID_ARG;
+        size_t sm = 0;
+        fdm_status st = persist_group(*groups[i], &g[i], &sm);
+        if (st != FDM_OK) return st;
+        if (sm > *smem) *smem = sm;
+    }
+    return FDM_OK;
+}
+
+cudaError_t persist_launch(const void* dev_desc, int ngroups, int nsteps, PersistBarrier* bar, size_t smem,
+                           cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(persistent_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_step_kernel, kPersistThreads, smem)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const PersistGroup* gd = static_cast<const PersistGroup*>(dev_desc);
+    void* args[] = {(void*)&gd, (void*)&ngroups, (void*)&nsteps, (void*)&bar};
+    return cudaLaunchCooperativeKernel((const void*)persistent_step_kernel, dim3(sms * per_sm),
+                                       dim3(kPersistThreads), args, smem, s);
 }
 
 // explicit instantiations

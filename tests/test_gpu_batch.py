@@ -216,3 +216,69 @@ def test_allocation_failures_release_everything():
         B.debug_fail_allocation(-1)
     torch.cuda.synchronize()
     assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+
+
+def test_persistent_launch_equals_graph_steps():
+    """The batched steps as one persistent cooperative launch (every phase of every size class,
+    grid barriers between phases) give the same results bit for bit as the graph-replayed
+    per-kernel launches, with uneven sizes and step budgets."""
+    specs = [(64, 0, 30), (128, 1, 17), (64, 2, 9), (256, 3, 30), (128, 4, 0), (32, 5, 22)]
+    params = [coupled(n, B.MIXED) for n, _, _ in specs]
+    ups = [inputs.random_up(n, seed=40 + s, ell=8.0) for n, s, _ in specs]
+    out = {}
+    for mode in ("graph", "persistent"):
+        with Batch(params) as b:
+            for i, (n, s, steps) in enumerate(specs):
+                b.set_plastic_distortion(i, ups[i])
+                b.set_budget(i, steps)
+            if mode == "graph":
+                b.enqueue_steps(12)
+                b.enqueue_steps(20)
+            else:
+                b.enqueue_steps_persistent(12)
+                b.enqueue_steps_persistent(20)
+            assert (b.sync() == 0).all()
+            out[mode] = [(b.read_fields(i, "up13", "tau13"), b.info(i)) for i in range(len(specs))]
+    for i, (n, s, steps) in enumerate(specs):
+        (fg, ig), (fp, ip) = out["graph"][i], out["persistent"][i]
+        assert ip.step == ig.step == steps and ip.t == ig.t
+        np.testing.assert_array_equal(fp["up13"], fg["up13"])
+        np.testing.assert_array_equal(fp["tau13"], fg["tau13"])
+
+
+def test_persistent_launch_barrier_wait_is_bounded():
+    """A barrier that can never complete (the test hook makes it wait for one block more than
+    the grid holds) gives up after its limit: the launch ends, the batch reports
+    FDM_ERR_TIMEOUT, and the device stays usable (a new batch steps normally)."""
+    import time
+    n = 64
+    params = [coupled(n, B.MIXED), coupled(128, B.MIXED)]
+    ups = [inputs.random_up(n, seed=50, ell=6.0), inputs.random_up(128, seed=51, ell=6.0)]
+    try:
+        B.debug_barrier(1, 0.05)
+        with Batch(params) as b:
+            for i in range(2):
+                b.set_plastic_distortion(i, ups[i])
+                b.set_budget(i, 5)
+            t0 = time.perf_counter()
+            b.enqueue_steps_persistent(3)
+            with pytest.raises(B.FDMError) as e:
+                b.sync()
+            assert e.value.status == B.FDM_ERR_TIMEOUT
+            assert time.perf_counter() - t0 < 5.0
+    finally:
+        B.debug_barrier(0, 0.0)
+    with Batch(params) as b:
+        for i in range(2):
+            b.set_plastic_distortion(i, ups[i])
+            b.set_budget(i, 5)
+        b.enqueue_steps_persistent(5)
+        assert (b.sync() == 0).all()
+        got = b.read_fields(0, "up13")["up13"]
+    with Batch(params) as b:
+        for i in range(2):
+            b.set_plastic_distortion(i, ups[i])
+            b.set_budget(i, 5)
+        b.enqueue_steps(5)
+        b.sync()
+        np.testing.assert_array_equal(got, b.read_fields(0, "up13")["up13"])
