@@ -230,6 +230,32 @@ fdm_status fdm_static_solve_heterogeneous(fdm_handle *h, const double *mu_factor
                                           double *sigma13, double *sigma23, int32_t *iterations,
                                           double *residual);
 
+/* Heterogeneous elasticity for a plastic layer thinner than the cell (Sec. 3.1.2,
+ * heterogeneous medium; the layer of nh planes in the cell of nz, Sec. 3.2.1), FDM_FP64
+ * handles with nz even.  The medium is isotropic with both Lame moduli scaled by
+ * mu_factor(x1, x2) (host [n2][n1], finite, > 0), uniform through the cell's depth; the
+ * eigenstrain is eps^p_13 = eps^p_31 = U13(x1, x2) chi(x3) / 2 of the current state.  The
+ * paper's series expansion is summed by the fixed-point iteration on the strain,
+ *   eps <- E - Gamma0 * ((C - C0) : eps - C : eps^p),
+ * from eps = 0, with the isotropic reference C0 = f0 C, f0 = (min + max of mu_factor) / 2, and
+ * the Green operator's terms odd in an axis at its Nyquist frequency removed (the operator
+ * averaged over that axis's sign).  Because the medium does not vary along x3 the Fourier
+ * modes in x3 are independent: the GPU iterates the nz/2 + 1 modes' complex 2-D fields
+ * together.  Loading of the current step as fdm_static_solve_heterogeneous: stress control
+ * prescribes the cell average <sigma> = sigma_bar13 (e1 (x) e3 + e3 (x) e1) (E from each
+ * iterate), strain control E = eps_bar13 (e1 (x) e3 + e3 (x) e1).  Stops when
+ * rms(eps_new - eps) <= tol max(rms(eps_new), rms(eps^p - <eps^p>)) over the cell (Frobenius)
+ * or after max_iter iterations (tol = 0: exactly max_iter).  Writes the layer average of
+ * sigma13 = 2 mu_factor mu (eps13 - eps^p13) to tau13 (host [n2][n1]) and, for nplanes > 0,
+ * sigma13 on planes[k] in [0, nz) to sigma13_planes ([nplanes][n2][n1]).  Device memory of
+ * the solve, allocated and freed by the call: 3 x 12 (nz/2 + 1) n1 n2 doubles plus the
+ * outputs (FDM_ERR_OOM when it does not fit).  The state is unchanged.  Errors:
+ * FDM_ERR_INVALID_ARG (not FP64, nz odd, bad field or planes), FDM_ERR_STATE (no state, or a
+ * step in progress), FDM_ERR_NONFINITE (the iteration diverged). */
+fdm_status fdm_static_solve_heterogeneous_layer(fdm_handle *h, const double *mu_factor, double tol, int32_t max_iter,
+                                                double *tau13, int32_t nplanes, const int32_t *planes,
+                                                double *sigma13_planes, int32_t *iterations, double *residual);
+
 /* Time steps with heterogeneous elasticity: mu_factor (host [n2][n1], as for
  * fdm_static_solve_heterogeneous; requires nh == nz) becomes the shear-modulus field of every
  * later fdm_static_solve and step of the handle, whose static problem is then the

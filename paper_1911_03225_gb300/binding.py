@@ -49,7 +49,8 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_set_launch_config", "fdm_launch_candidates", "fdm_set_mobility_field", "fdm_set_loading",
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
            "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field",
-           "fdm_measure_arith_rate", "fdm_batch_enqueue_steps_persistent", "fdm_debug_barrier"]
+           "fdm_measure_arith_rate", "fdm_batch_enqueue_steps_persistent", "fdm_debug_barrier",
+           "fdm_static_solve_heterogeneous_layer"]
 
 
 class CParams(C.Structure):
@@ -189,6 +190,10 @@ def load():
     lib.fdm_static_solve_heterogeneous.argtypes = [H, d, C.c_double, C.c_int32, d, d, C.POINTER(C.c_int32),
                                                    C.POINTER(C.c_double)]
     lib.fdm_static_solve_heterogeneous.restype = C.c_int
+    lib.fdm_static_solve_heterogeneous_layer.argtypes = [H, d, C.c_double, C.c_int32, d, C.c_int32,
+                                                         C.POINTER(C.c_int32), d, C.POINTER(C.c_int32),
+                                                         C.POINTER(C.c_double)]
+    lib.fdm_static_solve_heterogeneous_layer.restype = C.c_int
     lib.fdm_set_shear_modulus_field.argtypes = [H, d, C.c_double, C.c_int32]
     lib.fdm_set_shear_modulus_field.restype = C.c_int
     lib.fdm_debug_fail_allocation.argtypes = [C.c_int32]
@@ -363,6 +368,24 @@ class FDM:
                                                        _dptr(s23), C.byref(it), C.byref(r)),
                "fdm_static_solve_heterogeneous")
         return s13, s23, it.value, r.value
+
+    def static_solve_heterogeneous_layer(self, mu_factor, tol: float = 1e-12, max_iter: int = 200, planes=()):
+        """Static problem of a plastic layer thinner than the cell in a medium whose moduli
+        are scaled by mu_factor(x1, x2), uniform through the depth (FP64 handles, nz even):
+        returns (tau13 = layer average of sigma13, sigma13 on the planes or None, iterations,
+        residual)."""
+        p = self.params
+        f = _field(mu_factor, (p.n2, p.n1))
+        tau = np.zeros((p.n2, p.n1))
+        pl = np.ascontiguousarray(planes, dtype=np.int32)
+        out = np.zeros((len(pl), p.n2, p.n1)) if len(pl) else None
+        it, res = C.c_int32(0), C.c_double(0.0)
+        _check(self.lib.fdm_static_solve_heterogeneous_layer(
+            self.h, _dptr(f), float(tol), int(max_iter), _dptr(tau), len(pl),
+            pl.ctypes.data_as(C.POINTER(C.c_int32)) if len(pl) else None,
+            _dptr(out) if out is not None else None, C.byref(it), C.byref(res)),
+            "fdm_static_solve_heterogeneous_layer")
+        return tau, out, it.value, res.value
 
     def set_shear_modulus_field(self, mu_factor=None, tol: float = 1e-12, max_iter: int = 200):
         """Heterogeneous elasticity in every later static solve and step: shear modulus

@@ -828,6 +828,81 @@ fdm_status fdm_static_solve_heterogeneous(fdm_handle* h, const double* mu_factor
     return FDM_OK;
 }
 
+fdm_status fdm_static_solve_heterogeneous_layer(fdm_handle* h, const double* mu_factor, double tol, int32_t max_iter,
+                                                double* tau13, int32_t nplanes, const int32_t* planes,
+                                                double* sigma13_planes, int32_t* iterations, double* residual) {
+    if (!h || !mu_factor || !tau13 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1 || nplanes < 0)
+        return FDM_ERR_INVALID_ARG;
+    const fdm_params& p = h->d.p;
+    if (h->prec != FDM_FP64 || p.nz < 2 || (p.nz & 1)) return FDM_ERR_INVALID_ARG;
+    if (nplanes > 0 && (!planes || !sigma13_planes)) return FDM_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < nplanes; ++k)
+        if (planes[k] < 0 || planes[k] >= p.nz) return FDM_ERR_INVALID_ARG;
+    const size_t n = h->n;
+    double fmin = HUGE_VAL, fmax = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!(mu_factor[i] > 0.0) || !std::isfinite(mu_factor[i])) return FDM_ERR_INVALID_ARG;
+        fmin = std::fmin(fmin, mu_factor[i]);
+        fmax = std::fmax(fmax, mu_factor[i]);
+    }
+    if (!h->has_state || h->next_phase != 0) return FDM_ERR_STATE;
+    fdm_dev_scalars s;
+    fdm_status st;
+    if ((st = read_scalars(h, &s))) return st;
+    double eps = 0.0, sig = 0.0;
+    host_loading(p, s.step, s.t, s.mean_up13, &eps, &sig);
+    const bool stress = p.loading_mode == FDM_LOAD_STRESS || p.loading_mode == FDM_LOAD_ZERO_MEAN_STRESS;
+    // device memory of this solve only: the modulus field, three sets of 12 (nz/2 + 1) fields,
+    // the outputs and the reduction partials
+    const size_t fields = (size_t)12 * (p.nz / 2 + 1) * n;
+    const int nblk = red_blocks_for(fields);
+    void* f_dev = nullptr;
+    void* bufs[3] = {nullptr, nullptr, nullptr};
+    void *tau_dev = nullptr, *planes_dev = nullptr, *out_dev = nullptr, *part = nullptr;
+    auto release = [&]() {
+        for (void* q : {f_dev, bufs[0], bufs[1], bufs[2], tau_dev, planes_dev, out_dev, part})
+            if (q) h->arena.release(q);
+    };
+    st = h->arena.alloc(&f_dev, n * sizeof(double));
+    for (int b = 0; b < 3 && !st; ++b) st = h->arena.alloc(&bufs[b], fields * sizeof(double));
+    if (!st) st = h->arena.alloc(&tau_dev, n * sizeof(double));
+    if (!st) st = h->arena.alloc(&part, (size_t)2 * nblk * sizeof(double));
+    if (!st && nplanes > 0) st = h->arena.alloc(&planes_dev, (size_t)nplanes * sizeof(int32_t));
+    if (!st && nplanes > 0) st = h->arena.alloc(&out_dev, (size_t)nplanes * n * sizeof(double));
+    if (st) {
+        release();
+        return st;
+    }
+    int it = 0;
+    double r = 0.0;
+    do {
+        if (cudaMemcpyAsync(f_dev, mu_factor, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            (nplanes > 0 && cudaMemcpyAsync(planes_dev, planes, (size_t)nplanes * sizeof(int32_t),
+                                            cudaMemcpyHostToDevice, h->stream) != cudaSuccess)) {
+            cudaGetLastError();
+            st = FDM_ERR_DEVICE;
+            break;
+        }
+        st = hetero_layer_solve(h->d, (const double*)f_dev, 0.5 * (fmin + fmax), stress, stress ? sig : eps, tol,
+                                max_iter, (const int*)planes_dev, nplanes, (double*)tau_dev, (double*)out_dev, bufs,
+                                (double*)part, nblk, h->stream, &it, &r);
+        if (st) break;
+        if (cudaMemcpyAsync(tau13, tau_dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            (nplanes > 0 && cudaMemcpyAsync(sigma13_planes, out_dev, (size_t)nplanes * n * sizeof(double),
+                                            cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            st = FDM_ERR_DEVICE;
+        }
+    } while (0);
+    cudaStreamSynchronize(h->stream);
+    release();
+    if (st) return st;
+    if (iterations) *iterations = it;
+    if (residual) *residual = r;
+    return FDM_OK;
+}
+
 fdm_status fdm_read_stress13_planes(fdm_handle* h, int32_t nplanes, const int32_t* planes, double* out) {
     return read_stress_planes(h, FDM_S13, nplanes, planes, out);
 }

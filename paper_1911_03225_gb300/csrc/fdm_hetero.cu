@@ -274,6 +274,375 @@ fdm_status hetero_solve(const Dev& d, const HeteroBuffers& hb, double mu0, bool 
     return FDM_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Heterogeneous elasticity for a plastic layer thinner than the cell (Sec. 3.1.2,
+// heterogeneous medium; the layer of Sec. 3.2.1), FP64.  The modulus field f(x1, x2) is
+// uniform through the depth of the cell, so the problem is invariant along x3 and its
+// Fourier modes in x3 decouple: for each k3 = 0 .. nz/2 the strain's x3-transform
+// eps-hat_k3(x1, x2) (six complex components) obeys the same fixed-point iteration as the
+// 3-D problem, eps-hat_k3 <- E nz delta_k3,0 - Gamma0(xi1, xi2, xi3(k3)) * tau-hat_k3, with
+// tau-hat_k3 = (C - C0) : eps-hat_k3 - C : eps-hat^p_k3 and
+// eps-hat^p_k3,13 = chi-hat(k3) U13 / 2, chi-hat(k3) = sum_{j < nh} exp(-2 pi i k3 j / nz).
+// Each complex component is carried as two real fields (real and imaginary parts), so one
+// iteration is a pointwise polarisation, 12 (nz/2 + 1) forward real 2-D transforms (the
+// step's row and column kernels, one launch each over all fields), the Green operator on
+// the packed spectra, the inverse transforms and the increment norms (Parseval over k3).
+// ---------------------------------------------------------------------------------
+namespace {
+
+// component order of the symmetric strain: 00 11 22 12 02 01 (02 = 13 in the paper's
+// indexing)
+__constant__ int kHlI[6] = {0, 1, 2, 1, 0, 0};
+__constant__ int kHlJ[6] = {0, 1, 2, 2, 2, 1};
+
+struct LayerArgs {
+    int n1, n2, nz, nh, M;        // M = nz/2 + 1 modes in x3
+    double mu, lam, f0;           // isotropic moduli, reference factor
+    double mu0, lam0;             // reference medium
+    int stress_control;
+    double sigma_bar13, eps_bar13;
+    size_t n;                     // n1 n2
+};
+
+// chi-hat(k3) of the layer: sum_{j < nh} exp(-2 pi i k3 j / nz)
+__device__ __forceinline__ void layer_chi(int k3, int nh, int nz, double* re, double* im) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < nh; ++j) {
+        double sn, cs;
+        sincospi(-2.0 * (double)k3 * (double)j / (double)nz, &sn, &cs);
+        sr += cs;
+        si += sn;
+    }
+    *re = sr;
+    *im = si;
+}
+
+// field index of component c (0..5), part (0 real, 1 imaginary) of mode m
+__device__ __forceinline__ size_t hl_field(int m, int c, int part) { return (size_t)m * 12 + 2 * c + part; }
+
+// tau-hat = (C - C0) : eps-hat - C : eps-hat^p, per mode and point; the state's U13
+__global__ void hl_polarise_kernel(StateRef st, const double* __restrict__ f, const double* __restrict__ eps,
+                                   double* __restrict__ tau, LayerArgs a) {
+    const int cur = st.sc->cur;
+    const size_t total = (size_t)a.M * a.n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / a.n);
+        const size_t q = i - (size_t)m * a.n;
+        const double u = state_at<double>((const double*)st.phi0, (const double*)st.phi1, nullptr, nullptr, cur, q);
+        const double fq = f[q], dl = (fq - a.f0) * a.lam, dm = (fq - a.f0) * a.mu;
+        double er[6], ei[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            er[c] = eps[hl_field(m, c, 0) * a.n + q];
+            ei[c] = eps[hl_field(m, c, 1) * a.n + q];
+        }
+        const double trr = er[0] + er[1] + er[2], tri = ei[0] + ei[1] + ei[2];
+        double cr, ci;
+        layer_chi(m, a.nh, a.nz, &cr, &ci);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double tr_ = 2.0 * dm * er[c] + (c < 3 ? dl * trr : 0.0);
+            double ti_ = 2.0 * dm * ei[c] + (c < 3 ? dl * tri : 0.0);
+            if (c == 4) {   // - C : eps^p, eps^p_13 = chi-hat U13 / 2
+                tr_ -= fq * a.mu * cr * u;
+                ti_ -= fq * a.mu * ci * u;
+            }
+            tau[hl_field(m, c, 0) * a.n + q] = tr_;
+            tau[hl_field(m, c, 1) * a.n + q] = ti_;
+        }
+    }
+}
+
+// -Gamma0 of the reference medium applied to the complex symmetric tensor Z at the
+// frequency xi (vector form: v = Z xi, w = (v - c n (n . v)) / (mu0 |xi|^2),
+// Gamma0 Z = sym(xi (x) w)), with the terms odd in an axis at its Nyquist frequency removed:
+// the operator is averaged over the sign flips of those axes (reading G8)
+__device__ void hl_gamma(const double zr[6], const double zi[6], const double xi_in[3], const int nyq[3],
+                         double mu0, double cc, double scale, double wr[6], double wi[6]) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { wr[c] = 0.0; wi[c] = 0.0; }
+    int na = 0;
+    for (int s = 0; s < 8; ++s) {
+        if (((s & 1) && !nyq[0]) || ((s & 2) && !nyq[1]) || ((s & 4) && !nyq[2])) continue;
+        ++na;
+        const double xi[3] = {(s & 1) ? -xi_in[0] : xi_in[0], (s & 2) ? -xi_in[1] : xi_in[1],
+                              (s & 4) ? -xi_in[2] : xi_in[2]};
+        const double q2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+        double Zr[3][3], Zi[3][3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            Zr[kHlI[c]][kHlJ[c]] = Zr[kHlJ[c]][kHlI[c]] = zr[c];
+            Zi[kHlI[c]][kHlJ[c]] = Zi[kHlJ[c]][kHlI[c]] = zi[c];
+        }
+        double vr[3], vi[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            vr[i] = Zr[i][0] * xi[0] + Zr[i][1] * xi[1] + Zr[i][2] * xi[2];
+            vi[i] = Zi[i][0] * xi[0] + Zi[i][1] * xi[1] + Zi[i][2] * xi[2];
+        }
+        const double nvr = (xi[0] * vr[0] + xi[1] * vr[1] + xi[2] * vr[2]) / q2;
+        const double nvi = (xi[0] * vi[0] + xi[1] * vi[1] + xi[2] * vi[2]) / q2;
+        double w_r[3], w_i[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            w_r[i] = (vr[i] - cc * xi[i] * nvr) / (mu0 * q2);
+            w_i[i] = (vi[i] - cc * xi[i] * nvi) / (mu0 * q2);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const int i = kHlI[c], j = kHlJ[c];
+            wr[c] += 0.5 * (xi[i] * w_r[j] + xi[j] * w_r[i]);
+            wi[c] += 0.5 * (xi[i] * w_i[j] + xi[j] * w_i[i]);
+        }
+    }
+    const double sc = -scale / (double)na;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { wr[c] *= sc; wi[c] *= sc; }
+}
+
+// the new strain transforms of the two real fields (A: real part, B: imaginary part of the
+// mode) at 2-D frequency k, from their transforms A(k), B(k) (complex, six components):
+// A' = G_e A + i G_o B, B' = -i G_o A + G_e B with G_e, G_o the parts of -Gamma0 even and odd
+// in (xi1, xi2) at fixed xi3, i.e. from the operator at xi = (xi1, xi2, xi3) and at
+// xi' = (-xi1, -xi2, xi3)
+__device__ void hl_point(const cpx<double> A[6], const cpx<double> B[6], double x1, double x2, double x3,
+                         const int nyq[3], double mu0, double cc, double scale, cpx<double> Ao[6], cpx<double> Bo[6]) {
+    double ar[6], ai[6], br[6], bi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { ar[c] = A[c].x; ai[c] = A[c].y; br[c] = B[c].x; bi[c] = B[c].y; }
+    const double xi[3] = {x1, x2, x3}, xim[3] = {-x1, -x2, x3};
+    double gAr[6], gAi[6], hAr[6], hAi[6], gBr[6], gBi[6], hBr[6], hBi[6];
+    hl_gamma(ar, ai, xi, nyq, mu0, cc, scale, gAr, gAi);    // G(xi) A
+    hl_gamma(ar, ai, xim, nyq, mu0, cc, scale, hAr, hAi);   // G(xi') A
+    hl_gamma(br, bi, xi, nyq, mu0, cc, scale, gBr, gBi);
+    hl_gamma(br, bi, xim, nyq, mu0, cc, scale, hBr, hBi);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        // even part E = (G + G') / 2, odd part O = (G - G') / 2
+        const double eAr = 0.5 * (gAr[c] + hAr[c]), eAi = 0.5 * (gAi[c] + hAi[c]);
+        const double oAr = 0.5 * (gAr[c] - hAr[c]), oAi = 0.5 * (gAi[c] - hAi[c]);
+        const double eBr = 0.5 * (gBr[c] + hBr[c]), eBi = 0.5 * (gBi[c] + hBi[c]);
+        const double oBr = 0.5 * (gBr[c] - hBr[c]), oBi = 0.5 * (gBi[c] - hBi[c]);
+        Ao[c] = mk(eAr - oBi, eAi + oBr);    // E A + i O B
+        Bo[c] = mk(eBr + oAi, eBi - oAr);    // E B - i O A
+    }
+}
+
+// Green operator on the packed transposed spectra of every mode, in place, normalised by
+// 1/(n1 n2); the 3-D zero frequency (mode 0, k = 0) receives nz E, with E prescribed
+// (strain control) or from the polarisation's mean (stress control)
+__global__ void hl_green_kernel(cpx<double>* __restrict__ sp, LayerArgs a) {
+    const int L = a.n1 / 2, n2 = a.n2;
+    const size_t per = (size_t)L * n2;          // packed points per field
+    const size_t total = (size_t)a.M * per;
+    const double scale = 1.0 / (double)a.n;     // 1 / (n1 n2)
+    const double cc = (a.lam0 + a.mu0) / (a.lam0 + 2.0 * a.mu0);   // n (x) n part of the acoustic tensor's inverse
+    const double two_pi = 6.283185307179586476925286766559;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / per);
+        const size_t kq = i - (size_t)m * per;
+        const int kx = (int)(kq / n2), ky = (int)(kq - (size_t)kx * n2);
+        const double x3 = two_pi * (double)m / (double)a.nz;
+        auto at = [&](int c, int part, int kyy) -> cpx<double>& {
+            return sp[hl_field(m, c, part) * per + (size_t)kx * n2 + kyy];
+        };
+        const int kys = ky <= n2 / 2 ? ky : ky - n2;
+        const double x2 = two_pi * (double)kys / (double)n2;
+        if (kx > 0) {
+            cpx<double> A[6], B[6], Ao[6], Bo[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { A[c] = at(c, 0, ky); B[c] = at(c, 1, ky); }
+            const int nyq[3] = {0, 2 * ky == n2, 2 * m == a.nz};
+            hl_point(A, B, two_pi * (double)kx / (double)a.n1, x2, x3, nyq, a.mu0, cc, scale, Ao, Bo);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) { at(c, 0, ky) = Ao[c]; at(c, 1, ky) = Bo[c]; }
+            continue;
+        }
+        // packed column: P = C0 + i CN with C0, CN the transforms of the columns kx = 0 and
+        // kx = n1/2; the thread of ky <= n2/2 unpacks ky and -ky, applies the operator at the
+        // four frequencies (0, +-ky), (n1/2, +-ky) and repacks both entries
+        if (ky > n2 / 2) continue;
+        const int kr = (n2 - ky) & (n2 - 1);
+        const bool self = kr == ky;
+        cpx<double> A0[2][6], AN[2][6], B0[2][6], BN[2][6];   // [0]: ky, [1]: -ky
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            for (int part = 0; part < 2; ++part) {
+                const cpx<double> z = at(c, part, ky), zr = at(c, part, kr);
+                // C0(ky) = (P(ky) + conj P(-ky)) / 2, CN(ky) = (P(ky) - conj P(-ky)) / (2i)
+                const cpx<double> c0 = mk(0.5 * (z.x + zr.x), 0.5 * (z.y - zr.y));
+                const cpx<double> cN = mk(0.5 * (z.y + zr.y), -0.5 * (z.x - zr.x));
+                const cpx<double> c0r = mk(c0.x, -c0.y), cNr = mk(cN.x, -cN.y);   // the -ky entries
+                if (part == 0) { A0[0][c] = c0; AN[0][c] = cN; A0[1][c] = c0r; AN[1][c] = cNr; }
+                else { B0[0][c] = c0; BN[0][c] = cN; B0[1][c] = c0r; BN[1][c] = cNr; }
+            }
+        }
+        cpx<double> A0o[2][6], ANo[2][6], B0o[2][6], BNo[2][6];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const double y2 = sgn == 0 ? x2 : -x2;
+            const int nyq0[3] = {0, 2 * ky == n2, 2 * m == a.nz};
+            const int nyqN[3] = {1, 2 * ky == n2, 2 * m == a.nz};
+            if (m == 0 && ky == 0) {
+                // 3-D zero frequency: the macroscopic strain (x nz, the x3 transform's scale)
+                double E[6] = {0, 0, 0, 0, 0, 0};
+                if (a.stress_control) {
+                    // <tau> = A0(0) / (n1 n2 nz); E = C0^-1 : (Sigma - <tau>)
+                    double S[6];
+                    for (int c = 0; c < 6; ++c)
+                        S[c] = (c == 4 ? a.sigma_bar13 : 0.0) - A0[0][c].x / ((double)a.n * (double)a.nz);
+                    const double nu0 = a.lam0 / (2.0 * (a.lam0 + a.mu0)), trs = S[0] + S[1] + S[2];
+                    for (int c = 0; c < 6; ++c) E[c] = (S[c] - (c < 3 ? nu0 / (1.0 + nu0) * trs : 0.0)) / (2.0 * a.mu0);
+                } else {
+                    E[4] = a.eps_bar13;
+                }
+                for (int c = 0; c < 6; ++c) { A0o[sgn][c] = mk(E[c] * (double)a.nz, 0.0); B0o[sgn][c] = mk(0.0, 0.0); }
+            } else {
+                hl_point(A0[sgn], B0[sgn], 0.0, y2, x3, nyq0, a.mu0, cc, scale, A0o[sgn], B0o[sgn]);
+            }
+            hl_point(AN[sgn], BN[sgn], two_pi * 0.5, y2, x3, nyqN, a.mu0, cc, scale, ANo[sgn], BNo[sgn]);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            // repack: P(ky) = C0(ky) + i CN(ky), P(-ky) = C0(-ky) + i CN(-ky)
+            at(c, 0, ky) = mk(A0o[0][c].x - ANo[0][c].y, A0o[0][c].y + ANo[0][c].x);
+            at(c, 1, ky) = mk(B0o[0][c].x - BNo[0][c].y, B0o[0][c].y + BNo[0][c].x);
+            if (!self) {
+                at(c, 0, kr) = mk(A0o[1][c].x - ANo[1][c].y, A0o[1][c].y + ANo[1][c].x);
+                at(c, 1, kr) = mk(B0o[1][c].x - BNo[1][c].y, B0o[1][c].y + BNo[1][c].x);
+            }
+        }
+    }
+}
+
+// Parseval sums over the 3-D cell of |eps_new - eps|^2 and |eps_new|^2 (Frobenius, off-diagonal
+// components twice; mode weights 1 for k3 = 0 and nz/2, 2 otherwise; / nz), then eps <- eps_new
+__global__ void hl_update_kernel(const double* __restrict__ enew, double* __restrict__ eps, LayerArgs a,
+                                 double* __restrict__ partials) {
+    __shared__ double red[32];
+    double dd = 0.0, ee = 0.0;
+    const size_t total = (size_t)a.M * 12 * a.n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t fidx = i / a.n;
+        const int m = (int)(fidx / 12), c = (int)((fidx % 12) / 2);
+        const double w = ((m == 0 || 2 * m == a.nz) ? 1.0 : 2.0) * (c < 3 ? 1.0 : 2.0);
+        const double v = enew[i], d = v - eps[i];
+        dd += w * d * d;
+        ee += w * v * v;
+        eps[i] = v;
+    }
+    const double r1 = hsum_block(dd, red);
+    const double r2 = hsum_block(ee, red);
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = r1; partials[2 * blockIdx.x + 1] = r2; }
+}
+
+// sigma13 = 2 f mu (eps13 - eps^p13): its layer average (tau) and its value on chosen planes
+__global__ void hl_stress_kernel(StateRef st, const double* __restrict__ f, const double* __restrict__ eps,
+                                 LayerArgs a, double* __restrict__ tau, const int* __restrict__ planes, int nplanes,
+                                 double* __restrict__ out_planes) {
+    const int cur = st.sc->cur;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < a.n; q += (size_t)gridDim.x * blockDim.x) {
+        const double u = state_at<double>((const double*)st.phi0, (const double*)st.phi1, nullptr, nullptr, cur, q);
+        const double g = 2.0 * f[q] * a.mu;
+        double acc = 0.0;
+        for (int m = 0; m < a.M; ++m) {
+            double cr, ci;
+            layer_chi(m, a.nh, a.nz, &cr, &ci);
+            const double sr = g * (eps[hl_field(m, 4, 0) * a.n + q] - 0.5 * cr * u);
+            const double si = g * (eps[hl_field(m, 4, 1) * a.n + q] - 0.5 * ci * u);
+            const double w = (m == 0 || 2 * m == a.nz) ? 1.0 : 2.0;
+            acc += w * (sr * cr + si * ci);   // Re(sigma-hat conj(chi-hat))
+        }
+        tau[q] = acc / ((double)a.nz * (double)a.nh);
+        for (int p = 0; p < nplanes; ++p) {
+            double s = 0.0;
+            for (int m = 0; m < a.M; ++m) {
+                double cr, ci, sn, cs;
+                layer_chi(m, a.nh, a.nz, &cr, &ci);
+                sincospi(2.0 * (double)m * (double)planes[p] / (double)a.nz, &sn, &cs);
+                const double sr = g * (eps[hl_field(m, 4, 0) * a.n + q] - 0.5 * cr * u);
+                const double si = g * (eps[hl_field(m, 4, 1) * a.n + q] - 0.5 * ci * u);
+                const double w = (m == 0 || 2 * m == a.nz) ? 1.0 : 2.0;
+                s += w * (sr * cs - si * sn);   // Re(sigma-hat exp(2 pi i m x3 / nz))
+            }
+            out_planes[(size_t)p * a.n + q] = s / (double)a.nz;
+        }
+    }
+}
+
+}  // namespace
+
+fdm_status hetero_layer_solve(const Dev& d, const double* f_dev, double f0, bool stress_control, double load,
+                              double tol, int max_iter, const int* planes_dev, int nplanes, double* tau_out,
+                              double* planes_out, void* const bufs[3], double* partials, int nblk, cudaStream_t s,
+                              int* iterations, double* residual) {
+    const int n1 = d.p.n1, n2 = d.p.n2, nz = d.p.nz, nh = d.p.nh;
+    const size_t n = (size_t)n1 * n2;
+    LayerArgs a;
+    a.n1 = n1;
+    a.n2 = n2;
+    a.nz = nz;
+    a.nh = nh;
+    a.M = nz / 2 + 1;
+    a.mu = d.p.E / (2.0 * (1.0 + d.p.nu));
+    a.lam = 2.0 * a.mu * d.p.nu / (1.0 - 2.0 * d.p.nu);
+    a.f0 = f0;
+    a.mu0 = f0 * a.mu;
+    a.lam0 = f0 * a.lam;
+    a.stress_control = stress_control ? 1 : 0;
+    a.sigma_bar13 = stress_control ? load : 0.0;
+    a.eps_bar13 = stress_control ? 0.0 : load;
+    a.n = n;
+    const int count = 12 * a.M;
+    double* eps = (double*)bufs[0];
+    double* work = (double*)bufs[1];
+    void* spec = bufs[2];
+    StateRef st{d.phi[0], d.phi[1], nullptr, nullptr, d.sc};
+    // scale of the eigenstrain: rms over the cell of eps^p - <eps^p> (Frobenius), from U13
+    std::vector<double> u(n);
+    fdm_dev_scalars sc;
+    FDM_CK(cudaMemcpyAsync(&sc, d.sc, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    FDM_CK(cudaMemcpyAsync(u.data(), d.phi[sc.cur], n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FDM_CK(cudaStreamSynchronize(s));
+    const double pmean = 0.5 * ((double)nh / (double)nz) * (ksum(u.data(), n) / (double)n);
+    std::vector<double> sq(n);
+    for (size_t q = 0; q < n; ++q) {
+        const double e = 0.5 * u[q] - pmean;
+        sq[q] = (double)nh * e * e + (double)(nz - nh) * pmean * pmean;
+    }
+    const double prms = std::sqrt(2.0 * ksum(sq.data(), n) / ((double)n * (double)nz));
+    const size_t fields = (size_t)count * n;
+    FDM_CK(cudaMemsetAsync(eps, 0, fields * sizeof(double), s));
+    const int eblk = (int)std::min<size_t>((a.M * n + 255) / 256, 152 * 16);
+    const int gblk = (int)std::min<size_t>((a.M * n / 2 + 255) / 256, 152 * 16);
+    std::vector<double> buf;
+    double sums[2];
+    int it = 0;
+    double r = 0.0;
+    fdm_status e;
+    while (it < max_iter) {
+        ++it;
+        hl_polarise_kernel<<<eblk, 256, 0, s>>>(st, f_dev, eps, work, a);
+        launch_fft_forward_many<double>(d, work, spec, count, s);
+        hl_green_kernel<<<gblk, 256, 0, s>>>((cpx<double>*)spec, a);
+        launch_fft_inverse_many<double>(d, spec, work, count, s);
+        hl_update_kernel<<<nblk, 256, 0, s>>>(work, eps, a, partials);
+        FDM_CK(cudaGetLastError());
+        if ((e = host_sum(partials, nblk, s, buf, sums, 2, 2))) return e;
+        const double cells = (double)n * (double)nz;
+        const double scale = std::max(std::sqrt(sums[1] / (double)nz / cells), prms);
+        r = scale > 0.0 ? std::sqrt(sums[0] / (double)nz / cells) / scale : 0.0;
+        if (!std::isfinite(r)) return FDM_ERR_NONFINITE;
+        if (tol > 0.0 && r <= tol) break;
+    }
+    hl_stress_kernel<<<(int)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(st, f_dev, eps, a, tau_out,
+                                                                                     planes_dev, nplanes, planes_out);
+    FDM_CK(cudaGetLastError());
+    *iterations = it;
+    *residual = r;
+    return FDM_OK;
+}
+
 #define FDM_HETERO_INST(T)                                                                                   \
     template fdm_status hetero_solve<T>(const Dev&, const HeteroBuffers&, double, bool, double, double, int, \
                                         cudaStream_t, int*, double*);

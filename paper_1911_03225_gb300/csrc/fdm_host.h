@@ -199,6 +199,15 @@ struct HeteroBuffers {
 template <typename T>
 fdm_status hetero_solve(const Dev& d, const HeteroBuffers& hb, double mu0, bool stress_control, double load,
                         double tol, int max_iter, cudaStream_t s, int* iterations, double* residual);
+// Heterogeneous static problem for a plastic layer thinner than the cell (FP64 group d, the
+// current state): modulus field f_dev (device, n1 n2) uniform through the depth, reference
+// factor f0; bufs: three device arrays of 12 (nz/2 + 1) n1 n2 doubles; partials: nblk x 2
+// doubles.  Writes the layer average of sigma13 to tau_out (device, n1 n2) and sigma13 on the
+// planes planes_dev[nplanes] to planes_out (device, nplanes n1 n2).
+fdm_status hetero_layer_solve(const Dev& d, const double* f_dev, double f0, bool stress_control, double load,
+                              double tol, int max_iter, const int* planes_dev, int nplanes, double* tau_out,
+                              double* planes_out, void* const bufs[3], double* partials, int nblk, cudaStream_t s,
+                              int* iterations, double* residual);
 fdm_status download_field(double* dst, const void* src, size_t n, int prec, double offset, cudaStream_t s);
 // U13 of instance `inst` in state buffer b, from / to host doubles (minus / plus `offset`);
 // FDM_MIXED stores FP32 pairs: hi = fl(v), lo = fl(v - hi)

@@ -87,6 +87,9 @@ template <typename T> void launch_stress_to(const Dev& d, int comp, T* dst, cuda
 // unnormalised 2-D transforms of one real field (packed transposed spectrum of n/2 complex)
 template <typename T> void launch_fft_forward(const Dev& d, const T* src, void* spec, cudaStream_t s);
 template <typename T> void launch_fft_inverse(const Dev& d, void* spec, T* dst, cudaStream_t s);
+// the same for `count` consecutive fields of the group's grid (spectra consecutive too)
+template <typename T> void launch_fft_forward_many(const Dev& d, const T* src, void* spec, int count, cudaStream_t s);
+template <typename T> void launch_fft_inverse_many(const Dev& d, void* spec, T* dst, int count, cudaStream_t s);
 // the step's time step (single instance) from a tau13 already in d.tau: max |v0| and dt
 template <typename T> void launch_celerity_dt(const Dev& d, cudaStream_t s);
 template <typename T> void launch_alpha(const Dev& d, const T* phi, T* a11, T* a12, cudaStream_t s);

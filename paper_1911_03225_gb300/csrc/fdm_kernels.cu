@@ -1199,6 +1199,28 @@ void launch_fft_inverse(const Dev& d, void* spec, T* dst, cudaStream_t s) {
     launch_row_inverse<T>(d, (const cpx<T>*)spec, dst, ROW_PLAIN, 0.0, 1, s);
 }
 
+// 2-D transforms of `count` consecutive real fields of the group's grid (unnormalised): the
+// row and column kernels once each over all fields
+template <typename T>
+void launch_fft_forward_many(const Dev& d, const T* src, void* spec, int count, cudaStream_t s) {
+    Dev q = d;
+    q.sc = nullptr;
+    q.gated = 0;
+    InstCtl none{nullptr, 0};
+    launch_row_forward<T>(q, src, src, (cpx<T>*)spec, nullptr, none, count, s);
+    launch_col<T>(q, (const cpx<T>*)spec, (cpx<T>*)spec, COL_FWD, false, count, s);
+}
+template <typename T>
+void launch_fft_inverse_many(const Dev& d, void* spec, T* dst, int count, cudaStream_t s) {
+    Dev q = d;
+    q.sc = nullptr;
+    q.gated = 0;
+    q.phi[0] = q.phi[1] = nullptr;
+    q.mfac = nullptr;
+    launch_col<T>(q, (const cpx<T>*)spec, (cpx<T>*)spec, COL_INV, false, count, s);
+    launch_row_inverse<T>(q, (const cpx<T>*)spec, dst, ROW_PLAIN, 0.0, count, s);
+}
+
 // the step's dt from d.tau (single instance): see celerity_dt_kernel
 template <typename T>
 void launch_celerity_dt(const Dev& d, cudaStream_t s) {
@@ -1519,7 +1541,9 @@ cudaError_t persist_launch(const void* dev_desc, int ngroups, int nsteps, Persis
     template void launch_alpha_sums<T>(const Dev&, int, double*, int, cudaStream_t);                        \
     template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
                                      cudaStream_t);                                                     \
-    template void launch_twiddle_tables<T>(void*, int, void*, int, cudaStream_t);
+    template void launch_twiddle_tables<T>(void*, int, void*, int, cudaStream_t);                          \
+    template void launch_fft_forward_many<T>(const Dev&, const T*, void*, int, cudaStream_t);              \
+    template void launch_fft_inverse_many<T>(const Dev&, void*, T*, int, cudaStream_t);
 FDM_INST(double)
 FDM_INST(float)
 FDM_INST(df)

@@ -180,3 +180,85 @@ def test_hetero_steps_at_scale_never_increase_the_energy():
             sim.step(10)
     w = np.array(w)
     assert (np.diff(w) < 0).all(), w
+
+
+# ------------------------------------------------------------------ layer thinner than the cell
+def layer_params(n1, n2, nz, nh, stress):
+    common = dict(n1=n1, n2=n2, nz=nz, nh=nh, velocity_mode=B.V_STRESS, precision=B.FP64)
+    if stress:
+        return Params(loading_mode=B.LOAD_STRESS, sigma_bar13=0.02, **common)
+    return Params(loading_mode=B.LOAD_STRAIN_RAMP, eps_bar13_0=1e-3, eps_bar13_rate=1e-4, **common)
+
+
+@pytest.mark.parametrize("stress", [True, False])
+def test_hetero_layer_iterates_match_oracle(stress):
+    """A layer of 3 planes in a cell of 16 (Sec. 3.1.2 heterogeneous medium, Sec. 3.2.1 layer),
+    modulus contrast 4 uniform through the depth, 25 iterations exactly: the GPU iterates the
+    independent x3 modes, the oracle the full 3-D strain field; the layer average of sigma13
+    and sigma13 on planes in, at the edge of and far from the layer agree."""
+    n1, n2, nz, nh = 64, 32, 16, 3
+    up0 = inputs.random_up(64, seed=21, ell=4.0)[:n2, :n1].copy()
+    f = modulus_factor(n2, n1, 22)
+    planes = [0, 1, 2, 3, 8, 15]
+    p = layer_params(n1, n2, nz, nh, stress)
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        tau, got_planes, it, r = sim.static_solve_heterogeneous_layer(f, tol=0.0, max_iter=25, planes=planes)
+        assert sim.info().step == 0
+    load = 0.02 if stress else 1e-3
+    ref, ref_planes, it_o, r_o = oracle.hetero_layer(f, up0, nz, nh, MU, 0.3, stress, load, tol=0.0, max_iter=25,
+                                                     planes=True)
+    assert it == it_o == 25 and r == pytest.approx(r_o, rel=1e-9)
+    assert rel(tau, ref) < 1e-11
+    assert rel(got_planes, ref_planes[planes]) < 1e-11
+
+
+def test_hetero_layer_homogeneous_limit_and_filled_cell():
+    """A uniform modulus gives the layer solve's tau13 (one iteration is exact); a layer filling
+    the cell gives the antiplane solver's sigma13 iterate for iterate."""
+    n1, n2 = 64, 64
+    up0 = inputs.random_up(64, seed=23, ell=5.0)
+    with FDM(layer_params(n1, n2, 32, 4, True)) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.static_solve()
+        ref = sim.read_fields("tau13")["tau13"]
+        tau, _, it, _ = sim.static_solve_heterogeneous_layer(np.ones((n2, n1)), tol=0.0, max_iter=2)
+    assert rel(tau, ref) < 1e-12
+    f = modulus_factor(n2, n1, 24)
+    with FDM(layer_params(n1, n2, 8, 8, True)) as sim:
+        sim.set_plastic_distortion(up0)
+        s13, _, it_a, r_a = sim.static_solve_heterogeneous(f, tol=0.0, max_iter=20)
+        tau, planes, it, r = sim.static_solve_heterogeneous_layer(f, tol=0.0, max_iter=20, planes=[0, 5])
+    assert it == it_a == 20 and r == pytest.approx(r_a, rel=1e-9)
+    assert rel(tau, s13) < 1e-12 and rel(planes[1], s13) < 1e-12
+
+
+def test_hetero_layer_at_scale_converges_symmetric_about_the_layer():
+    """512^2 cell 16 deep, layer of 4 planes, contrast 4: converges to 1e-10; sigma13 is even about
+    the layer's mid-plane (x3 = 1.5), and differs from the homogeneous layer solve."""
+    n, nz, nh = 512, 16, 4
+    up0 = inputs.random_up(n, seed=25, ell=16.0)
+    f = modulus_factor(n, n, 26, ell=12.0)
+    with FDM(layer_params(n, n, nz, nh, True)) as sim:
+        sim.set_plastic_distortion(up0)
+        tau, planes, it, r = sim.static_solve_heterogeneous_layer(f, tol=1e-10, max_iter=300,
+                                                                  planes=[0, 3, 1, 2, 6, 13])
+        sim.static_solve()
+        homog = sim.read_fields("tau13")["tau13"]
+    assert it < 300 and r <= 1e-10
+    scale = np.abs(planes).max()
+    assert np.abs(planes[0] - planes[1]).max() < 1e-9 * scale
+    assert np.abs(planes[2] - planes[3]).max() < 1e-9 * scale
+    assert np.abs(planes[4] - planes[5]).max() < 1e-9 * scale   # x3 = 6 and 13 -> 1.5 +- 4.5
+    assert rel(tau, homog) > 1e-2
+
+
+def test_hetero_layer_rejects_other_precisions_and_odd_depth():
+    n = 32
+    up0 = inputs.random_up(n, seed=27, ell=4.0)
+    for p in (Params(n1=n, n2=n, nz=8, nh=2, precision=B.MIXED), Params(n1=n, n2=n, nz=9, nh=2)):
+        with FDM(p) as sim:
+            sim.set_plastic_distortion(up0)
+            with pytest.raises(FDMError) as e:
+                sim.static_solve_heterogeneous_layer(np.ones((n, n)), max_iter=2)
+            assert e.value.status == B.FDM_ERR_INVALID_ARG
