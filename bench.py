@@ -372,7 +372,8 @@ def run_ours(args, world, rank, local):
                          "mixed": round(cufft_static_solve_ms(n, torch.float32), 5)}}
         # the mixed path's iterates stop improving at FP32 rounding (~1e-7)
         line["hetero_static"] = {"fp64": hetero_static(n, "fp64", tol=1e-12),
-                                 "mixed": hetero_static(n, "mixed", tol=1e-6)}
+                                 "mixed": hetero_static(n, "mixed", tol=1e-6),
+                                 "fp64_thin_layer": hetero_layer_static(512)}
     for rr in results.values():
         rr["sim"].close()
     if args.sub_records:
@@ -646,16 +647,47 @@ def run_serve(args, world, rank, local):
         }), flush=True)
 
 
+def hetero_layer_static(n, nz=16, nh=4, tol=1e-10, contrast=4.0):
+    """Heterogeneous static problem of a plastic layer thinner than the cell (nh of nz planes,
+    moduli scaled by a contrast-4 field uniform through the depth, stress control), FP64: a
+    converged solve and the time of one iteration (difference of two fixed-length solves)."""
+    import torch
+    from paper_1911_03225_gb300 import FDM, inputs
+    from paper_1911_03225_gb300 import binding as B
+    p = B.Params(n1=n, n2=n, nz=nz, nh=nh, velocity_mode=B.V_STRESS, loading_mode=B.LOAD_STRESS, sigma_bar13=0.01)
+    up0 = inputs.random_up(n, seed=0, ell=16.0, rms_alpha=0.1)
+    f = inputs.modulus_factor(n, n, seed=1, lo=1.0 / contrast, hi=1.0, ell=24.0)
+
+    def timed(**kw):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = sim.static_solve_heterogeneous_layer(f, **kw)
+        return (time.perf_counter() - t0) * 1e3, out
+
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        ms, (_, _, it, res) = timed(tol=tol, max_iter=400)
+        t5, _ = timed(tol=0.0, max_iter=5)
+        t15, _ = timed(tol=0.0, max_iter=15)
+    per_it = (t15 - t5) / 10.0
+    fields = 12 * (nz // 2 + 1)
+    return {"n": n, "nz": nz, "nh": nh, "contrast": contrast, "tol": tol, "iterations": it, "residual": res,
+            "ms": round(ms, 3), "ms_per_iteration": round(per_it, 4), "real_2d_fields": fields,
+            "note": "the x3 modes of the depth-uniform medium iterate together: %d real n x n fields, each "
+                    "transformed forward and back per iteration" % fields}
+
+
 def run_hetero(args, world, rank, local):
-    """The heterogeneous static problem alone (shear-modulus contrast 4, layer filling the
-    cell, n x n): a converged solve per precision and the time of one iteration."""
+    """The heterogeneous static problems alone (shear-modulus contrast 4, n x n): a layer filling
+    the cell per precision, and a layer thinner than the cell (FP64)."""
     import torch
     build_once(rank, world)
     torch.cuda.set_device(local)
     if rank == 0:
         out = {"fp64": hetero_static(args.n, "fp64", tol=1e-12), "mixed": hetero_static(args.n, "mixed", tol=1e-6)}
+        layer = hetero_layer_static(min(args.n, 512))
         print(json.dumps({"workload": "heterogeneous static problem, %dx%d, contrast 4, stress control" % (args.n, args.n),
-                          "hetero_static": out}), flush=True)
+                          "hetero_static": out, "hetero_layer_static": layer}), flush=True)
 
 
 def run_reference(args, world, rank):
