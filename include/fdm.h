@@ -293,6 +293,16 @@ fdm_status fdm_read_stress_planes(fdm_handle *h, int32_t comp, int32_t nplanes, 
 fdm_status fdm_set_loading(fdm_handle *h, int32_t mode, double sigma_bar13, double eps_bar13_0,
                            double eps_bar13_rate);
 
+/* The equilibration stage of Sec. 5.1: switches the loading to FDM_LOAD_ZERO_MEAN_STRESS and
+ * steps in chunks of `chunk` steps until a chunk changes U13 by less than tol in relative L2
+ * (||U_after - U_before|| / ||U_before||, reduced on the device in FP64; only two numbers per
+ * chunk leave the device) or max_steps steps are taken.  *taken (nullable) receives the steps
+ * taken, *change (nullable) the last relative change.  The loading stays at zero mean stress.
+ * Errors: FDM_ERR_INVALID_ARG (tol <= 0, chunk < 1, max_steps < 0), FDM_ERR_STATE (no state),
+ * the first device-side error of a chunk. */
+fdm_status fdm_equilibrate(fdm_handle *h, double tol, int32_t chunk, int64_t max_steps, int64_t *taken,
+                           double *change);
+
 /* Heterogeneous drag (Sec. 5.3, Orowan mechanism: precipitates with infinite drag):
  * factor[n2][n1] (host, float64, finite, >= 0) multiplies the celerity of every node,
  * v0(x) = m(x) v0_law(x), i.e. eta(x) = eta~ / m(x); m = 0 inside impenetrable particles,

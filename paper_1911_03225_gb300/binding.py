@@ -50,7 +50,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
            "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field",
            "fdm_measure_arith_rate", "fdm_batch_enqueue_steps_persistent", "fdm_debug_barrier",
-           "fdm_static_solve_heterogeneous_layer"]
+           "fdm_static_solve_heterogeneous_layer", "fdm_equilibrate"]
 
 
 class CParams(C.Structure):
@@ -194,6 +194,9 @@ def load():
                                                          C.POINTER(C.c_int32), d, C.POINTER(C.c_int32),
                                                          C.POINTER(C.c_double)]
     lib.fdm_static_solve_heterogeneous_layer.restype = C.c_int
+    lib.fdm_equilibrate.argtypes = [H, C.c_double, C.c_int32, C.c_int64, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double)]
+    lib.fdm_equilibrate.restype = C.c_int
     lib.fdm_set_shear_modulus_field.argtypes = [H, d, C.c_double, C.c_int32]
     lib.fdm_set_shear_modulus_field.restype = C.c_int
     lib.fdm_debug_fail_allocation.argtypes = [C.c_int32]
@@ -415,24 +418,14 @@ class FDM:
                                         float(eps_bar13_rate)), "fdm_set_loading")
 
     def equilibrate(self, tol: float = 1e-6, chunk: int = 50, max_steps: int = 100000):
-        """Equilibration stage of Sec. 5.1: zero mean stress until the microstructure stops
-        evolving, i.e. until a chunk of steps changes U13 by less than ``tol`` (relative L2)
-        or ``max_steps`` are taken.  Returns (steps taken, last relative change); the loading
+        """Equilibration stage of Sec. 5.1 (``fdm_equilibrate``): zero mean stress until a chunk
+        of steps changes U13 by less than ``tol`` (relative L2, reduced on the device) or
+        ``max_steps`` are taken.  Returns (steps taken, last relative change); the loading
         stays at zero mean stress (switch it with ``set_loading`` for the next stage)."""
-        self.set_loading(LOAD_ZERO_MEAN_STRESS)
-        prev = self.read_fields("up13")["up13"]
-        taken, change = 0, float("inf")
-        while taken < max_steps:
-            k = min(chunk, max_steps - taken)
-            self.enqueue_steps(k)
-            self.sync()
-            taken += k
-            cur = self.read_fields("up13")["up13"]
-            change = float(np.linalg.norm(cur - prev) / max(np.linalg.norm(prev), 1e-300))
-            if change < tol:
-                break
-            prev = cur
-        return taken, change
+        taken, change = C.c_int64(0), C.c_double(0.0)
+        _check(self.lib.fdm_equilibrate(self.h, float(tol), int(chunk), int(max_steps), C.byref(taken),
+                                        C.byref(change)), "fdm_equilibrate")
+        return int(taken.value), float(change.value)
 
     def step(self, nsteps: int = 1, info: bool = True) -> Optional[StepInfo]:
         if info:

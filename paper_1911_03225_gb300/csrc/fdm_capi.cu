@@ -903,6 +903,59 @@ fdm_status fdm_static_solve_heterogeneous_layer(fdm_handle* h, const double* mu_
     return FDM_OK;
 }
 
+fdm_status fdm_equilibrate(fdm_handle* h, double tol, int32_t chunk, int64_t max_steps, int64_t* taken,
+                           double* change) {
+    if (!h || !(tol > 0.0) || !std::isfinite(tol) || chunk < 1 || max_steps < 0) return FDM_ERR_INVALID_ARG;
+    if (!h->has_state) return FDM_ERR_STATE;
+    const fdm_params& p = h->d.p;
+    fdm_status st = fdm_set_loading(h, FDM_LOAD_ZERO_MEAN_STRESS, p.sigma_bar13, p.eps_bar13_0, p.eps_bar13_rate);
+    if (st) return st;
+    const size_t n = h->n;
+    const int nblk = red_blocks_for(n);
+    void* prev = nullptr;
+    void* part = nullptr;
+    if ((st = h->arena.alloc(&prev, n * sizeof(double)))) return st;
+    if ((st = h->arena.alloc(&part, (size_t)2 * nblk * sizeof(double)))) {
+        h->arena.release(prev);
+        return st;
+    }
+    int64_t done = 0;
+    double rel = HUGE_VAL;
+    std::vector<double> buf(2 * (size_t)nblk), col(nblk);
+    FDM_DISPATCH(h->prec, launch_state_change<T>(h->d, (double*)prev, 1, (double*)part, nblk, h->stream));
+    while (st == FDM_OK && done < max_steps) {
+        const int32_t k = (int32_t)std::min<int64_t>(chunk, max_steps - done);
+        if ((st = fdm_enqueue_steps(h, k))) break;
+        FDM_DISPATCH(h->prec, launch_state_change<T>(h->d, (double*)prev, 0, (double*)part, nblk, h->stream));
+        if (cudaMemcpyAsync(buf.data(), part, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            st = FDM_ERR_DEVICE;
+            break;
+        }
+        if ((st = fdm_sync(h))) break;   // device-side errors of the chunk's steps
+        done += k;
+        double sums[2];
+        for (int q = 0; q < 2; ++q) {
+            for (int b = 0; b < nblk; ++b) col[b] = buf[2 * (size_t)b + q];
+            sums[q] = ksum(col.data(), col.size());
+        }
+        rel = std::sqrt(sums[0]) / std::max(std::sqrt(sums[1]), 1e-300);
+        if (!std::isfinite(rel)) {
+            st = FDM_ERR_NONFINITE;
+            break;
+        }
+        if (rel < tol) break;
+    }
+    cudaStreamSynchronize(h->stream);
+    h->arena.release(prev);
+    h->arena.release(part);
+    if (taken) *taken = done;
+    if (change) *change = rel;
+    return st;
+}
+
 fdm_status fdm_read_stress13_planes(fdm_handle* h, int32_t nplanes, const int32_t* planes, double* out) {
     return read_stress_planes(h, FDM_S13, nplanes, planes, out);
 }

@@ -573,4 +573,201 @@ __device__ __forceinline__ f2 knp_node_x2(F f, f2 v0, float dt_h, float theta, i
     return acc;
 }
 
+// ---------------------------------------------------------------------------------
+// Packed double words: two double-word values, one per lane of the packed FP32 instructions.
+// Every operation is the one of fdm_df.cuh (TwoSum, FastTwoSum, FMA TwoProd, the sloppy
+// double-word sum and the double-word product of Joldes, Muller & Popescu), carried out on
+// both lanes by one instruction, each lane rounded as the scalar operation is, so a lane's
+// result equals the scalar double-word result bit for bit.
+// ---------------------------------------------------------------------------------
+struct df2 { f2 hi, lo; };
+__device__ __forceinline__ df lane(const df2& v, int i) { return i == 0 ? df(v.hi.x, v.lo.x) : df(v.hi.y, v.lo.y); }
+__device__ __forceinline__ df2 mkdf2(df a, df b) { df2 r; r.hi = mkf2(a.hi, b.hi); r.lo = mkf2(a.lo, b.lo); return r; }
+__device__ __forceinline__ df2 bcast2(df a) { return mkdf2(a, a); }
+__device__ __forceinline__ void two_sum2(f2 a, f2 b, f2& s, f2& e) {
+    s = a + b;
+    const f2 bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum2(f2 a, f2 b, f2& s, f2& e) {   // |a| >= |b|
+    s = a + b;
+    e = b - (s - a);
+}
+__device__ __forceinline__ df2 operator+(df2 x, df2 y) {
+    f2 sh, sl, zh, zl;
+    two_sum2(x.hi, y.hi, sh, sl);
+    const f2 v = x.lo + y.lo;
+    const f2 w = sl + v;
+    fast_two_sum2(sh, w, zh, zl);
+    df2 r;
+    r.hi = zh;
+    r.lo = zl;
+    return r;
+}
+__device__ __forceinline__ df2 operator-(df2 x) { df2 r; r.hi = -x.hi; r.lo = -x.lo; return r; }
+__device__ __forceinline__ df2 operator-(df2 x, df2 y) { return x + (-y); }
+__device__ __forceinline__ df2 operator*(df2 x, df2 y) {
+    const f2 ch = x.hi * y.hi;
+    const f2 cl1 = fma2(x.hi, y.hi, -ch);
+    const f2 tl0 = x.lo * y.lo;
+    const f2 tl1 = fma2(x.hi, y.lo, tl0);
+    const f2 cl2 = fma2(x.lo, y.hi, tl1);
+    const f2 cl3 = cl1 + cl2;
+    df2 r;
+    fast_two_sum2(ch, cl3, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df2 mul_f2(df2 x, f2 y) {
+    const f2 ch = x.hi * y;
+    const f2 cl1 = fma2(x.hi, y, -ch);
+    const f2 cl3 = fma2(x.lo, y, cl1);
+    df2 r;
+    fast_two_sum2(ch, cl3, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df2 scale2x(df2 x, float p2) { df2 r; r.hi = x.hi * bcast(p2); r.lo = x.lo * bcast(p2); return r; }
+__device__ __forceinline__ df2 thalf(df2 x) { return scale2x(x, 0.5f); }
+// reciprocal and reciprocal square root: the float seeds per lane, the Newton step packed
+__device__ __forceinline__ df2 trcp(df2 y) {
+    const f2 r0 = mkf2(rcp_seed(y.hi.x), rcp_seed(y.hi.y));
+    const df2 p = mul_f2(y, r0);
+    const f2 e = (bcast(1.0f) - p.hi) - p.lo;
+    df2 r;
+    two_sum2(r0, r0 * e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df2 trsqrt(df2 x) {
+    const f2 r0 = mkf2(rsqrt_seed(x.hi.x), rsqrt_seed(x.hi.y));
+    const f2 q = r0 * r0;
+    const f2 qe = fma2(r0, r0, -q);
+    df2 qq;
+    qq.hi = q;
+    qq.lo = qe;
+    const df2 h = x * qq;
+    const f2 e = (bcast(1.0f) - h.hi) - h.lo;
+    df2 r;
+    two_sum2(r0, (bcast(0.5f) * r0) * e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df2 sel2(bool ca, bool cb, df2 a, df2 b) {
+    df2 r;
+    r.hi = sel2(ca, cb, a.hi, b.hi);
+    r.lo = sel2(ca, cb, a.lo, b.lo);
+    return r;
+}
+__device__ __forceinline__ df2 minmod3(df2 a, df2 b, df2 c) {
+    return mkdf2(minmod3(lane(a, 0), lane(b, 0), lane(c, 0)), minmod3(lane(a, 1), lane(b, 1), lane(c, 1)));
+}
+__device__ __forceinline__ df2 theta_mul(df2 x, df theta, int theta_code) {
+    if (theta_code == 1) return x;
+    if (theta_code == 2) return scale2x(x, 2.0f);
+    return bcast2(theta) * x;
+}
+__device__ __forceinline__ void speed_range(df2 h, df2& ap, df2& am) {
+    df a0 = lane(ap, 0), a1 = lane(ap, 1), m0 = lane(am, 0), m1 = lane(am, 1);
+    speed_range(lane(h, 0), a0, m0);
+    speed_range(lane(h, 1), a1, m1);
+    ap = mkdf2(a0, a1);
+    am = mkdf2(m0, m1);
+}
+
+// knp_node for two nodes of double-word fields at once (one per lane): the same operations
+// in the same order as knp_node<df>, so each lane is that function's result bit for bit;
+// per-lane decisions (limiter, speeds, guards) become selects.
+template <typename F>
+__device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int theta_code, int time_level) {
+    const df2 f0 = f(0, 0);
+    const df2 dxm3 = f(-1, 0) - f(-2, 0), dxm1 = f0 - f(-1, 0), dxp1 = f(1, 0) - f0, dxp3 = f(2, 0) - f(1, 0);
+    const df2 dym3 = f(0, -1) - f(0, -2), dym1 = f0 - f(0, -1), dyp1 = f(0, 1) - f0, dyp3 = f(0, 2) - f(0, 1);
+    df2 xD[2], xS[2], yD[2], yS[2];   // [0] = + side, [1] = - side
+    {
+        const df2 c = theta_mul(dxp1 - dxm1, theta, theta_code);
+        xD[0] = dxp1; xS[0] = minmod3(theta_mul(dxp3 - dxp1, theta, theta_code), thalf(dxp3 - dxm1), c);
+        xD[1] = dxm1; xS[1] = minmod3(c, thalf(dxp1 - dxm3), theta_mul(dxm1 - dxm3, theta, theta_code));
+    }
+    {
+        const df2 c = theta_mul(dyp1 - dym1, theta, theta_code);
+        yD[0] = dyp1; yS[0] = minmod3(theta_mul(dyp3 - dyp1, theta, theta_code), thalf(dyp3 - dym1), c);
+        yD[1] = dym1; yS[1] = minmod3(c, thalf(dyp1 - dym3), theta_mul(dym1 - dym3, theta, theta_code));
+    }
+    const df2 px[2] = {xD[0] - thalf(xS[0]), xD[1] + thalf(xS[1])};
+    const df2 qy[2] = {yD[0] - thalf(yS[0]), yD[1] + thalf(yS[1])};
+    bool tq[2], tp[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        tq[i] = tmag_less(lane(qy[1], i), lane(qy[0], i));
+        tp[i] = tmag_less(lane(px[1], i), lane(px[0], i));
+    }
+    const df2 qm = sel2(tq[0], tq[1], qy[1], qy[0]), qo = sel2(tq[0], tq[1], qy[0], qy[1]);
+    const df2 pm = sel2(tp[0], tp[1], px[1], px[0]);
+    const df2 zero = bcast2(df(0.0f)), half = bcast2(df(0.5f)), one = bcast2(df(1.0f));
+    auto inv_norm = [&](df2 p, df2 q) -> df2 {   // v0 / |(p, q)|, 0 at the origin
+        const df2 r2 = p * p + q * q;
+        return sel2(tguard(lane(r2, 0)), tguard(lane(r2, 1)), v0 * trsqrt(r2), zero);
+    };
+    const df2 r0 = inv_norm(px[0], qm), r1 = inv_norm(px[1], qm), rc = inv_norm(pm, qo);
+    df2 ap = zero, am = zero, bp = zero, bm = zero;
+    speed_range(r0 * px[0], ap, am);
+    speed_range(r1 * px[1], ap, am);
+    speed_range(sel2(tp[0], tp[1], r1, r0) * qm, bp, bm);
+    speed_range(rc * qo, bp, bm);
+    df2 dxw = ap - am, dyw = bp - bm;
+    const bool gx0 = tguard(lane(dxw, 0)), gx1 = tguard(lane(dxw, 1));
+    const bool gy0 = tguard(lane(dyw, 0)), gy1 = tguard(lane(dyw, 1));
+    df2 nx[2] = {sel2(gx0, gx1, -am, half), sel2(gx0, gx1, ap, half)};
+    df2 ny[2] = {sel2(gy0, gy1, -bm, half), sel2(gy0, gy1, bp, half)};
+    dxw = sel2(gx0, gx1, dxw, one);
+    dyw = sel2(gy0, gy1, dyw, one);
+    const df2 ix = trcp(dxw), iy = trcp(dyw);
+    nx[0] = nx[0] * ix; nx[1] = nx[1] * ix;
+    ny[0] = ny[0] * iy; ny[1] = ny[1] * iy;
+    const df2 dth = bcast2(dt_h);
+    const df2 vdt = v0 * dth;
+    const df2 hvdt = thalf(vdt);
+    df2 Y[2], dY[2], ey[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        ey[t] = (t == 0 ? bp : bm) * dth;
+        const df2 sgn = bcast2(df((t == 0) ? -1.0f : 1.0f));
+        Y[t] = yD[t] * ey[t] + thalf(yS[t] * ey[t] * (ey[t] + sgn));
+        dY[t] = yD[t] + yS[t] * (ey[t] + thalf(sgn));
+    }
+    df2 acc = zero;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int cx = (s == 0) ? 1 : -1;
+        const df2 ex = (s == 0 ? ap : am) * dth;
+        const df2 Dx = xD[s], Sx = xS[s];
+        const df2 sgn = bcast2(df((s == 0) ? -1.0f : 1.0f));
+        const df2 X = Dx * ex + thalf(Sx * ex * (ex + sgn));
+        const df2 dX = Dx + Sx * (ex + thalf(sgn));
+        const df2 fx = f(cx, 0);
+        df2 accs = zero;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int cy = (t == 0) ? 1 : -1;
+            const df2 mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
+            const df2 cross = (cx * cy > 0) ? mixed : -mixed;
+            const df2 val = f0 + X + Y[t] + cross * ex * ey[t];
+            df2 p = dX + cross * ey[t];
+            df2 q = dY[t] + cross * ex;
+            if (time_level == 0) {
+                const df2 r2 = p * p + q * q;
+                const bool g0 = tguard(lane(r2, 0)), g1 = tguard(lane(r2, 1));
+                const df2 w = hvdt * trsqrt(r2);
+                const df2 np = p - w * (Sx * p + cross * q);
+                const df2 nq = q - w * (cross * p + yS[t] * q);
+                p = sel2(g0, g1, np, p);
+                q = sel2(g0, g1, nq, q);
+            }
+            const df2 s2 = p * p + q * q;
+            const df2 g = sel2(tguard(lane(s2, 0)), tguard(lane(s2, 1)), s2 * trsqrt(s2), zero);
+            const df2 psi = val - vdt * g;
+            accs = accs + ny[t] * psi;
+        }
+        acc = acc + nx[s] * accs;
+    }
+    return acc * one;
+}
+
 }  // namespace fdm

@@ -103,6 +103,10 @@ template <typename T>
 void launch_velocity(const Dev& d, const T* a11, const T* a12, const T* tau, const T* phi, T* v1, T* v2,
                      cudaStream_t s);
 void launch_pair_to_double(const float* hi, const float* lo, double* out, size_t n, cudaStream_t s);
+// U13 of the current state (FP64) against prev[n]: partials[2 nblk] = per block sum of
+// (U - prev)^2 and of prev^2, then prev <- U; first = 1 only copies
+template <typename T>
+void launch_state_change(const Dev& d, double* prev, int first, double* partials, int nblk, cudaStream_t s);
 // twiddles exp(-2 pi i m / n) into tw (cpx<T> [n]) and the pass tables of an L-point
 // transform into pt (cpx<T> [pass_table_len(L)]); either may be null
 template <typename T> void launch_twiddle_tables(void* tw, int n, void* pt, int L, cudaStream_t s);

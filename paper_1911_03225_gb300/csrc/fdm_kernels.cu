@@ -598,9 +598,9 @@ template <> struct KnpShapes<double> {
     static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 4},
                          minb[kKnpShapes] = {2, 2, 1, 2};
 };
-template <> struct KnpShapes<df> {
-    static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 2},
-                         minb[kKnpShapes] = {3, 3, 1, 2};
+template <> struct KnpShapes<df> {   // nodes are updated two at a time (packed FP32 pairs)
+    static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 4, 2, 2},
+                         minb[kKnpShapes] = {2, 2, 1, 1};
 };
 
 // grid (n1 / tx, n2 / (ty npt), instances); block (tx, ty); thread (i, j) updates the
@@ -720,6 +720,25 @@ __device__ __forceinline__ void knp_step_body(const T* phi0, const T* phi1, cons
                 out[(size_t)yb * n1 + x] = hi;
                 lo_out[(size_t)yb * n1 + x] = lo;
             }
+        }
+    } else if constexpr (std::is_same<T, df>::value) {
+        // two nodes per pass in the lanes of the packed FP32 instructions (double words), an
+        // odd last node paired with itself and written once
+#pragma unroll 1
+        for (int k = 0; k < npt; k += 2) {
+            const int k2 = (k + 1 < npt) ? k + 1 : k;
+            const int ya = by + ty_ + k * TY, yb = by + ty_ + k2 * TY;
+            const int la = ty_ + k * TY + 2, lb = ty_ + k2 * TY + 2;
+            T va = celerity(a.vel, s_tau[la - 2][tx_], tile[la][lx], phi_ref);
+            T vb = celerity(a.vel, s_tau[lb - 2][tx_], tile[lb][lx], phi_ref);
+            if (a.vel.mfac) {
+                va = va * a.vel.mfac[inst * nn + (size_t)ya * n1 + x];
+                vb = vb * a.vel.mfac[inst * nn + (size_t)yb * n1 + x];
+            }
+            auto f = [&](int i, int j) -> df2 { return mkdf2(tile[la + j][lx + i], tile[lb + j][lx + i]); };
+            const df2 res = knp_node_df2(f, mkdf2(va, vb), dt, a.theta, a.theta_code, a.time_level);
+            out[(size_t)ya * n1 + x] = lane(res, 0);
+            if (k2 != k) out[(size_t)yb * n1 + x] = lane(res, 1);
         }
     } else {
 #pragma unroll 1
@@ -932,6 +951,38 @@ __global__ void alpha_sums_kernel(const T* __restrict__ phi0, const T* __restric
         double r = block_sum(s[q], red);
         if (threadIdx.x == 0) partials[6 * blockIdx.x + q] = r;
     }
+}
+
+// U13 of the current state as FP64 against a stored copy: per block sum (U - prev)^2 and
+// sum prev^2, then prev <- U (first = 1: only the copy, partial sums zero)
+template <typename T>
+__global__ void state_change_kernel(const T* __restrict__ phi0, const T* __restrict__ phi1, const T* __restrict__ lo0,
+                                    const T* __restrict__ lo1, const fdm_dev_scalars* __restrict__ sc, size_t n,
+                                    double* __restrict__ prev, int first, double* __restrict__ partials) {
+    __shared__ double red[32];
+    const int cur = sc->cur;
+    const double ref = sc->phi_ref;
+    const T* phi = cur ? phi1 : phi0;
+    const T* lo = cur ? lo1 : lo0;
+    double dd = 0.0, pp = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double u = (lo ? (double)phi[i] + (double)lo[i] : (double)phi[i]) + ref;
+        if (!first) {
+            const double p = prev[i], d = u - p;
+            dd += d * d;
+            pp += p * p;
+        }
+        prev[i] = u;
+    }
+    const double r1 = block_sum(dd, red);
+    const double r2 = block_sum(pp, red);
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = r1; partials[2 * blockIdx.x + 1] = r2; }
+}
+template <typename T>
+void launch_state_change(const Dev& d, double* prev, int first, double* partials, int nblk, cudaStream_t s) {
+    state_change_kernel<T><<<nblk, 256, 0, s>>>((const T*)d.phi[0], (const T*)d.phi[1], (const T*)d.phi_lo[0],
+                                               (const T*)d.phi_lo[1], d.sc, (size_t)d.p.n1 * d.p.n2, prev, first,
+                                               partials);
 }
 
 // velocity readout V = v0 (alpha12, -alpha11)/|alpha| (Sec. 4.1)
@@ -1542,6 +1593,7 @@ cudaError_t persist_launch(const void* dev_desc, int ngroups, int nsteps, Persis
     template void launch_velocity<T>(const Dev&, const T*, const T*, const T*, const T*, T*, T*,            \
                                      cudaStream_t);                                                     \
     template void launch_twiddle_tables<T>(void*, int, void*, int, cudaStream_t);                          \
+    template void launch_state_change<T>(const Dev&, double*, int, double*, int, cudaStream_t);                          \
     template void launch_fft_forward_many<T>(const Dev&, const T*, void*, int, cudaStream_t);              \
     template void launch_fft_inverse_many<T>(const Dev&, void*, T*, int, cudaStream_t);
 FDM_INST(double)

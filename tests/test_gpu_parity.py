@@ -420,17 +420,34 @@ def test_lattice_friction_at_the_paper_parameters():
         assert abs(i.sum_a11_pos + i.sum_a11_neg) < 1e-9 * i.sum_abs_alpha
 
 
-def test_equilibration_driver_stops_when_the_field_settles():
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED])
+def test_equilibration_driver_stops_when_the_field_settles(precision):
+    """The zero-mean-stress stage (Sec. 5.1) run by the library in chunks, its stopping test
+    reduced on the device, stops where a host-side loop over the same chunks (reading the
+    field back after each) stops, with the same relative change."""
     n = 64
     up0 = inputs.random_up(n, seed=13, ell=6.0, rms_alpha=0.1)
     p = Params(n1=n, n2=n, velocity_mode=B.V_STRESS, tau_y=0.05, beta=0.05, loading_mode=B.LOAD_STRESS,
-               sigma_bar13=0.3, cfl=0.4, theta=1.0)
+               sigma_bar13=0.3, cfl=0.4, theta=1.0, precision=precision)
     with FDM(p) as sim:
         sim.set_plastic_distortion(up0)
         taken, change = sim.equilibrate(tol=1e-4, chunk=20, max_steps=4000)
         info = sim.info()
     assert taken < 4000 and change < 1e-4
     assert info.sigma_bar13 == 0.0 and info.step == taken
+    with FDM(p) as sim:
+        sim.set_plastic_distortion(up0)
+        sim.set_loading(B.LOAD_ZERO_MEAN_STRESS)
+        prev, k, ch = sim.read_fields("up13")["up13"], 0, np.inf
+        while k < 4000:
+            sim.step(20, info=False)
+            k += 20
+            cur = sim.read_fields("up13")["up13"]
+            ch = np.linalg.norm(cur - prev) / np.linalg.norm(prev)
+            if ch < 1e-4:
+                break
+            prev = cur
+    assert k == taken and ch == pytest.approx(change, rel=1e-9)
 
 
 def test_mobility_field_cleared_and_uniform_factor_rescales_time():
