@@ -168,12 +168,14 @@ fdm_status fdm_batch_enqueue_steps(fdm_batch* b, int32_t nsteps) {
     return replay_steps(b->graphs, nsteps, b->stream);
 }
 
-// FDM_ERR_TIMEOUT if a persistent launch of the batch gave up at a barrier (waits)
+// FDM_ERR_TIMEOUT if the last persistent launch of the batch gave up at a barrier (waits);
+// the status is reported once
 static fdm_status persist_status(fdm_batch* b) {
     if (!b->persist_used) return FDM_OK;
     int st = 0;
     FDM_CK(cudaMemcpyAsync(&st, &b->persist_bar->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     FDM_CK(cudaStreamSynchronize(b->stream));
+    b->persist_used = false;
     return (fdm_status)st;
 }
 
