@@ -282,3 +282,26 @@ def test_persistent_launch_barrier_wait_is_bounded():
         b.enqueue_steps(5)
         b.sync()
         np.testing.assert_array_equal(got, b.read_fields(0, "up13")["up13"])
+
+
+def test_persistent_launch_refuses_other_precisions_and_narrow_grids():
+    """The persistent trial runs mixed-precision groups of at least 32 columns; anything else
+    is refused before any launch, and the batch still steps through the graphs."""
+    up = inputs.random_up(64, seed=60, ell=6.0)
+    for params in ([coupled(64, B.FP64)], [coupled(64, B.MIXED), coupled(64, B.DF64)]):
+        with Batch(params) as b:
+            for i in range(len(params)):
+                b.set_plastic_distortion(i, up)
+                b.set_budget(i, 3)
+            with pytest.raises(B.FDMError) as e:
+                b.enqueue_steps_persistent(3)
+            assert e.value.status == B.FDM_ERR_INVALID_ARG
+            b.enqueue_steps(3)
+            assert (b.sync() == 0).all()
+    narrow = Params(**{**coupled(16, B.MIXED).__dict__, "n1": 16, "n2": 64})
+    with Batch([narrow]) as b:
+        b.set_plastic_distortion(0, inputs.random_up(64, seed=61, ell=6.0)[:, :16].copy())
+        b.set_budget(0, 2)
+        with pytest.raises(B.FDMError) as e:
+            b.enqueue_steps_persistent(2)
+        assert e.value.status == B.FDM_ERR_INVALID_ARG

@@ -112,3 +112,13 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     with pytest.raises(B.FDMError) as e:
         B.static_solve_noalloc(Params(n1=64, n2=64, precision=B.MIXED), 0.0, d.data_ptr(), o.data_ptr())
     assert e.value.status == B.FDM_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_unaligned_arrays():
+    """Both arrays must start on a 16-byte boundary (the transforms move complex doubles)."""
+    import torch
+    p = Params(n1=64, n2=64)
+    d = torch.zeros(3 * 64 * 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.FDMError) as e:
+        B.static_solve_noalloc(p, 0.0, d[1:].data_ptr(), d[64 * 64 + 2:].data_ptr())
+    assert e.value.status == B.FDM_ERR_INVALID_ARG
