@@ -116,7 +116,10 @@ __host__ __device__ __forceinline__ void pass_table_entry(int L, int i, int* num
 //   a[(j - k) R + k + r Ns] = v_r.
 // Each thread keeps its butterflies' values in registers between the read and the write of a
 // pass (a barrier in between), so one shared buffer suffices and twice as many blocks fit
-// on an SM as with a ping-pong pair.  Unnormalised; sign -1 forward, +1 inverse.
+// on an SM as with a ping-pong pair (the FP64 transforms).  The FP32 transforms, whose
+// blocks are limited by registers before shared memory, pass between two buffers instead
+// (smem_fft_pp: one barrier per pass, the same arithmetic).  Unnormalised; sign -1
+// forward, +1 inverse.
 // Requires blockDim.x * 8 >= nseq * L: a thread owns at most one radix-8 butterfly per pass
 // (two radix-4 or four radix-2 butterflies in the last pass).  Element i of sequence s at
 // a[s * ld + swz(i)].  pt: the pass twiddle tables (pass_table_len(L) entries).  Must be
@@ -155,6 +158,54 @@ __device__ __forceinline__ void stockham_pass_ip(cpx<T>* a, int L, int nseq, int
     __syncthreads();
 }
 
+// One Stockham pass from src to a second buffer dst (the same layout): with the read and the
+// write in different buffers the pass needs one barrier instead of two.
+template <typename T, int R, int PER, int S>
+__device__ __forceinline__ void stockham_pass_pp(const cpx<T>* src, cpx<T>* dst, int L, int nseq, int ld, int Ns,
+                                                 const cpx<T>* __restrict__ ptw) {
+    const int q = L / R;
+    const int lq = 31 - __clz(q);
+    const int items = nseq * q;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int it = threadIdx.x + u * blockDim.x;
+        if (it >= items) continue;
+        const int s = it >> lq, j = it & (q - 1);
+        const int k = j & (Ns - 1);
+        const int base = s * ld, d = (j - k) * R + k;
+        cpx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[base + swz(j + r * q)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<S>(ptw, (r - 1) * Ns + k));
+        }
+        Dft<T, R>::template run<S>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[base + swz(d + r * Ns)] = v[r];
+    }
+    __syncthreads();
+}
+
+// The transform through two buffers a and b (each nseq sequences of stride ld), starting in a;
+// returns the buffer that holds the result.  Same arithmetic as smem_fft_ip.
+template <int S, typename T>
+__device__ cpx<T>* smem_fft_pp(cpx<T>* a, cpx<T>* b, int L, int nseq, int ld, const cpx<T>* __restrict__ pt) {
+    int Ns = 1;
+    cpx<T>* src = a;
+    cpx<T>* dst = b;
+    while (pass_radix(L, Ns) == 8) {
+        stockham_pass_pp<T, 8, 1, S>(src, dst, L, nseq, ld, Ns, pt);
+        pt += 7 * Ns;
+        Ns *= 8;
+        cpx<T>* t = src; src = dst; dst = t;
+    }
+    const int R = pass_radix(L, Ns);
+    if (R == 4) { stockham_pass_pp<T, 4, 2, S>(src, dst, L, nseq, ld, Ns, pt); return dst; }
+    if (R == 2) { stockham_pass_pp<T, 2, 4, S>(src, dst, L, nseq, ld, Ns, pt); return dst; }
+    return src;
+}
+
 template <int S, typename T>
 __device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, const cpx<T>* __restrict__ pt) {
     int Ns = 1;
@@ -173,6 +224,11 @@ __device__ void smem_fft_ip(cpx<T>* a, int L, int nseq, int ld, const cpx<T>* __
 // P_k = X_k (1 <= k < n/2), from / to the n/2-point complex FFT of z_m = x_2m + i x_2m+1.
 // Z, P: one padded sequence each (L = n/2 entries).  W^k = exp(-2 pi i k / n) = tw_n[k].
 // ---------------------------------------------------------------------------------
+// exact halves (the FP64 ones on the integer pipe, defined below)
+__device__ __forceinline__ float thalf(float x);
+__device__ __forceinline__ double thalf(double x);
+template <typename T> __device__ __forceinline__ cpx<T> chalf(cpx<T> a) { return mk(thalf(a.x), thalf(a.y)); }
+
 template <typename T>
 __device__ __forceinline__ void r2c_twist_pair(const cpx<T>* Z, cpx<T>* P, int L, int k,
                                                const cpx<T>* __restrict__ tw_n) {
@@ -182,8 +238,8 @@ __device__ __forceinline__ void r2c_twist_pair(const cpx<T>* Z, cpx<T>* P, int L
         return;
     }
     cpx<T> A = Z[swz(k)], B = conj(Z[swz(L - k)]);
-    cpx<T> E = scale(A + B, T(0.5));
-    cpx<T> D = scale(A - B, T(0.5));
+    cpx<T> E = chalf(A + B);
+    cpx<T> D = chalf(A - B);
     cpx<T> O = mk(D.y, -D.x);          // -i (A - B) / 2
     cpx<T> WO = cmul(tw_n[k], O);
     P[swz(k)] = E + WO;
@@ -225,14 +281,15 @@ __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
 // x / 2 (exact)
 __device__ __forceinline__ float thalf(float x) { return 0.5f * x; }
-__device__ __forceinline__ double thalf(double x) { return 0.5 * x; }
+__device__ __forceinline__ double thalf(double x);
 // x > 0 (false for zero and NaN)
 template <typename T> __device__ __forceinline__ bool tpos(T x) { return x > T(0); }
 
 // ---------------------------------------------------------------------------------
-// Decisions on doubles made on their bit patterns.  GB300's FP64 pipe retires 2 lanes per
-// SM per clock against 64 for the integer pipe, and comparisons, min/max and sign tests
-// occupy it like an FMA, so the FP64 path takes them on integers.  With the sign bit
+// Decisions on doubles, and their exact scalings by 2, made on their bit patterns.  GB300's
+// FP64 pipe retires 2 lanes per SM per clock against 64 for the integer pipe, and
+// comparisons, min/max, sign tests and multiplications by 1/2 or 2 occupy it like an FMA,
+// so the FP64 path takes them on integers (bit for bit the same results).  With the sign bit
 // cleared, the bits of a double order like its magnitude (NaN above infinity).
 // ---------------------------------------------------------------------------------
 constexpr unsigned long long kMagBits = 0x7fffffffffffffffull, kInfBits = 0x7ff0000000000000ull;
@@ -240,6 +297,30 @@ __device__ __forceinline__ unsigned long long ubits(double x) { return (unsigned
 // nonzero magnitude up to infinity: x is neither +-0 nor NaN
 __device__ __forceinline__ bool mag_ok(unsigned long long m) { return m - 1ull < kInfBits; }
 __device__ __forceinline__ bool tpos(double x) { return mag_ok(ubits(x)); }   // bits in [1, +inf]
+
+// x / 2 exactly, on the integer pipe: one less in the exponent field for normal x above the
+// least normal exponent; zero, subnormals and the least normal exponent halve their
+// magnitude bits (ties to even, as the rounded product); infinities and NaN unchanged
+__device__ __forceinline__ double thalf(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (__builtin_expect(e - 2u < 0x7fdu, 1)) return __hiloint2double(hi - 0x100000, lo);
+    if (e == 0x7ffu) return x;
+    const unsigned long long u = ubits(x), m = u & kMagBits;
+    return __longlong_as_double((long long)((u & ~kMagBits) | ((m >> 1) + (m & (m >> 1) & 1ull))));
+}
+// 2 x exactly, on the integer pipe: one more in the exponent field for normal x below the
+// largest exponent; zero and subnormals double their magnitude bits (exact, and carries
+// into the exponent field where the result is normal); the largest exponent (overflow to
+// infinity), infinities and NaN through the rounded sum
+__device__ __forceinline__ double ttwice(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (__builtin_expect(e - 1u < 0x7fdu, 1)) return __hiloint2double(hi + 0x100000, lo);
+    if (e != 0u) return x + x;
+    const unsigned long long u = ubits(x);
+    return __longlong_as_double((long long)((u & ~kMagBits) | ((u & kMagBits) << 1)));
+}
 
 // ---------------------------------------------------------------------------------
 // Kurganov-Noelle-Petrova update of one node (Sec. 3.2.3 Steps 1-4; readings G1-G7).
@@ -300,6 +381,7 @@ struct Side {  // one-dimensional limited quadratic on the cell on one side of t
 __device__ __forceinline__ float theta_mul(float x, float theta, int) { return theta * x; }
 __device__ __forceinline__ double theta_mul(double x, double theta, int theta_code) {
     if (theta_code == 1) return x;
+    if (theta_code == 2) return ttwice(x);
     return theta * x;
 }
 __device__ __forceinline__ df theta_mul(df x, df theta, int theta_code) {

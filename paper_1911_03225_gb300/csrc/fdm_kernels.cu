@@ -112,6 +112,20 @@ template <> struct FftBounds<float> { static constexpr int threads = 512, minb =
 template <typename T> __host__ __device__ __forceinline__ size_t staged_twiddle_bytes(int L) {
     return std::is_same<T, float>::value ? (size_t)pass_table_len(L) * sizeof(cpx<T>) : 0;
 }
+// The FP32 transforms pass between two shared buffers (one barrier per pass); the others
+// transform in place in one.  Buffers of the block's sequences: nbuf<T>() x nseq x ld.
+template <typename T> __host__ __device__ constexpr int fft_buffers() { return std::is_same<T, float>::value ? 2 : 1; }
+// the transform of the block's sequences in A (and the second buffer B for FP32); returns the
+// buffer holding the result
+template <int S, typename T>
+__device__ __forceinline__ cpx<T>* block_fft(cpx<T>* A, cpx<T>* B, int L, int nseq, int ld, const cpx<T>* ptw) {
+    if constexpr (fft_buffers<T>() == 2) {
+        return smem_fft_pp<S>(A, B, L, nseq, ld, ptw);
+    } else {
+        smem_fft_ip<S>(A, L, nseq, ld, ptw);
+        return A;
+    }
+}
 template <typename T>
 __device__ __forceinline__ const cpx<T>* stage_twiddles(const cpx<T>* pt, cpx<T>* slot, int L) {
     if constexpr (std::is_same<T, float>::value) {
@@ -145,7 +159,8 @@ __device__ __forceinline__ void row_forward_body(const T* src0, const T* src1, c
     const int L = n1 >> 1;
     const int ld = padded_len(L);  // padded sequence stride (bank spread for the transposed store)
     cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);  // R * ld elements
-    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + R * ld, L);
+    cpx<T>* B = A + R * ld;   // second buffer (FP32)
+    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + fft_buffers<T>() * R * ld, L);
     const int y0 = tile * R;
     const int lL = 31 - __clz(L), lR = 31 - __clz(R);  // powers of two
     const cpx<T>* src2 = reinterpret_cast<const cpx<T>*>(src) + (size_t)y0 * L;  // rows are contiguous
@@ -171,16 +186,19 @@ __device__ __forceinline__ void row_forward_body(const T* src0, const T* src1, c
             if (lane == 0) row_partials[y0 + r] = rs;
         }
     }
-    smem_fft_ip<-1>(A, L, R, ld, ptw);
-    const int half = L / 2 + 1;
-    for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
-        int r = e / half, k = e - r * half;  // half = L/2 + 1 is not a power of two
-        r2c_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
+    cpx<T>* F = block_fft<-1>(A, B, L, R, ld, ptw);
+    // in place: a thread owns the pair (k, L - k), k < L/2, of one row; the cheap k = 0 item
+    // also takes the middle k = L/2 (L >= 8)
+    const int hq = L >> 1;
+    for (int e = threadIdx.x; e < R * hq; e += blockDim.x) {
+        const int r = e >> (lL - 1), k = e & (hq - 1);
+        r2c_twist_pair(F + r * ld, F + r * ld, L, k, tw1);
+        if (k == 0) r2c_twist_pair(F + r * ld, F + r * ld, L, hq, tw1);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < R * L; e += blockDim.x) {
         int kx = e >> lR, r = e & (R - 1);
-        spec[(size_t)kx * n2 + y0 + r] = A[r * ld + swz(kx)];
+        spec[(size_t)kx * n2 + y0 + r] = F[r * ld + swz(kx)];
     }
 }
 
@@ -274,7 +292,8 @@ __device__ __forceinline__ void col_pass_body(const cpx<T>* in, cpx<T>* out, int
     }
     __syncthreads();
     if (!s_run) return;
-    const cpx<T>* ptw = stage_twiddles<T>(pt2, A + C * ld, n2);
+    cpx<T>* B = A + C * ld;   // second buffer (FP32)
+    const cpx<T>* ptw = stage_twiddles<T>(pt2, A + fft_buffers<T>() * C * ld, n2);
     const size_t half_n = (size_t)n1 * n2 / 2;
     in += inst * half_n;
     out += inst * half_n;
@@ -314,15 +333,17 @@ __device__ __forceinline__ void col_pass_body(const cpx<T>* in, cpx<T>* out, int
         }
     }
     __syncthreads();
-    if (a.mode != COL_INV) smem_fft_ip<-1>(A, n2, C, ld, ptw);
+    cpx<T>* F = A;
+    if (a.mode != COL_INV) F = block_fft<-1>(A, B, n2, C, ld, ptw);
+    cpx<T>* G = (F == A) ? B : A;   // the other buffer
     if (a.mode == COL_K || a.mode == COL_DERIV1 || a.mode == COL_DERIV2N || a.mode == COL_SYM) {
-        // in place: a thread owns the pair (ky, n2 - ky) of one column
-        const int hp = n2 / 2 + 1;
-        for (int e = threadIdx.x; e < C * hp; e += blockDim.x) {
-            const int c = e / hp, ky = e - c * hp;
+        // in place: a thread owns the pair (ky, n2 - ky), ky < n2/2, of one column, and the
+        // ky = 0 item also the middle ky = n2/2
+        const int hq = n2 >> 1;
+        auto item = [&](int c, int ky) {
             const int kyr = (n2 - ky) & (n2 - 1);
             const int kx = kx0 + c;
-            cpx<T>* col = A + c * ld;
+            cpx<T>* col = F + c * ld;
             const cpx<T> z = col[swz(ky)], zr = col[swz(kyr)];
             cpx<T> o, orr;
             if (kx > 0) {
@@ -342,12 +363,17 @@ __device__ __forceinline__ void col_pass_body(const cpx<T>* in, cpx<T>* out, int
             }
             col[swz(ky)] = o;
             if (kyr != ky) col[swz(kyr)] = orr;
+        };
+        for (int e = threadIdx.x; e < C * hq; e += blockDim.x) {
+            const int c = e >> (ln2 - 1), ky = e & (hq - 1);
+            item(c, ky);
+            if (ky == 0) item(c, hq);
         }
         __syncthreads();
     }
-    if (a.mode != COL_FWD) smem_fft_ip<+1>(A, n2, C, ld, ptw);
+    if (a.mode != COL_FWD) F = block_fft<+1>(F, G, n2, C, ld, ptw);
     cpx<T>* dst = out + (size_t)kx0 * n2;
-    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = A[(e >> ln2) * ld + swz(e & (n2 - 1))];
+    for (int e = threadIdx.x; e < C * n2; e += blockDim.x) dst[e] = F[(e >> ln2) * ld + swz(e & (n2 - 1))];
 }
 
 template <typename T>
@@ -435,7 +461,8 @@ __device__ __forceinline__ void row_inverse_body(const cpx<T>* spec, T* dst, int
     }
     __syncthreads();
     if (!s_run) return;
-    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + R * ld, L);
+    cpx<T>* B = A + R * ld;   // second buffer (FP32)
+    const cpx<T>* ptw = stage_twiddles<T>(pt1, A + fft_buffers<T>() * R * ld, L);
     const size_t nn = (size_t)n1 * n2;
     spec += inst * (nn / 2);
     dst += inst * nn;
@@ -449,14 +476,14 @@ __device__ __forceinline__ void row_inverse_body(const cpx<T>* spec, T* dst, int
         copy_async_wait_all();
     }
     __syncthreads();
-    const int half = L / 2 + 1;
-    for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
-        int r = e / half, k = e - r * half;
+    const int hq = L >> 1;   // pairs (k, L - k), k < L/2; k = 0 also takes k = L/2
+    for (int e = threadIdx.x; e < R * hq; e += blockDim.x) {
+        const int r = e >> (lL - 1), k = e & (hq - 1);
         c2r_twist_pair(A + r * ld, A + r * ld, L, k, tw1);  // in place: a thread owns k and L - k
+        if (k == 0) c2r_twist_pair(A + r * ld, A + r * ld, L, hq, tw1);
     }
     __syncthreads();
-    smem_fft_ip<+1>(A, L, R, ld, ptw);
-    const cpx<T>* z = A;
+    const cpx<T>* z = block_fft<+1>(A, B, L, R, ld, ptw);
     T vmax = T(0);
     bool bad = false;
     unsigned long long vbits = 0ull;  // FP64: max of |v0| as magnitude bits (a NaN wins)
@@ -468,13 +495,15 @@ __device__ __forceinline__ void row_inverse_body(const cpx<T>* spec, T* dst, int
         int r = e >> lL, m = e & (L - 1);
         cpx<T> v = z[r * ld + swz(m)];
         size_t o = (size_t)(y0 + r) * n1 + 2 * m;
+        // the pair (o, o + 1) moves as one aligned vector (o is even)
         if (a.mode == ROW_TAU) {
-            T u0 = T(0), u1 = T(0);
-            if (need_up) { u0 = up[o]; u1 = up[o + 1]; }
-            T c0 = celerity(a.vel, v.x, u0, phi_ref), c1 = celerity(a.vel, v.y, u1, phi_ref);
+            cpx<T> u = mk(T(0), T(0));
+            if (need_up) u = *reinterpret_cast<const cpx<T>*>(up + o);
+            T c0 = celerity(a.vel, v.x, u.x, phi_ref), c1 = celerity(a.vel, v.y, u.y, phi_ref);
             if (a.vel.mfac) {
-                c0 = c0 * a.vel.mfac[inst * nn + o];
-                c1 = c1 * a.vel.mfac[inst * nn + o + 1];
+                const cpx<T> mf = *reinterpret_cast<const cpx<T>*>(a.vel.mfac + inst * nn + o);
+                c0 = c0 * mf.x;
+                c1 = c1 * mf.y;
             }
             if constexpr (std::is_same<T, double>::value) {
                 const unsigned long long m0 = ubits(c0) & kMagBits, m1 = ubits(c1) & kMagBits;
@@ -484,11 +513,9 @@ __device__ __forceinline__ void row_inverse_body(const cpx<T>* spec, T* dst, int
                 vmax = tmax(vmax, tmax(tabs(c0), tabs(c1)));
                 bad |= (c0 != c0) || (c1 != c1);
             }
-            dst[o] = v.x;
-            dst[o + 1] = v.y;
+            *reinterpret_cast<cpx<T>*>(dst + o) = v;
         } else {
-            dst[o] = v.x + a.offset;
-            dst[o + 1] = v.y + a.offset;
+            *reinterpret_cast<cpx<T>*>(dst + o) = mk(v.x + a.offset, v.y + a.offset);
         }
     }
     if (a.mode == ROW_TAU) {
@@ -592,7 +619,7 @@ struct KnpArgs {
 template <typename T> struct KnpShapes;
 template <> struct KnpShapes<float> {   // nodes are updated two at a time (packed FP32)
     static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {4, 2, 2, 4},
-                         minb[kKnpShapes] = {2, 3, 1, 3};
+                         minb[kKnpShapes] = {4, 4, 1, 3};
 };
 template <> struct KnpShapes<double> {
     static constexpr int ty[kKnpShapes] = {8, 8, 16, 8}, npt[kKnpShapes] = {2, 1, 1, 4},
@@ -1002,15 +1029,20 @@ __global__ void velocity_kernel(const T* __restrict__ a11, const T* __restrict__
 // ------------------------------------------------------------------ launchers
 constexpr size_t kMaxDynSmem = 200 * 1024;  // dynamic shared memory the FFT kernels may request
 
+// dynamic shared memory of a transform block of nseq sequences of length L: the sequence
+// buffers and the staged twiddles
+template <typename T> static size_t fft_block_smem(int nseq, int L) {
+    return (size_t)fft_buffers<T>() * nseq * padded_len(L) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(L);
+}
+
 // R rows per row-kernel block is valid when R <= n2, R <= 16, R n1/2 <= 8 x the thread
 // bound (one radix-8 butterfly per thread) and the rows fit the shared-memory limit
 template <typename T> static bool row_ok(int n1, int n2, int R) {
     return R <= n2 && R <= 16 && R * (n1 / 2) <= 8 * FftBounds<T>::threads &&
-           (size_t)R * padded_len(n1 / 2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n1 / 2) <= kMaxDynSmem;
+           fft_block_smem<T>(R, n1 / 2) <= kMaxDynSmem;
 }
 template <typename T> static bool col_ok(int n1, int n2, int C) {
-    return C <= n1 / 2 && C <= 16 && C * n2 <= 8 * FftBounds<T>::threads &&
-           (size_t)C * padded_len(n2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n2) <= kMaxDynSmem;
+    return C <= n1 / 2 && C <= 16 && C * n2 <= 8 * FftBounds<T>::threads && fft_block_smem<T>(C, n2) <= kMaxDynSmem;
 }
 
 template <typename T>
@@ -1031,7 +1063,7 @@ int col_candidates(int n1, int n2, int* out, int max) {
 // heuristic shapes: as many valid rows as fit 40 KB of shared memory; columns until a
 // block has 1024 points
 template <typename T> static int pick_rows(int n1, int n2) {
-    const size_t per_row = (size_t)padded_len(n1 / 2) * sizeof(cpx<T>);
+    const size_t per_row = (size_t)padded_len(n1 / 2) * sizeof(cpx<T>);   // one buffer
     int R = 1;
     while (row_ok<T>(n1, n2, 2 * R) && (size_t)(2 * R) * per_row <= 40 * 1024) R *= 2;
     return R;
@@ -1047,8 +1079,8 @@ LaunchGeom geometry(int n1, int n2, int R, int C, int knp_shape) {
     LaunchGeom g{};
     g.R = R > 0 ? R : pick_rows<T>(n1, n2);
     g.C = C > 0 ? C : pick_cols(n1, n2);
-    g.row_smem = (size_t)g.R * padded_len(n1 / 2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n1 / 2);
-    g.col_smem = (size_t)g.C * padded_len(n2) * sizeof(cpx<T>) + staged_twiddle_bytes<T>(n2);
+    g.row_smem = fft_block_smem<T>(g.R, n1 / 2);
+    g.col_smem = fft_block_smem<T>(g.C, n2);
     g.row_blocks = n2 / g.R;
     g.col_blocks = (n1 / 2) / g.C;
     // the in-place FFT needs at least one thread per radix-8 butterfly; at least a warp
