@@ -11,7 +11,7 @@
 // variant), so later groups of the same kind start without timing.  If the environment
 // variable FDM_TUNE_CACHE names a file, choices also persist across processes there, one
 // JSON object per line keyed by the GPU's name and SM count; lines that do not parse or
-// name shapes this build does not offer are ignored.
+// name shapes this library does not offer are ignored.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
