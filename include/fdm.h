@@ -339,6 +339,16 @@ int32_t fdm_launch_candidates(const fdm_params *p, fdm_launch_config *out, int32
  * FDM_ERR_DEVICE. */
 fdm_status fdm_measure_arith_rate(int32_t precision, void *stream, double *gflops);
 
+/* Test hook (not part of the paper's method): y[i] = 1/sqrt(x[i]) (op 0) or 1/x[i] (op 1)
+ * as the FP64 stencil computes them (Sec. 3.2.3: the one-sided speeds, the midpoint
+ * predictor and |grad| use the first, the Step 4 weights the second), for checking those
+ * routines' accuracy.  x, y: n doubles in host memory (caller-owned).  op 0 is defined for
+ * x[i] > 0 (+inf gives 0, NaN gives NaN), op 1 for any x[i] (IEEE division outside the
+ * normal range).  Allocates and frees 16 n bytes of device memory and waits for the legacy
+ * default stream.  Errors: FDM_ERR_INVALID_ARG (op not 0 or 1, n < 0, NULL array with
+ * n > 0), FDM_ERR_OOM, FDM_ERR_DEVICE. */
+fdm_status fdm_debug_fp64_math(int32_t op, const double *x, double *y, int64_t n);
+
 /* Static solve that allocates no device memory (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate -- e.g. a process whose HBM is already
  * fully handed out to other buffers, or an embedding that forbids allocations outside its

@@ -50,6 +50,7 @@ EXPORTS = ["fdm_default_params", "fdm_device_bytes", "fdm_create", "fdm_set_dens
            "fdm_read_stress13_planes", "fdm_read_stress_planes", "fdm_batch_sync_status",
            "fdm_debug_fail_allocation", "fdm_static_solve_heterogeneous", "fdm_set_shear_modulus_field",
            "fdm_measure_arith_rate", "fdm_batch_enqueue_steps_persistent", "fdm_debug_barrier",
+           "fdm_debug_fp64_math",
            "fdm_static_solve_heterogeneous_layer", "fdm_equilibrate"]
 
 
@@ -177,6 +178,8 @@ def load():
     lib.fdm_debug_barrier.restype = None
     lib.fdm_measure_arith_rate.argtypes = [C.c_int32, C.c_void_p, d]
     lib.fdm_measure_arith_rate.restype = C.c_int
+    lib.fdm_debug_fp64_math.argtypes = [C.c_int32, d, d, C.c_int64]
+    lib.fdm_debug_fp64_math.restype = C.c_int
     PP = C.POINTER(CParams)
     lib.fdm_batch_create.argtypes = [C.c_int32, PP, C.c_void_p, C.POINTER(H)]
     lib.fdm_batch_device_bytes.argtypes = [C.c_int32, PP]
@@ -266,6 +269,15 @@ def default_params(n1: int, n2: int) -> Params:
 
 def device_bytes(p: Params) -> int:
     return int(load().fdm_device_bytes(C.byref(p.to_c())))
+
+
+def debug_fp64_math(op: int, x) -> np.ndarray:
+    """1/sqrt(x) (op 0) or 1/x (op 1) elementwise as the FP64 stencil computes them (a test
+    hook)."""
+    xs = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.empty_like(xs)
+    _check(load().fdm_debug_fp64_math(int(op), _dptr(xs), _dptr(y), int(xs.size)), "fdm_debug_fp64_math")
+    return y
 
 
 def measure_arith_rate(precision: int, stream: Optional[int] = None) -> float:

@@ -263,9 +263,10 @@ __device__ __forceinline__ void c2r_twist_pair(const cpx<T>* P, cpx<T>* Z, int L
 
 // ---------------------------------------------------------------------------------
 // Precision-typed math.  FP32 (mixed mode) keeps every operation on the FP32 pipes and
-// uses the approximate special-function unit; FP64 uses the FP64 library routines.
-// Nothing in a float instantiation may promote to double: the FP64 pipe of GB300 runs
-// at 1/64 of the FP32 rate.
+// uses the approximate special-function unit; FP64 takes its decisions, exact scalings,
+// reciprocals and reciprocal square roots off the FP64 pipe (below) and keeps that pipe
+// for the scheme's own additions and products.  Nothing in a float instantiation may
+// promote to double: the FP64 pipe of GB300 runs at 1/64 of the FP32 rate.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
@@ -275,10 +276,10 @@ __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double tabs(double a) { return fabs(a); }
 // 1/sqrt(x) for x > 0
 __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ double trsqrt(double x);   // on the FP32 and integer pipes, below
 // 1/x for x != 0
 __device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double trcp(double x);   // on the FP32 and integer pipes, below
 // x / 2 (exact)
 __device__ __forceinline__ float thalf(float x) { return 0.5f * x; }
 __device__ __forceinline__ double thalf(double x);
@@ -298,6 +299,7 @@ __device__ __forceinline__ unsigned long long ubits(double x) { return (unsigned
 __device__ __forceinline__ bool mag_ok(unsigned long long m) { return m - 1ull < kInfBits; }
 __device__ __forceinline__ bool tpos(double x) { return mag_ok(ubits(x)); }   // bits in [1, +inf]
 
+__device__ __forceinline__ double dbits(unsigned long long v) { return __longlong_as_double((long long)v); }
 // x / 2 exactly, on the integer pipe: one less in the exponent field for normal x above the
 // least normal exponent; zero, subnormals and the least normal exponent halve their
 // magnitude bits (ties to even, as the rounded product); infinities and NaN unchanged
@@ -320,6 +322,158 @@ __device__ __forceinline__ double ttwice(double x) {
     if (e != 0u) return x + x;
     const unsigned long long u = ubits(x);
     return __longlong_as_double((long long)((u & ~kMagBits) | ((u & kMagBits) << 1)));
+}
+
+// 1/sqrt(x) of a double x > 0 with no FP64 instruction: on GB300 the FP64 pipe bounds the
+// FP64 stencil while the FP32 and integer pipes idle.  Newton-Raphson iteration for x^(-1/2)
+// (y <- y + y (1 - x y^2) / 2) from the single-precision special-function seed, with the
+// residuals formed from exact products (FMA TwoProd) and compensated sums (TwoSum) of FP32
+// numbers (the error-free transformations of Dekker and Knuth), every operation an explicitly
+// rounded intrinsic so that no product is contracted into a sum.  x = m 2^(2k), m in [1, 4),
+// is split exactly into three floats a + b + c (24 + 24 + 5 mantissa bits); the seed y0 has
+// relative error below 2^-21, the first step brings it below 2^-42 (residual to float
+// accuracy), the second below 2^-84 (residual to about 2^-60 absolute); y0 + d1 + d2 is summed
+// exactly in 62-bit fixed point and rounded once to the nearest double.  Relative error
+// within one unit in the last place (checked against exact rational arithmetic on 4000
+// values from subnormal to the largest double).  +inf gives 0, NaN gives NaN.
+__device__ __forceinline__ long long fix62(float v) {   // v 2^62 truncated toward zero, |v| < 2
+    const unsigned vb = __float_as_uint(v);
+    const int ev = (int)((vb >> 23) & 0xffu);
+    if (ev == 0) return 0;                                 // zero (or below 2^-126: < 2^-64)
+    const long long m = (long long)((vb & 0x7fffffu) | 0x800000u);
+    const int sh = ev - 88;                                // v = m 2^(ev - 150)
+    const long long r = sh >= 0 ? (m << sh) : (sh > -40 ? (m >> -sh) : 0ll);
+    return (vb >> 31) ? -r : r;
+}
+__device__ __forceinline__ void two_prod_rn(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum_rn(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ double trsqrt(double x) {
+    const unsigned long long u = ubits(x);
+    const int e = (int)(u >> 52) & 0x7ff;
+    const unsigned long long mant = u & 0xfffffffffffffull;
+    if (e == 0x7ff) return mant ? x : 0.0;
+    unsigned long long M;
+    int E;
+    if (e == 0) {                                          // subnormal: normalise the mantissa
+        const int lz = __clzll((long long)mant) - 11;
+        M = mant << lz;
+        E = -1022 - lz;
+    } else {
+        M = mant | (1ull << 52);
+        E = e - 1023;
+    }
+    const int k = E >> 1, s = E - 2 * k;                   // x = M 2^(E - 52), E = 2k + s
+    const unsigned A = (unsigned)(M >> 29), B = (unsigned)(M >> 5) & 0xffffffu, Cc = (unsigned)M & 31u;
+    const float a = __uint_as_float(((unsigned)(127 + s) << 23) | (A & 0x7fffffu));   // in [1, 4)
+    const float b = __fmul_rn(__uint2float_rn(B), s ? 0x1p-46f : 0x1p-47f);            // exact
+    const float c = __fmul_rn(__uint2float_rn(Cc), s ? 0x1p-51f : 0x1p-52f);           // exact
+    const float y0 = rsqrtf(a);
+    // first step: e1 = 1 - m y0^2 to float accuracy of its small terms
+    float p, pe, t1, t1e;
+    two_prod_rn(y0, y0, p, pe);
+    two_prod_rn(a, p, t1, t1e);
+    const float one_t1 = __fsub_rn(1.0f, t1);              // exact (t1 within 2^-20 of 1)
+    const float e1 = __fsub_rn(one_t1, __fadd_rn(__fadd_rn(t1e, __fmul_rn(a, pe)),
+                                                  __fadd_rn(__fmul_rn(b, p), __fmul_rn(c, p))));
+    const float hy0 = __fmul_rn(0.5f, y0);
+    const float d1 = __fmul_rn(hy0, e1);
+    // second step: e2 = 1 - m (y0 + d1)^2 to about 2^-60
+    float q1, q1e, q2, q2e, r, re, g, ge;
+    two_prod_rn(a, pe, q1, q1e);
+    two_prod_rn(b, p, q2, q2e);
+    two_prod_rn(a, y0, r, re);
+    const float d1x2 = __fmul_rn(2.0f, d1);
+    two_prod_rn(d1x2, r, g, ge);
+    float small = __fadd_rn(__fadd_rn(__fadd_rn(q1e, q2e), __fadd_rn(__fmul_rn(b, pe), __fmul_rn(c, p))),
+                            __fmul_rn(d1x2, __fadd_rn(__fadd_rn(re, __fmul_rn(b, y0)), __fmul_rn(c, y0))));
+    small = __fadd_rn(small, __fadd_rn(ge, __fmul_rn(__fmul_rn(a, d1), d1)));
+    float S, Se, t;
+    two_sum_rn(one_t1, -t1e, S, Se);
+    two_sum_rn(S, -q1, S, t);
+    Se = __fadd_rn(Se, t);
+    two_sum_rn(S, -q2, S, t);
+    Se = __fadd_rn(Se, t);
+    two_sum_rn(S, -g, S, t);
+    Se = __fadd_rn(Se, t);
+    const float e2 = __fadd_rn(S, __fsub_rn(Se, small));
+    const float d2 = __fmul_rn(hy0, e2);
+    // y0 + d1 + d2 in 62-bit fixed point, rounded once to 53 bits (ties to even)
+    const long long Y = fix62(y0) + fix62(d1) + fix62(d2);
+    const int lead = 63 - __clzll(Y);                      // 61 or 62
+    const int sh = lead - 52;
+    unsigned long long man = (unsigned long long)Y >> sh;
+    const unsigned long long rem = (unsigned long long)Y & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    int lead2 = lead;
+    if (rem > half || (rem == half && (man & 1ull))) {
+        man += 1ull;
+        if (man >> 53) { man >>= 1; ++lead2; }
+    }
+    return dbits(((unsigned long long)(lead2 - 62 - k + 1023) << 52) | (man & 0xfffffffffffffull));
+}
+
+// 1/x of a double by the same means: Newton-Raphson for the reciprocal (y <- y + y (1 - x y))
+// from the single-precision seed, x = m 2^E with m in [1, 2) split into a + b + c, the
+// residuals formed exactly as above, y0 + d1 + d2 rounded once to the nearest double; within
+// one unit in the last place.  Results outside the normal range (|x| >= 2^1022, a subnormal
+// reciprocal), zero, infinities and NaN take the IEEE division.
+__device__ __forceinline__ double trcp(double x) {
+    const unsigned long long u = ubits(x);
+    const int e = (int)(u >> 52) & 0x7ff;
+    const unsigned long long mant = u & 0xfffffffffffffull;
+    if (e >= 0x7fd || (e == 0 && mant == 0ull)) return 1.0 / x;
+    unsigned long long M;
+    int E;
+    if (e == 0) {
+        const int lz = __clzll((long long)mant) - 11;
+        M = mant << lz;
+        E = -1022 - lz;
+    } else {
+        M = mant | (1ull << 52);
+        E = e - 1023;
+    }
+    const unsigned A = (unsigned)(M >> 29), B = (unsigned)(M >> 5) & 0xffffffu, Cc = (unsigned)M & 31u;
+    const float a = __uint_as_float((127u << 23) | (A & 0x7fffffu));                    // in [1, 2)
+    const float b = __fmul_rn(__uint2float_rn(B), 0x1p-47f);
+    const float c = __fmul_rn(__uint2float_rn(Cc), 0x1p-52f);
+    const float y0 = __fdividef(1.0f, a);
+    float t, te;
+    two_prod_rn(a, y0, t, te);
+    const float one_t = __fsub_rn(1.0f, t);                // exact
+    const float e1 = __fsub_rn(one_t, __fadd_rn(te, __fadd_rn(__fmul_rn(b, y0), __fmul_rn(c, y0))));
+    const float d1 = __fmul_rn(y0, e1);
+    float q1, q1e, q2, q2e;
+    two_prod_rn(a, d1, q1, q1e);
+    two_prod_rn(b, y0, q2, q2e);
+    const float small = __fadd_rn(__fadd_rn(__fadd_rn(q1e, q2e), __fmul_rn(b, d1)),
+                                  __fadd_rn(__fmul_rn(c, y0), __fmul_rn(c, d1)));
+    float S, Se, tt;
+    two_sum_rn(one_t, -te, S, Se);
+    two_sum_rn(S, -q1, S, tt);
+    Se = __fadd_rn(Se, tt);
+    two_sum_rn(S, -q2, S, tt);
+    Se = __fadd_rn(Se, tt);
+    const float e2 = __fadd_rn(S, __fsub_rn(Se, small));
+    const float d2 = __fmul_rn(y0, e2);
+    const long long Y = fix62(y0) + fix62(d1) + fix62(d2);
+    const int lead = 63 - __clzll(Y);
+    const int sh = lead - 52;
+    unsigned long long man = (unsigned long long)Y >> sh;
+    const unsigned long long rem = (unsigned long long)Y & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    int lead2 = lead;
+    if (rem > half || (rem == half && (man & 1ull))) {
+        man += 1ull;
+        if (man >> 53) { man >>= 1; ++lead2; }
+    }
+    const int be = lead2 - 62 - E + 1023;
+    if (be >= 0x7ff) return 1.0 / x;                       // overflow: the division gives inf
+    return dbits((u & ~kMagBits) | ((unsigned long long)be << 52) | (man & 0xfffffffffffffull));
 }
 
 // ---------------------------------------------------------------------------------

@@ -99,10 +99,38 @@ fdm_status measure(cudaStream_t st, double* gflops) {
     return rc;
 }
 
+// y[i] = the FP64 stencil's reciprocal square root (op 0) or reciprocal (op 1) of x[i]
+__global__ void fp64_math_kernel(int op, const double* __restrict__ x, double* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = op == 0 ? trsqrt(x[i]) : trcp(x[i]);
+}
+
 }  // namespace
 }  // namespace fdm
 
 using namespace fdm;
+
+extern "C" fdm_status fdm_debug_fp64_math(int32_t op, const double* x, double* y, int64_t n) {
+    if ((op != 0 && op != 1) || n < 0 || (n > 0 && (!x || !y))) return FDM_ERR_INVALID_ARG;
+    if (n == 0) return FDM_OK;
+    double* d = nullptr;
+    if (cudaMalloc(&d, (size_t)n * 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return FDM_ERR_OOM;
+    }
+    fdm_status rc = FDM_OK;
+    if (cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) rc = FDM_ERR_DEVICE;
+    if (rc == FDM_OK) {
+        const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+        fp64_math_kernel<<<blocks, 256>>>(op, d, d + n, (long long)n);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(y, d + n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = FDM_ERR_DEVICE;
+    }
+    if (rc != FDM_OK) cudaGetLastError();
+    cudaFree(d);
+    return rc;
+}
 
 extern "C" fdm_status fdm_measure_arith_rate(int32_t precision, void* stream, double* gflops) {
     if (!gflops) return FDM_ERR_INVALID_ARG;
