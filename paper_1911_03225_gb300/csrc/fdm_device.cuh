@@ -614,7 +614,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
     for (int t = 0; t < 2; ++t) {
         ey[t] = (t == 0 ? bp : bm) * dt_h;
         const T sgn = (t == 0) ? T(-1) : T(1);
-        Y[t] = ys[t].D * ey[t] + thalf(ys[t].S * ey[t] * (ey[t] + sgn));
+        Y[t] = ey[t] * (ys[t].D + thalf(ys[t].S) * (ey[t] + sgn));
         dY[t] = ys[t].D + ys[t].S * (ey[t] + thalf(sgn));
     }
     T acc = T(0);
@@ -624,7 +624,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
         const T ex = (s == 0 ? ap : am) * dt_h;
         const T Dx = xs[s].D, Sx = xs[s].S;
         const T sgn = (s == 0) ? T(-1) : T(1);
-        const T X = Dx * ex + thalf(Sx * ex * (ex + sgn));
+        const T X = ex * (Dx + thalf(Sx) * (ex + sgn));
         const T dX = Dx + Sx * (ex + thalf(sgn));
         const T fx = f(cx, 0);
         T accs = T(0);
@@ -634,7 +634,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
             // mixed second difference of the quadrant cell (h^2 times the bilinear cross term)
             const T mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
             const T cross = (cx * cy > 0) ? mixed : -mixed;
-            const T val = f0 + X + Y[t] + cross * ex * ey[t];
+            const T val = X + Y[t] + cross * ex * ey[t];   // minus f0, added once below
             T p = dX + cross * ey[t];
             T q = dY[t] + cross * ex;
             if (time_level == 0) {
@@ -654,7 +654,7 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
         }
         acc += nx[s] * accs;
     }
-    return acc * inv_w;
+    return f0 + acc * inv_w;   // the weights sum to one
 }
 
 // ---------------------------------------------------------------------------------
