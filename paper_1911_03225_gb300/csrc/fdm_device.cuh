@@ -965,7 +965,7 @@ __device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int 
     for (int t = 0; t < 2; ++t) {
         ey[t] = (t == 0 ? bp : bm) * dth;
         const df2 sgn = bcast2(df((t == 0) ? -1.0f : 1.0f));
-        Y[t] = yD[t] * ey[t] + thalf(yS[t] * ey[t] * (ey[t] + sgn));
+        Y[t] = ey[t] * (yD[t] + thalf(yS[t]) * (ey[t] + sgn));
         dY[t] = yD[t] + yS[t] * (ey[t] + thalf(sgn));
     }
     df2 acc = zero;
@@ -975,7 +975,7 @@ __device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int 
         const df2 ex = (s == 0 ? ap : am) * dth;
         const df2 Dx = xD[s], Sx = xS[s];
         const df2 sgn = bcast2(df((s == 0) ? -1.0f : 1.0f));
-        const df2 X = Dx * ex + thalf(Sx * ex * (ex + sgn));
+        const df2 X = ex * (Dx + thalf(Sx) * (ex + sgn));
         const df2 dX = Dx + Sx * (ex + thalf(sgn));
         const df2 fx = f(cx, 0);
         df2 accs = zero;
@@ -984,7 +984,7 @@ __device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int 
             const int cy = (t == 0) ? 1 : -1;
             const df2 mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
             const df2 cross = (cx * cy > 0) ? mixed : -mixed;
-            const df2 val = f0 + X + Y[t] + cross * ex * ey[t];
+            const df2 val = X + Y[t] + cross * ex * ey[t];   // minus f0, added once below
             df2 p = dX + cross * ey[t];
             df2 q = dY[t] + cross * ex;
             if (time_level == 0) {
@@ -1003,7 +1003,7 @@ __device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int 
         }
         acc = acc + nx[s] * accs;
     }
-    return acc * one;
+    return f0 + acc;   // the weights sum to one
 }
 
 }  // namespace fdm
