@@ -626,13 +626,13 @@ __device__ __forceinline__ T knp_node(F f, T v0, T dt_h, T theta, int theta_code
         const T sgn = (s == 0) ? T(-1) : T(1);
         const T X = ex * (Dx + thalf(Sx) * (ex + sgn));
         const T dX = Dx + Sx * (ex + thalf(sgn));
-        const T fx = f(cx, 0);
+        const T fx0 = (s == 0) ? Dx : -Dx;   // f(cx, 0) - f0, the side's first difference
         T accs = T(0);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int cy = (t == 0) ? 1 : -1;
             // mixed second difference of the quadrant cell (h^2 times the bilinear cross term)
-            const T mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
+            const T mixed = (f(cx, cy) - f(0, cy)) - fx0;
             const T cross = (cx * cy > 0) ? mixed : -mixed;
             const T val = X + Y[t] + cross * ex * ey[t];   // minus f0, added once below
             T p = dX + cross * ey[t];
@@ -977,12 +977,12 @@ __device__ __forceinline__ df2 knp_node_df2(F f, df2 v0, df dt_h, df theta, int 
         const df2 sgn = bcast2(df((s == 0) ? -1.0f : 1.0f));
         const df2 X = ex * (Dx + thalf(Sx) * (ex + sgn));
         const df2 dX = Dx + Sx * (ex + thalf(sgn));
-        const df2 fx = f(cx, 0);
+        const df2 fx0 = (s == 0) ? Dx : -Dx;   // f(cx, 0) - f0, the side's first difference
         df2 accs = zero;
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int cy = (t == 0) ? 1 : -1;
-            const df2 mixed = (f(cx, cy) - f(0, cy)) - (fx - f0);
+            const df2 mixed = (f(cx, cy) - f(0, cy)) - fx0;
             const df2 cross = (cx * cy > 0) ? mixed : -mixed;
             const df2 val = X + Y[t] + cross * ex * ey[t];   // minus f0, added once below
             df2 p = dX + cross * ey[t];
