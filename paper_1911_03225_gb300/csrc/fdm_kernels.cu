@@ -113,7 +113,7 @@ template <typename T> __host__ __device__ __forceinline__ size_t staged_twiddle_
     return std::is_same<T, float>::value ? (size_t)pass_table_len(L) * sizeof(cpx<T>) : 0;
 }
 // The FP32 transforms pass between two shared buffers (one barrier per pass); the others
-// transform in place in one.  Buffers of the block's sequences: nbuf<T>() x nseq x ld.
+// transform in place in one.  Buffers of the block's sequences: fft_buffers<T>() x nseq x ld.
 template <typename T> __host__ __device__ constexpr int fft_buffers() { return std::is_same<T, float>::value ? 2 : 1; }
 // the transform of the block's sequences in A (and the second buffer B for FP32); returns the
 // buffer holding the result
